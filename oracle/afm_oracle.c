@@ -1,0 +1,588 @@
+/*
+ * afm_oracle.c -- FP64 CPU oracle (TEST INFRASTRUCTURE ONLY; see afm_oracle.h).
+ *
+ * Plain double-precision restatement, in SI units, of:
+ *   - the modal reduction of the Euler-Bernoulli cantilever (Eq. 1 -> Eq. 2,
+ *     App. B) with the paper's overflow-safe exponential mode shapes
+ *     (Sec. 3.2, Eqs. 6-7), Newton roots and Simpson integration (Sec. 3.2);
+ *   - the explicit classic 4th-order Runge-Kutta time loop (Sec. 3.2);
+ *   - the L2 cost functional J^2 = int (U - u)^2 dt (Eq. 5), as a sum over the
+ *     sampled record;
+ *   - particle-swarm optimisation with the velocity update of Eq. 8 (Sec. 3.4);
+ *   - synthetic records made at a finer step than the solver (the paper's
+ *     inverse-crime measure, Sec. 4.1);
+ *   - the DMT and DMT + Kelvin-Voigt tip-sample laws (Hertz contact and van
+ *     der Waals, named as the richer force models in Sec. 2.2 and Sec. 5),
+ *     the paper's Hooke and spring-damper laws (Eqs. 3-4), and a linear test
+ *     spring whose response has a closed form.
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), written
+ * here from its published definition.
+ *
+ * Nothing here is blocked, fused or reordered beyond what the method states.
+ */
+#include "afm_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+int orc_get_threads(void) { return g_threads; }
+
+/* ======================================================================== */
+/* Philox4x32-10 (SC'11): ten rounds of two 32x32->64 multiplies, xor with  */
+/* the other counter words and the round key; the key is bumped by the Weyl  */
+/* constants between rounds.                                                 */
+/* ======================================================================== */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Top 24 bits of a word scaled by 2^-24: a uniform on [0, 1) that is exact in
+ * both float and double. */
+double orc_uniform(uint32_t word) { return (double)(word >> 8) * (1.0 / 16777216.0); }
+
+/* One uniform from the stream: key = seed, counter = (c0, c1, c2, tag<<16|block),
+ * word `word` of the four outputs. */
+double orc_draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                uint32_t tag, uint32_t block, int word)
+{
+    uint32_t ctr[4] = {c0, c1, c2, (tag << 16) | block};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return orc_uniform(out[word]);
+}
+
+/* ======================================================================== */
+/* Modal setup (Sec. 3.2): beta_i L by Newton, mode shapes in exponential    */
+/* form, Simpson integrals.                                                  */
+/* ======================================================================== */
+
+/* i-th root (i >= 1) of cos x cosh x + 1 = 0, found by Newton on the
+ * equivalent cos x + 1/cosh x = 0 (no overflow for large x). */
+double orc_beam_root(int i)
+{
+    double x = (2.0 * i - 1.0) * M_PI / 2.0;
+    for (int it = 0; it < 200; ++it) {
+        double f = cos(x) + 1.0 / cosh(x);
+        double fp = -sin(x) - tanh(x) / cosh(x);
+        double dx = f / fp;
+        x -= dx;
+        if (fabs(dx) < 1e-16 * x) break;
+    }
+    return x;
+}
+
+/* Paper's exponential form of the clamped-free mode shape (Eq. 6), as a
+ * function of xi = x / L for b = beta L:
+ *   Phi = [2 sin(b xi) - 2G cos(b xi) + (G-1) e^{b xi} + (G+1) e^{-b xi}] / 2
+ * with G from Eq. 7.  The printed denominator of Eq. 7 has "- e^{-2 beta L}";
+ * the free-end conditions require "+ e^{-2 beta L}" (reading R2).  G - 1 is
+ * formed directly (same algebra) so that it keeps its relative precision. */
+double orc_mode_shape(double b, double xi)
+{
+    double e1 = exp(-b), e2 = exp(-2.0 * b);
+    double num = 1.0 - e2 + 2.0 * e1 * sin(b);
+    double den = 1.0 + e2 + 2.0 * e1 * cos(b);
+    double Gm1 = (-2.0 * e2 + 2.0 * e1 * (sin(b) - cos(b))) / den;  /* = num/den - 1 */
+    double G = num / den;
+    double bx = b * xi;
+    return (2.0 * sin(bx) - 2.0 * G * cos(bx) + Gm1 * exp(bx) + (G + 1.0) * exp(-bx)) / 2.0;
+}
+
+/* Composite Simpson rule on [0, 1] with n_points (odd) samples. */
+static double simpson(const double* f, int n_points)
+{
+    int n = n_points - 1;
+    double h = 1.0 / n, s = f[0] + f[n];
+    for (int j = 1; j < n; ++j) s += (j % 2 ? 4.0 : 2.0) * f[j];
+    return s * h / 3.0;
+}
+
+/* For each mode: beta_i L, gamma_i = <phi,1>/<phi,phi> and <phi,phi>/L of the
+ * tip-normalised shape phi = Phi / Phi(L), and Phi(L).  Integrals by Simpson
+ * on n_points samples (Sec. 3.2; App. A uses 501 points). */
+int orc_modal_factors(int n_modes, int n_points, double* bL, double* gam,
+                      double* int_phi2, double* phi_tip)
+{
+    if (n_modes < 1 || n_modes > ORC_MAXM || n_points < 3 || n_points % 2 == 0) return -1;
+    double* f1 = (double*)malloc(sizeof(double) * n_points);
+    double* f2 = (double*)malloc(sizeof(double) * n_points);
+    for (int i = 0; i < n_modes; ++i) {
+        double b = orc_beam_root(i + 1);
+        double tip = orc_mode_shape(b, 1.0);
+        for (int j = 0; j < n_points; ++j) {
+            double p = orc_mode_shape(b, (double)j / (n_points - 1)) / tip;
+            f1[j] = p;
+            f2[j] = p * p;
+        }
+        double I1 = simpson(f1, n_points), I2 = simpson(f2, n_points);
+        bL[i] = b;
+        gam[i] = I1 / I2;
+        if (int_phi2) int_phi2[i] = I2;
+        if (phi_tip) phi_tip[i] = tip;
+    }
+    free(f1);
+    free(f2);
+    return 0;
+}
+
+/* Problem setup for the modal models (R3, R4, R6):
+ *   omega_i = omega_1 (beta_i / beta_1)^2, modal mass m = k / omega_1^2,
+ *   base y_b = a sin(w t + psi) with w = omega_1, and a, psi such that the free
+ *   linear steady tip deflection is A0 cos(w t); the initial state is that
+ *   steady state at t = 0.  Point mass: one mode with gamma = 1. */
+int orc_setup(const orc_case* c, orc_modal* md)
+{
+    memset(md, 0, sizeof(*md));
+    int m = c->model == ORC_POINT_MASS ? 1 : c->n_modes;
+    if (m < 1 || m > ORC_MAXM || c->spc < 2) return -1;
+    md->m = m;
+    double w1 = 2.0 * M_PI * c->f1;
+    if (c->model == ORC_POINT_MASS) {
+        md->w[0] = w1;
+        md->gam[0] = 1.0;
+    } else {
+        double bL[ORC_MAXM], gam[ORC_MAXM];
+        if (orc_modal_factors(m, 501, bL, gam, NULL, NULL)) return -1;
+        for (int i = 0; i < m; ++i) {
+            md->w[i] = w1 * (bL[i] / bL[0]) * (bL[i] / bL[0]);
+            md->gam[i] = gam[i];
+        }
+    }
+    md->mass = c->k / (w1 * w1);
+    md->wd = w1;
+    double w = md->wd;
+    double complex H[ORC_MAXM], Hs = 0.0;
+    for (int i = 0; i < m; ++i) {
+        H[i] = md->gam[i] / (md->w[i] * md->w[i] - w * w + I * w * md->w[i] / c->Q[i]);
+        Hs += H[i];
+    }
+    md->a = c->A0 / (w * w * cabs(Hs));
+    md->psi = M_PI / 2.0 - carg(Hs);
+    for (int i = 0; i < m; ++i) {
+        double complex ci = md->a * w * w * H[i] * cexp(I * md->psi);
+        md->eta0[i] = cimag(ci);
+        md->etad0[i] = w * creal(ci);
+    }
+    md->dt = 1.0 / (c->f1 * c->spc);
+    return 0;
+}
+
+/* g = -d^2 y_b/dt^2 at the half-step index j, i.e. t = j dt / 2, with the
+ * phase reduced modulo one drive period (2 spc half steps). */
+double orc_drive_half(const orc_modal* md, int spc, long j)
+{
+    long jj = j % (2L * spc);
+    double t = (double)jj * (md->dt / 2.0);
+    return md->a * md->wd * md->wd * sin(md->wd * t + md->psi);
+}
+
+/* ======================================================================== */
+/* Tip-sample forces.  d is the gap, ddot its rate; F > 0 pushes the tip     */
+/* away from the sample.                                                     */
+/* ======================================================================== */
+double orc_force(int kind, const double th[5], double d, double ddot)
+{
+    switch (kind) {
+    case ORC_F_LINEAR:
+        return -th[0] * (d - th[1]);
+    case ORC_F_DMT:
+    case ORC_F_DMT_KV: {
+        double E = th[0], H = th[1], R = th[2], a0 = th[3];
+        if (d > a0) return -H * R / (6.0 * d * d);
+        double delta = a0 - d;
+        double F = (4.0 / 3.0) * E * sqrt(R) * pow(delta, 1.5) - H * R / (6.0 * a0 * a0);
+        if (kind == ORC_F_DMT_KV) F -= th[4] * sqrt(R * delta) * ddot;
+        return F;
+    }
+    case ORC_F_HOOKE:
+        return d < th[1] ? th[0] * (th[1] - d) : 0.0;
+    case ORC_F_SPRING_DAMPER:
+        return d < th[1] ? th[0] * (th[1] - d) - th[2] * ddot : 0.0;
+    default:
+        return 0.0;
+    }
+}
+
+/* Right-hand side of the modal system (Eq. 2 with 2 zeta omega_i = omega_i/Q,
+ * reading R4):  eta_i'' = F/m + gamma_i g - omega_i^2 eta_i - (omega_i/Q_i) eta_i'
+ * with the gap d = Zc + sum_i eta_i (tip-normalised shapes, reading R5). */
+static void rhs(const orc_case* c, const orc_modal* md, const double th[5], double g,
+                const double* y, double* f)
+{
+    int m = md->m;
+    double u = 0.0, ud = 0.0;
+    for (int i = 0; i < m; ++i) { u += y[i]; ud += y[m + i]; }
+    double F = orc_force(c->force, th, c->Zc + u, ud);
+    for (int i = 0; i < m; ++i) {
+        f[i] = y[m + i];
+        f[m + i] = F / md->mass + md->gam[i] * g - md->w[i] * md->w[i] * y[i]
+                   - (md->w[i] / c->Q[i]) * y[m + i];
+    }
+}
+
+/* Classic RK4 (Sec. 3.2) over n_steps record steps, each split into `sub`
+ * equal sub-steps (sub = 1: the solver's own step; sub = 4: the finer step of
+ * the synthetic records, reading R10).  u[n] = tip deflection at the end of
+ * record step n + 1.  state (optional) receives [n_steps + 1][2m] modal states
+ * at the record instants, starting with t = 0. */
+int orc_forward(const orc_case* c, const double th[5], int n_steps, int sub,
+                double* u, double* state)
+{
+    orc_case cf = *c;
+    cf.spc = c->spc * sub;
+    orc_modal md;
+    if (orc_setup(&cf, &md)) return -1;
+    int m = md.m, n2 = 2 * m;
+    double y[2 * ORC_MAXM], k1[2 * ORC_MAXM], k2[2 * ORC_MAXM], k3[2 * ORC_MAXM],
+        k4[2 * ORC_MAXM], yt[2 * ORC_MAXM];
+    for (int i = 0; i < m; ++i) { y[i] = md.eta0[i]; y[m + i] = md.etad0[i]; }
+    if (state) memcpy(state, y, sizeof(double) * n2);
+    double h = md.dt;
+    long step = 0;
+    for (int n = 0; n < n_steps; ++n) {
+        for (int s = 0; s < sub; ++s, ++step) {
+            double g0 = orc_drive_half(&md, cf.spc, 2 * step);
+            double gh = orc_drive_half(&md, cf.spc, 2 * step + 1);
+            double g1 = orc_drive_half(&md, cf.spc, 2 * step + 2);
+            rhs(&cf, &md, th, g0, y, k1);
+            for (int q = 0; q < n2; ++q) yt[q] = y[q] + 0.5 * h * k1[q];
+            rhs(&cf, &md, th, gh, yt, k2);
+            for (int q = 0; q < n2; ++q) yt[q] = y[q] + 0.5 * h * k2[q];
+            rhs(&cf, &md, th, gh, yt, k3);
+            for (int q = 0; q < n2; ++q) yt[q] = y[q] + h * k3[q];
+            rhs(&cf, &md, th, g1, yt, k4);
+            for (int q = 0; q < n2; ++q)
+                y[q] = y[q] + (h / 6.0) * (k1[q] + 2.0 * k2[q] + 2.0 * k3[q] + k4[q]);
+        }
+        double tip = 0.0;
+        for (int i = 0; i < m; ++i) tip += y[i];
+        u[n] = tip;
+        if (state) memcpy(state + (size_t)(n + 1) * n2, y, sizeof(double) * n2);
+    }
+    return 0;
+}
+
+/* Eq. 5 on the sampled record (reading R8): S = sum_n (U_n - u_n)^2, so that
+ * J^2 = dt * S. */
+double orc_misfit(const double* U, const double* u, int n)
+{
+    double S = 0.0;
+    for (int j = 0; j < n; ++j) S += (U[j] - u[j]) * (U[j] - u[j]);
+    return S;
+}
+
+/* Normalised coordinates x in [0,1]^D -> physical slots (reading R12):
+ * log10-linear for log dims, linear otherwise. */
+void orc_map(const orc_pmap* pm, const double* x, double th[5])
+{
+    for (int s = 0; s < 5; ++s) th[s] = pm->fixed[s];
+    for (int d = 0; d < pm->D; ++d) {
+        double lo = pm->lo[d], hi = pm->hi[d];
+        if (pm->logs[d])
+            th[pm->slot[d]] = pow(10.0, log10(lo) + x[d] * (log10(hi) - log10(lo)));
+        else
+            th[pm->slot[d]] = lo + x[d] * (hi - lo);
+    }
+}
+
+static int forward_any(const orc_case* c, const double th[5], int n, double* u)
+{
+    return orc_forward(c, th, n, 1, u, NULL);
+}
+
+int orc_misfit_x(const orc_case* c, const orc_pmap* pm, const double* x,
+                 const double* U, int n, double* S)
+{
+    double th[5];
+    orc_map(pm, x, th);
+    double* u = (double*)malloc(sizeof(double) * n);
+    int rc = forward_any(c, th, n, u);
+    *S = rc ? INFINITY : orc_misfit(U, u, n);
+    free(u);
+    return rc;
+}
+
+/* Misfit of P candidates; x is [D][P] (dimension-major). Non-finite -> +inf. */
+int orc_misfit_batch(const orc_case* c, const orc_pmap* pm, const double* x,
+                     int P, const double* U, int n, double* S)
+{
+    int D = pm->D, bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads) reduction(+ : bad)
+#endif
+    for (int p = 0; p < P; ++p) {
+        double xp[5];
+        for (int d = 0; d < D; ++d) xp[d] = x[(size_t)d * P + p];
+        double s;
+        bad += orc_misfit_x(c, pm, xp, U, n, &s) != 0;
+        S[p] = isfinite(s) ? s : INFINITY;
+    }
+    return bad ? -1 : 0;
+}
+
+/* ======================================================================== */
+/* Particle swarm (Sec. 3.4, Eq. 8; reading R12).                           */
+/* Counter words: (particle, iteration, pixel, tag<<16 | block);            */
+/* tags 0 = initial x, 1 = initial v, 2 = r1/r2.                            */
+/* ======================================================================== */
+void orc_pso_init(int P, int D, uint64_t seed, uint32_t pixel, double* x, double* v)
+{
+    for (int p = 0; p < P; ++p)
+        for (int d = 0; d < D; ++d) {
+            double u0 = orc_draw(seed, (uint32_t)p, 0, pixel, 0, (uint32_t)(d / 4), d % 4);
+            double u1 = orc_draw(seed, (uint32_t)p, 0, pixel, 1, (uint32_t)(d / 4), d % 4);
+            x[(size_t)d * P + p] = u0;
+            v[(size_t)d * P + p] = (u1 - u0) / 2.0;
+        }
+}
+
+/* Eq. 8: v <- w v + c1 r1 (b_l - x) + c2 r2 (b_g - x); x <- x + v; a
+ * coordinate that leaves [0, 1] is put on the bound and its velocity zeroed.
+ * r1, r2 per particle and dimension: words 2d and 2d+1 of the tag-2 stream. */
+void orc_pso_update(int P, int D, uint32_t it, uint64_t seed, uint32_t pixel,
+                    double w, double c1, double c2, double* x, double* v,
+                    const double* pbest_x, const double* gbest_x)
+{
+    for (int p = 0; p < P; ++p)
+        for (int d = 0; d < D; ++d) {
+            size_t q = (size_t)d * P + p;
+            uint32_t blk = (uint32_t)((2 * d) / 4);
+            double r1 = orc_draw(seed, (uint32_t)p, it, pixel, 2, blk, (2 * d) % 4);
+            double r2 = orc_draw(seed, (uint32_t)p, it, pixel, 2, blk, (2 * d + 1) % 4);
+            double vn = w * v[q] + c1 * r1 * (pbest_x[q] - x[q]) + c2 * r2 * (gbest_x[d] - x[q]);
+            double xn = x[q] + vn;
+            if (xn < 0.0) { xn = 0.0; vn = 0.0; }
+            if (xn > 1.0) { xn = 1.0; vn = 0.0; }
+            x[q] = xn;
+            v[q] = vn;
+        }
+}
+
+static int argmin_first(const double* S, int P)
+{
+    int b = 0;
+    for (int p = 1; p < P; ++p)
+        if (S[p] < S[b]) b = p;
+    return b;
+}
+
+/* Synchronous PSO: evaluate all, update personal bests (strictly better),
+ * global best = lowest personal best (lowest index on ties), then move.
+ * iters counts position updates: P * (iters + 1) forward solves.
+ * hist (optional) receives the global-best misfit after each evaluation. */
+int orc_invert(const orc_case* c, const orc_pmap* pm, const double* U, int n,
+               const orc_pso* cfg, double* best_x, double* best_S, double* hist)
+{
+    int P = cfg->P, D = pm->D;
+    size_t sz = (size_t)P * D;
+    double* x = (double*)malloc(sizeof(double) * sz);
+    double* v = (double*)malloc(sizeof(double) * sz);
+    double* pb = (double*)malloc(sizeof(double) * sz);
+    double* S = (double*)malloc(sizeof(double) * P);
+    double* pbS = (double*)malloc(sizeof(double) * P);
+    double gb[5];
+    orc_pso_init(P, D, cfg->seed, cfg->pixel, x, v);
+    orc_misfit_batch(c, pm, x, P, U, n, S);
+    memcpy(pb, x, sizeof(double) * sz);
+    memcpy(pbS, S, sizeof(double) * P);
+    int g = argmin_first(pbS, P);
+    for (int d = 0; d < D; ++d) gb[d] = pb[(size_t)d * P + g];
+    if (hist) hist[0] = pbS[g];
+    for (int it = 1; it <= cfg->iters; ++it) {
+        orc_pso_update(P, D, (uint32_t)it, cfg->seed, cfg->pixel, cfg->w, cfg->c1, cfg->c2,
+                       x, v, pb, gb);
+        orc_misfit_batch(c, pm, x, P, U, n, S);
+        for (int p = 0; p < P; ++p)
+            if (S[p] < pbS[p]) {
+                pbS[p] = S[p];
+                for (int d = 0; d < D; ++d) pb[(size_t)d * P + p] = x[(size_t)d * P + p];
+            }
+        g = argmin_first(pbS, P);
+        for (int d = 0; d < D; ++d) gb[d] = pb[(size_t)d * P + g];
+        if (hist) hist[it] = pbS[g];
+    }
+    for (int d = 0; d < D; ++d) best_x[d] = gb[d];
+    *best_S = pbS[g];
+    free(x); free(v); free(pb); free(S); free(pbS);
+    return 0;
+}
+
+/* ======================================================================== */
+/* Synthetic records (reading R9-R11).                                       */
+/* ======================================================================== */
+
+/* Truth drawn from tag 3 in the interior [0.1, 0.9]^D of the cube. */
+void orc_truth_x(int D, uint64_t seed, uint32_t pixel, double* x)
+{
+    for (int d = 0; d < D; ++d)
+        x[d] = 0.1 + 0.8 * orc_draw(seed, 0, 0, pixel, 3, (uint32_t)(d / 4), d % 4);
+}
+
+/* Record length in drive cycles, uniform on the integers lo..hi: tag 3,
+ * block 2, word 0, scaled by integer multiply-high. */
+int orc_cycles(uint64_t seed, uint32_t pixel, int lo, int hi)
+{
+    uint32_t ctr[4] = {0, 0, pixel, (3u << 16) | 2u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    uint32_t span = (uint32_t)(hi - lo + 1);
+    return lo + (int)(((uint64_t)out[0] * span) >> 32);
+}
+
+/* Record: tip deflection of the truth integrated at dt/sub, sampled every
+ * `sub` fine steps, plus Gaussian noise of std sigma.  Noise sample n uses
+ * the tag-4 counter (n/2, 0, pixel, 4<<16) and Box-Muller on words 0, 1:
+ *   u1 = ((w0 >> 8) + 1) 2^-24 in (0, 1],  u2 = (w1 >> 8) 2^-24,
+ *   z = sqrt(-2 ln u1) * (cos 2 pi u2 for even n, sin 2 pi u2 for odd n). */
+int orc_record(const orc_case* c, const orc_pmap* pm, const double* x, int n,
+               int sub, double sigma, uint64_t seed, uint32_t pixel, double* U)
+{
+    double th[5];
+    orc_map(pm, x, th);
+    if (orc_forward(c, th, n, sub, U, NULL)) return -1;
+    if (sigma > 0.0) {
+        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+        for (int j = 0; j < n; ++j) {
+            uint32_t ctr[4] = {(uint32_t)(j / 2), 0, pixel, 4u << 16};
+            uint32_t out[4];
+            orc_philox4x32_10(ctr, key, out);
+            double u1 = ((double)(out[0] >> 8) + 1.0) * (1.0 / 16777216.0);
+            double u2 = (double)(out[1] >> 8) * (1.0 / 16777216.0);
+            double r = sqrt(-2.0 * log(u1));
+            double z = (j % 2 == 0) ? r * cos(2.0 * M_PI * u2) : r * sin(2.0 * M_PI * u2);
+            U[j] += sigma * z;
+        }
+    }
+    return 0;
+}
+
+/* ======================================================================== */
+/* Complex-step gradient of S(x) (the oracle side of the adjoint check).     */
+/* The whole forward solve is repeated in complex arithmetic with the        */
+/* perturbation i*h on one coordinate; branches are taken on real parts.     */
+/* ======================================================================== */
+static double complex cforce(int kind, const double complex th[5], double complex d,
+                             double complex ddot)
+{
+    switch (kind) {
+    case ORC_F_LINEAR:
+        return -th[0] * (d - th[1]);
+    case ORC_F_DMT:
+    case ORC_F_DMT_KV: {
+        double complex E = th[0], H = th[1], R = th[2], a0 = th[3];
+        if (creal(d) > creal(a0)) return -H * R / (6.0 * d * d);
+        double complex delta = a0 - d;
+        double complex F = (4.0 / 3.0) * E * csqrt(R) * delta * csqrt(delta)
+                           - H * R / (6.0 * a0 * a0);
+        if (kind == ORC_F_DMT_KV) F -= th[4] * csqrt(R * delta) * ddot;
+        return F;
+    }
+    case ORC_F_HOOKE:
+        return creal(d) < creal(th[1]) ? th[0] * (th[1] - d) : 0.0;
+    case ORC_F_SPRING_DAMPER:
+        return creal(d) < creal(th[1]) ? th[0] * (th[1] - d) - th[2] * ddot : 0.0;
+    default:
+        return 0.0;
+    }
+}
+
+static void cmap(const orc_pmap* pm, const double complex* x, double complex th[5])
+{
+    for (int s = 0; s < 5; ++s) th[s] = pm->fixed[s];
+    for (int d = 0; d < pm->D; ++d) {
+        double lo = pm->lo[d], hi = pm->hi[d];
+        if (pm->logs[d])
+            th[pm->slot[d]] = cexp(log(10.0) * (log10(lo) + x[d] * (log10(hi) - log10(lo))));
+        else
+            th[pm->slot[d]] = lo + x[d] * (hi - lo);
+    }
+}
+
+static double complex cmisfit(const orc_case* c, const orc_modal* md,
+                              const double complex th[5], const double* U, int n)
+{
+    int m = md->m, n2 = 2 * m;
+    double complex y[2 * ORC_MAXM], k[4][2 * ORC_MAXM], yt[2 * ORC_MAXM];
+    for (int i = 0; i < m; ++i) { y[i] = md->eta0[i]; y[m + i] = md->etad0[i]; }
+    double h = md->dt;
+    double complex S = 0.0;
+    for (int step = 0; step < n; ++step) {
+        double g[3] = {orc_drive_half(md, c->spc, 2L * step),
+                       orc_drive_half(md, c->spc, 2L * step + 1),
+                       orc_drive_half(md, c->spc, 2L * step + 2)};
+        const double cs[4] = {0.0, 0.5, 0.5, 1.0};
+        const int gi[4] = {0, 1, 1, 2};
+        for (int s = 0; s < 4; ++s) {
+            for (int q = 0; q < n2; ++q) yt[q] = s == 0 ? y[q] : y[q] + cs[s] * h * k[s - 1][q];
+            double complex u = 0.0, ud = 0.0;
+            for (int i = 0; i < m; ++i) { u += yt[i]; ud += yt[m + i]; }
+            double complex F = cforce(c->force, th, c->Zc + u, ud);
+            for (int i = 0; i < m; ++i) {
+                k[s][i] = yt[m + i];
+                k[s][m + i] = F / md->mass + md->gam[i] * g[gi[s]]
+                              - md->w[i] * md->w[i] * yt[i] - (md->w[i] / c->Q[i]) * yt[m + i];
+            }
+        }
+        for (int q = 0; q < n2; ++q)
+            y[q] = y[q] + (h / 6.0) * (k[0][q] + 2.0 * k[1][q] + 2.0 * k[2][q] + k[3][q]);
+        double complex tip = 0.0;
+        for (int i = 0; i < m; ++i) tip += y[i];
+        S += (U[step] - tip) * (U[step] - tip);
+    }
+    return S;
+}
+
+/* dS/dx_d = Im S(x + i h e_d) / h with h = 1e-30 (no subtractive error). */
+int orc_grad_cs(const orc_case* c, const orc_pmap* pm, const double* x,
+                const double* U, int n, double* S, double* grad)
+{
+    orc_modal md;
+    if (orc_setup(c, &md)) return -1;
+    const double h = 1e-30;
+    int D = pm->D;
+    double Sr = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+#endif
+    for (int d = 0; d < D; ++d) {
+        double complex xc[5], th[5];
+        for (int e = 0; e < D; ++e) xc[e] = x[e] + (e == d ? I * h : 0.0);
+        cmap(pm, xc, th);
+        double complex Sc = cmisfit(c, &md, th, U, n);
+        grad[d] = cimag(Sc) / h;
+        if (d == 0) Sr = creal(Sc);
+    }
+    *S = Sr;
+    return 0;
+}

@@ -1,0 +1,309 @@
+"""ctypes binding of the FP64 CPU oracle (``afm_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the
+CPU-baseline leg of the benchmark are the only callers.  The CUDA library
+never imports this module and shares no code with it.
+
+All quantities here are SI double precision.  Arrays of swarm coordinates
+are dimension-major ``[D][P]`` like the CUDA side's, but nothing else is
+shared.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAXM = 8
+POINT_MASS, MODAL_EB, FE_HERMITE = 0, 1, 2
+F_LINEAR, F_DMT, F_DMT_KV, F_HOOKE, F_SPRING_DAMPER = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no fast-math)."""
+    src = [os.path.join(_HERE, "afm_oracle.c")]
+    hdr = os.path.join(_HERE, "afm_oracle.h")
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in src + [hdr])
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall",
+           "-o", tmp] + src + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Case(C.Structure):
+    _fields_ = [("model", C.c_int), ("n_modes", C.c_int), ("f1", C.c_double),
+                ("k", C.c_double), ("Q", C.c_double * MAXM), ("A0", C.c_double),
+                ("Zc", C.c_double), ("spc", C.c_int), ("force", C.c_int),
+                ("n_elem", C.c_int), ("L", C.c_double), ("E", C.c_double),
+                ("rho", C.c_double), ("fe_k", C.c_double), ("fe_f1", C.c_double),
+                ("fe_Q", C.c_double), ("nm_beta", C.c_double)]
+
+
+class Modal(C.Structure):
+    _fields_ = [("m", C.c_int), ("w", C.c_double * MAXM), ("gam", C.c_double * MAXM),
+                ("mass", C.c_double), ("wd", C.c_double), ("a", C.c_double),
+                ("psi", C.c_double), ("eta0", C.c_double * MAXM),
+                ("etad0", C.c_double * MAXM), ("dt", C.c_double)]
+
+
+class Pmap(C.Structure):
+    _fields_ = [("D", C.c_int), ("slot", C.c_int * 5), ("lo", C.c_double * 5),
+                ("hi", C.c_double * 5), ("logs", C.c_int * 5), ("fixed", C.c_double * 5)]
+
+
+class Pso(C.Structure):
+    _fields_ = [("P", C.c_int), ("iters", C.c_int), ("w", C.c_double), ("c1", C.c_double),
+                ("c2", C.c_double), ("seed", C.c_uint64), ("pixel", C.c_uint32)]
+
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+            L.orc_uniform.argtypes = [C.c_uint32]
+            L.orc_uniform.restype = C.c_double
+            L.orc_draw.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                   C.c_uint32, C.c_uint32, C.c_int]
+            L.orc_draw.restype = C.c_double
+            L.orc_beam_root.argtypes = [C.c_int]
+            L.orc_beam_root.restype = C.c_double
+            L.orc_mode_shape.argtypes = [C.c_double, C.c_double]
+            L.orc_mode_shape.restype = C.c_double
+            L.orc_modal_factors.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp]
+            L.orc_setup.argtypes = [C.POINTER(Case), C.POINTER(Modal)]
+            L.orc_drive_half.argtypes = [C.POINTER(Modal), C.c_int, C.c_long]
+            L.orc_drive_half.restype = C.c_double
+            L.orc_force.argtypes = [C.c_int, _dp, C.c_double, C.c_double]
+            L.orc_force.restype = C.c_double
+            L.orc_forward.argtypes = [C.POINTER(Case), _dp, C.c_int, C.c_int, _dp, C.c_void_p]
+            L.orc_misfit.argtypes = [_dp, _dp, C.c_int]
+            L.orc_misfit.restype = C.c_double
+            L.orc_map.argtypes = [C.POINTER(Pmap), _dp, _dp]
+            L.orc_misfit_batch.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int,
+                                           _dp, C.c_int, _dp]
+            L.orc_pso_init.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32, _dp, _dp]
+            L.orc_pso_update.argtypes = [C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
+                                         C.c_double, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
+            L.orc_invert.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int,
+                                     C.POINTER(Pso), _dp, C.POINTER(C.c_double), _dp]
+            L.orc_truth_x.argtypes = [C.c_int, C.c_uint64, C.c_uint32, _dp]
+            L.orc_cycles.argtypes = [C.c_uint64, C.c_uint32, C.c_int, C.c_int]
+            L.orc_record.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int, C.c_int,
+                                     C.c_double, C.c_uint64, C.c_uint32, _dp]
+            L.orc_grad_cs.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, _dp, C.c_int,
+                                      C.POINTER(C.c_double), _dp]
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_get_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+# --------------------------------------------------------------------------
+# Builders from plain workload descriptions (dicts of SI values)
+# --------------------------------------------------------------------------
+_MODEL = {"point_mass": POINT_MASS, "modal_eb": MODAL_EB, "fe_hermite": FE_HERMITE}
+_FORCE = {"linear_spring": F_LINEAR, "dmt": F_DMT, "dmt_kv": F_DMT_KV, "hooke": F_HOOKE,
+          "spring_damper": F_SPRING_DAMPER}
+
+
+def make_case(spec: dict) -> Case:
+    c = Case()
+    c.model = _MODEL[spec["model"]]
+    c.n_modes = int(spec.get("n_modes", 1))
+    c.f1 = float(spec.get("f1_hz", 0.0))
+    c.k = float(spec.get("k", 0.0))
+    q = spec.get("Q", 400.0)
+    qs = list(q) if hasattr(q, "__len__") else [q] * MAXM
+    for i in range(MAXM):
+        c.Q[i] = float(qs[i] if i < len(qs) else qs[-1])
+    c.A0 = float(spec.get("A0", 0.0))
+    c.Zc = float(spec.get("Zc", 0.0))
+    c.spc = int(spec["spc"])
+    c.force = _FORCE[spec["force"]]
+    c.n_elem = int(spec.get("n_elem", 0))
+    c.L = float(spec.get("L", 0.0))
+    c.E = float(spec.get("E", 0.0))
+    c.rho = float(spec.get("rho", 0.0))
+    c.fe_k = float(spec.get("k", 0.0))
+    c.fe_f1 = float(spec.get("f1_hz", 0.0))
+    c.fe_Q = float(qs[0])
+    c.nm_beta = float(spec.get("newmark_beta", 0.25))
+    return c
+
+
+def make_pmap(spec: dict) -> Pmap:
+    """spec["free"]: list of (slot, lo, hi, log); spec["fixed"]: 5 slot values."""
+    pm = Pmap()
+    free = spec["free"]
+    pm.D = len(free)
+    for d, (slot, lo, hi, lg) in enumerate(free):
+        pm.slot[d] = int(slot)
+        pm.lo[d] = float(lo)
+        pm.hi[d] = float(hi)
+        pm.logs[d] = int(bool(lg))
+    for s in range(5):
+        pm.fixed[s] = float(spec["fixed"][s])
+    return pm
+
+
+# --------------------------------------------------------------------------
+# Thin wrappers
+# --------------------------------------------------------------------------
+def philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(c, k, out)
+    return out
+
+
+def beam_root(i: int) -> float:
+    return lib().orc_beam_root(int(i))
+
+
+def mode_shape(bL: float, xi: float) -> float:
+    return lib().orc_mode_shape(float(bL), float(xi))
+
+
+def modal_factors(n_modes: int, n_points: int = 501):
+    bL, gam, i2, tip = (np.zeros(n_modes) for _ in range(4))
+    rc = lib().orc_modal_factors(n_modes, n_points, bL, gam, i2, tip)
+    if rc:
+        raise ValueError("orc_modal_factors failed")
+    return bL, gam, i2, tip
+
+
+def setup(case: Case) -> Modal:
+    md = Modal()
+    if lib().orc_setup(C.byref(case), C.byref(md)):
+        raise ValueError("orc_setup failed")
+    return md
+
+
+def drive_half(md: Modal, spc: int, j: int) -> float:
+    return lib().orc_drive_half(C.byref(md), int(spc), int(j))
+
+
+def force(kind: int, th, d: float, ddot: float = 0.0) -> float:
+    return lib().orc_force(int(kind), np.ascontiguousarray(th, dtype=np.float64),
+                           float(d), float(ddot))
+
+
+def forward(case: Case, th, n_steps: int, sub: int = 1, want_state: bool = False):
+    th = np.ascontiguousarray(th, dtype=np.float64)
+    u = np.zeros(n_steps)
+    m = 1 if case.model == POINT_MASS else case.n_modes
+    st = np.zeros((n_steps + 1, 2 * m)) if want_state else None
+    rc = lib().orc_forward(C.byref(case), th, int(n_steps), int(sub), u,
+                           st.ctypes.data if want_state else None)
+    if rc:
+        raise ValueError("orc_forward failed")
+    return (u, st) if want_state else u
+
+
+def misfit(U, u) -> float:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().orc_misfit(U, u, len(U))
+
+
+def map_x(pm: Pmap, x) -> np.ndarray:
+    th = np.zeros(5)
+    lib().orc_map(C.byref(pm), np.ascontiguousarray(x, dtype=np.float64), th)
+    return th
+
+
+def misfit_batch(case: Case, pm: Pmap, x_dp, U) -> np.ndarray:
+    x = np.ascontiguousarray(x_dp, dtype=np.float64)
+    D, P = x.shape
+    assert D == pm.D
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    S = np.zeros(P)
+    lib().orc_misfit_batch(C.byref(case), C.byref(pm), x, P, U, len(U), S)
+    return S
+
+
+def pso_init(P: int, D: int, seed: int, pixel: int = 0):
+    x = np.zeros((D, P))
+    v = np.zeros((D, P))
+    lib().orc_pso_init(P, D, seed, pixel, x, v)
+    return x, v
+
+
+def pso_update(it: int, seed: int, pixel: int, w: float, c1: float, c2: float,
+               x, v, pbest_x, gbest_x):
+    x = np.array(x, dtype=np.float64, order="C")
+    v = np.array(v, dtype=np.float64, order="C")
+    D, P = x.shape
+    lib().orc_pso_update(P, D, it, seed, pixel, w, c1, c2, x, v,
+                         np.ascontiguousarray(pbest_x, dtype=np.float64),
+                         np.ascontiguousarray(gbest_x, dtype=np.float64))
+    return x, v
+
+
+def invert(case: Case, pm: Pmap, U, P: int, iters: int, w: float, c1: float, c2: float,
+           seed: int, pixel: int = 0):
+    cfg = Pso(P=P, iters=iters, w=w, c1=c1, c2=c2, seed=seed, pixel=pixel)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    bx = np.zeros(pm.D)
+    bS = C.c_double()
+    hist = np.zeros(iters + 1)
+    lib().orc_invert(C.byref(case), C.byref(pm), U, len(U), C.byref(cfg), bx, C.byref(bS), hist)
+    return bx, bS.value, hist
+
+
+def truth_x(D: int, seed: int, pixel: int = 0) -> np.ndarray:
+    x = np.zeros(D)
+    lib().orc_truth_x(D, seed, pixel, x)
+    return x
+
+
+def cycles(seed: int, pixel: int, lo: int, hi: int) -> int:
+    return int(lib().orc_cycles(seed, pixel, lo, hi))
+
+
+def record(case: Case, pm: Pmap, x, n: int, sub: int, sigma: float, seed: int,
+           pixel: int = 0) -> np.ndarray:
+    U = np.zeros(n)
+    rc = lib().orc_record(C.byref(case), C.byref(pm), np.ascontiguousarray(x, dtype=np.float64),
+                          n, sub, sigma, seed, pixel, U)
+    if rc:
+        raise ValueError("orc_record failed")
+    return U
+
+
+def grad_cs(case: Case, pm: Pmap, x, U):
+    g = np.zeros(pm.D)
+    S = C.c_double()
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    lib().orc_grad_cs(C.byref(case), C.byref(pm), np.ascontiguousarray(x, dtype=np.float64),
+                      U, len(U), C.byref(S), g)
+    return S.value, g

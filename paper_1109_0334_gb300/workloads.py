@@ -1,0 +1,82 @@
+"""Seeded synthetic workloads: the five cantilever / force / swarm
+configurations the library is exercised on, as plain SI values.
+
+This module holds inputs only (physical constants, bounds, swarm sizes,
+seeds, and a seeded sampler for swarm coordinates).  It contains none of the
+method's arithmetic, so both the CUDA path and the independent CPU oracle
+may read it.
+
+Parameter slots (theta[0..4]) of the DMT family: E* [Pa], H [J], R [m],
+a0 [m], eta [Pa s].  A free parameter is (slot, lo, hi, log_scale).
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+SEED_BASE = 1109033400
+
+_CANTILEVER = dict(f1_hz=300e3, k=40.0, Q=400.0, A0=20e-9, Zc=16e-9)
+_NOISE = 0.005 * 20e-9          # 0.5 % of A0
+_PSO = dict(w=0.7, c1=1.5, c2=1.5)
+
+_E = (0, 1e8, 1e10, True)       # E* in [0.1, 10] GPa, log
+_H = (1, 1e-20, 1e-19, True)    # Hamaker constant, log
+_R = (2, 5e-9, 30e-9, False)    # tip radius, linear
+_A0 = (3, 0.2e-9, 0.5e-9, False)  # intermolecular distance, linear
+_ETA = (4, 0.0, 500.0, False)   # contact viscosity, linear
+
+WORKLOADS = {
+    # Single-mode point mass, FP64 oracle scale: 20 cycles x 200 steps.
+    "c1": dict(name="point-mass DMT, 2 unknowns, 64 particles x 50 updates",
+               model="point_mass", n_modes=1, spc=200, cycles=20, force="dmt",
+               free=[_E, _H], fixed=[0.0, 0.0, 10e-9, 0.3e-9, 0.0],
+               P=64, iters=50, seed=SEED_BASE + 1, **_CANTILEVER, **_PSO),
+    # 3-mode Euler-Bernoulli modal cantilever: 100 cycles x 256 steps.
+    "c2": dict(name="3-mode EB DMT, 4 unknowns, 1024 particles x 100 updates",
+               model="modal_eb", n_modes=3, spc=256, cycles=100, force="dmt",
+               free=[_E, _H, _R, _A0], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
+               P=1024, iters=100, seed=SEED_BASE + 2, **_CANTILEVER, **_PSO),
+    # 4096 independent pixels, 20..200 cycles each, 256 particles x 60 updates.
+    "c3": dict(name="4096 pixels, 3-mode EB DMT, 256 particles x 60 updates",
+               model="modal_eb", n_modes=3, spc=256, cycles=(20, 200), force="dmt",
+               free=[_E, _H, _R, _A0], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
+               P=256, iters=60, n_pix=4096, seed=SEED_BASE + 3, **_CANTILEVER, **_PSO),
+    # DMT + Kelvin-Voigt contact damping, adjoint-polished.
+    "c4": dict(name="3-mode EB DMT+KV, 5 unknowns, 1024 x 40 + 20 polish on 32",
+               model="modal_eb", n_modes=3, spc=256, cycles=100, force="dmt_kv",
+               free=[_E, _H, _R, _A0, _ETA], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
+               P=1024, iters=40, polish_k=32, polish_steps=20, seed=SEED_BASE + 4,
+               **_CANTILEVER, **_PSO),
+    # 32-element Hermite FE beam, Newmark beta = 1/4.
+    "c5": dict(name="FE Hermite 32 elements DMT, 4 unknowns, 8192 particles x 60 updates",
+               model="fe_hermite", n_elem=32, L=125e-6, E=1.76e11, rho=2330.0,
+               newmark_beta=0.25, spc=512, cycles=50, force="dmt",
+               free=[_E, _H, _R, _A0], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
+               P=8192, iters=60, seed=SEED_BASE + 5, **_CANTILEVER, **_PSO),
+}
+for _w in WORKLOADS.values():
+    _w["sigma"] = _NOISE
+    _w["record_sub"] = 4
+
+
+def get(name: str, **overrides) -> dict:
+    """A copy of one workload with fields overridden (e.g. cycles, P, iters)."""
+    w = copy.deepcopy(WORKLOADS[name])
+    w.update(overrides)
+    return w
+
+
+def n_steps(w: dict) -> int:
+    cyc = w["cycles"]
+    if isinstance(cyc, (tuple, list)):
+        raise ValueError("per-pixel record lengths: use the pixel's own cycle count")
+    return int(cyc) * int(w["spc"])
+
+
+def sample_x(D: int, P: int, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """Seeded uniform swarm coordinates, shape [D][P], float32-exact."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(lo, hi, size=(D, P)).astype(np.float32)
+    return x
