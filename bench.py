@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark of the fused inversion hot path on GB300.
+
+One step = one full particle-swarm inversion of the 3-mode Euler-Bernoulli
+cantilever with the DMT law (1024 particles x (100 + 1) evaluations x 25 600
+RK4 steps, fused forward + misfit + swarm update, winner re-evaluated in
+FP64), on a synthetic record made on the GPU from a seeded truth.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank inverts its own
+pixel's record (independent problems: weak scaling, no data-path
+collective); the timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle·timesteps/s forward+misfit; ms per inversion at ≤0.5% param error"
+UNIT = "particle·timesteps/s"
+WORKLOAD = "c2"
+
+
+# ---------------------------------------------------------------------------
+# FP32 operation count of the fused kernel per particle and RK4 step
+# ---------------------------------------------------------------------------
+def fp32_ops_per_step(m: int, force: str) -> int:
+    """FP32 instructions (add/mul/fma/min/max) per particle per RK4 step of
+    the fused forward + misfit kernel, counted from its source:
+    accel(): tip sum (m-1), gap (1), force law, per mode 4 (+1 for mode 1's
+    low word); RK4 stage states and slope sums 12m; compensated update 8m;
+    tip deflection (m-1); compensated misfit 5."""
+    force_ops = {"dmt": 7, "dmt_kv": 9 + (m - 1), "linear_spring": 2, "hooke": 3,
+                 "spring_damper": 4 + (m - 1)}[force]
+    accel = (m - 1) + 1 + force_ops + 4 * m + 1
+    return 4 * accel + 12 * m + 8 * m + (m - 1) + 5
+
+
+# ---------------------------------------------------------------------------
+# nvidia-smi clock sampler (runs during the timed region)
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1109_0334_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (profiles/*.md lines 'traffic: <kernel>
+    <workload> <bytes> <source-hash>')."""
+    want = kernel_source_hash()
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(f):
+            parts = line.strip().split()
+            if len(parts) == 5 and parts[0] == "traffic:" and parts[1] == kernel \
+                    and parts[2] == workload and parts[4] == want:
+                return float(parts[3])
+    return None
+
+
+# ---------------------------------------------------------------------------
+# Distributed plumbing
+# ---------------------------------------------------------------------------
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        if torch.cuda.is_available():
+            torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def all_max(val: float, world: int) -> float:
+    if world == 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([val], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(spec, target_cpu_s: float = 12.0, max_evals: int = 50):
+    """Times whole-swarm evaluations (forward + misfit of every particle) of
+    the oracle until about target_cpu_s of CPU work.  Returns
+    (particle-steps/s, threads, description)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1109_0334_gb300 import workloads as W
+    O.build()
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    O.set_threads(threads)
+    c, pm = O.make_case(spec), O.make_pmap(spec)
+    n = W.n_steps(spec)
+    xt = O.truth_x(pm.D, spec["seed"])
+    U = O.record(c, pm, xt, n, spec["record_sub"], spec["sigma"], spec["seed"])
+    P = spec["P"]
+    x, _ = O.pso_init(P, pm.D, spec["seed"])
+    evals, t0 = 0, time.perf_counter()
+    while True:
+        O.misfit_batch(c, pm, x, U)
+        evals += 1
+        wall = time.perf_counter() - t0
+        if wall * threads >= target_cpu_s or evals >= max_evals:
+            break
+    rate = evals * P * n / wall
+    desc = (f"{evals} whole-swarm evaluations ({P} particles x {n} RK4 steps, FP64 oracle, "
+            f"OpenMP over particles) = {evals}/{spec['iters'] + 1} of one inversion; "
+            f"{wall:.2f} s wall")
+    return rate, threads, desc, wall / evals
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1109_0334_gb300 import build as B
+    B.build()
+    from paper_1109_0334_gb300 import afminv as A
+    from paper_1109_0334_gb300 import workloads as W
+
+    rank, world, local = dist_setup()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = W.get(args.workload)
+    N = W.n_steps(spec)
+    D = len(spec["free"])
+    P, iters = spec["P"], spec["iters"]
+    m = 1 if spec["model"] == "point_mass" else spec["n_modes"]
+    pixel = rank
+
+    # synthetic record of a seeded truth, made by the library (finer step + noise)
+    rng = np.random.default_rng(spec["seed"] + 1000 * pixel)
+    x_truth = rng.uniform(0.1, 0.9, size=(D, 1))
+    prob = A.make_problem(spec)
+    off = torch.tensor([0, N], dtype=torch.int64, device=dev)
+    U = A.synth_records(prob, torch.from_numpy(x_truth).to(dev), off, spec["record_sub"],
+                        spec["sigma"], spec["seed"], pixel)
+    torch.cuda.synchronize()
+    U_host = U.cpu().pin_memory()
+    cfg = A.make_pso(spec, pixel=pixel)
+    ws = torch.empty(A.invert_workspace_size(prob, cfg), dtype=torch.uint8, device=dev)
+    res = torch.zeros(A.result_dtype_size(), dtype=torch.uint8, device=dev)
+    hist = torch.empty(iters + 1, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        A.invert(prob, U, cfg, workspace=ws, result=res, history=hist)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    A.profile_enable(True)
+    A.profile_read()
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    kern_ms, kern_n = A.profile_read()
+    A.profile_enable(False)
+    T_ms = all_max(sum(step_ms), world)
+    r = A.decode_result(res)
+
+    units = P * (iters + 1) * N
+    value = world * units * args.steps / (T_ms / 1e3)
+
+    # end to end through the public API with host buffers
+    res_host = torch.empty_like(res, device="cpu").pin_memory()
+    hist_host = torch.empty_like(hist, device="cpu").pin_memory()
+    U_dev = torch.empty_like(U)
+    e2e_ms = []
+    barrier(world)
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        U_dev.copy_(U_host, non_blocking=True)
+        A.invert(prob, U_dev, cfg, workspace=ws, result=res, history=hist)
+        res_host.copy_(res, non_blocking=True)
+        hist_host.copy_(hist, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    E_ms = all_max(sum(e2e_ms), world)
+    e2e = {"value": world * units * args.steps / (E_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(U.numel() * 4),
+           "d2h_bytes_per_step": int(res.numel() + hist.numel() * 4),
+           "ms_per_inversion": E_ms / args.steps}
+
+    # roofline of the dominant kernel (fused iteration kernel)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * 128 * sm_max * 1e6
+    ops_launch = P * N * fp32_ops_per_step(m, spec["force"])
+    avg_launch_s = (kern_ms / max(kern_n, 1)) / 1e3
+    achieved = ops_launch / avg_launch_s
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+            "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
+            "traffic": ncu_traffic("invert_iter_kernel", args.workload),
+            "kernel": "invert_iter_kernel<3,DMT>",
+            "ops_per_particle_step": fp32_ops_per_step(m, spec["force"]),
+            "launches_timed": kern_n, "avg_launch_ms": avg_launch_s * 1e3,
+            "kernel_share_of_step": kern_ms / sum(step_ms),
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz"
+                          + (" (sm_max_mhz of measured)" if peaks else " (nominal max clock)")}
+
+    # throughput regime: one wide forward + misfit launch (262 144 particles)
+    batched = None
+    if not args.no_batched:
+        Pb = 256 * 1024
+        xb = torch.rand((D, Pb), dtype=torch.float32, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+        A.forward_batch(prob, xb, U, want_defl=False)
+        torch.cuda.synchronize()
+        A.profile_enable(True)
+        A.profile_read()
+        for _ in range(2):
+            flush.zero_()
+            A.forward_batch(prob, xb, U, want_defl=False)
+        ms_b, n_b = A.profile_read()
+        A.profile_enable(False)
+        ops_b = Pb * N * fp32_ops_per_step(m, spec["force"])
+        ach_b = ops_b / ((ms_b / n_b) / 1e3)
+        batched = {"particles": Pb, "steps": N, "ms_per_launch": ms_b / n_b,
+                   "value": Pb * N / ((ms_b / n_b) / 1e3), "unit": UNIT,
+                   "roofline": {"bound": "alu", "achieved": ach_b / 1e12, "peak": peak_ops / 1e12,
+                                "unit": "T FP32 lane-ops/s", "frac": ach_b / peak_ops,
+                                "traffic": ncu_traffic("fwd_kernel", "c2_batched")}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, threads, desc, _ = oracle_sample(spec)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        theta = r["theta"]
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded truth, GPU-made record at dt/4 + 0.5% A0 noise)",
+            "config": {"workload": "c2: 3-mode Euler-Bernoulli cantilever, DMT 4 unknowns, "
+                                   "1024 particles x 100 updates, 100 cycles x 256 steps",
+                       "particles": P, "updates": iters, "record_steps": N, "modes": m,
+                       "force": spec["force"], "per_rank": "one pixel inversion per step",
+                       "l2": "flushed between steps (256 MiB write)"},
+            "ms_per_inversion": T_ms / args.steps / 1.0,
+            "gpu_launches": (iters + 3) * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "result": {"S_nm2": r["S"], "S_f64_nm2": r["S_f64"], "J_rel": r["J_rel"],
+                       "x": list(r["x"][:D]), "x_truth": list(x_truth[:, 0]),
+                       "status": r["status"], "theta": list(theta)},
+            "batched_forward": batched,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1109_0334_gb300 import workloads as W
+    spec = W.get(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(spec, target_cpu_s=0.0, max_evals=1)
+    rates, walls, desc, threads = [], [], "", 1
+    for _ in range(args.steps):
+        rate, threads, desc, wall = oracle_sample(spec, target_cpu_s=0.0, max_evals=1)
+        rates.append(rate)
+        walls.append(wall)
+    n = W.n_steps(spec)
+    units = spec["P"] * n
+    T = sum(walls)
+    value = units * args.steps / T
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "c2 (one whole-swarm evaluation per step)",
+                      "particles": spec["P"], "record_steps": n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": f"per step: {desc}"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-batched", action="store_true", help="skip the wide forward launch")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

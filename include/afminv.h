@@ -1,0 +1,220 @@
+/*
+ * afminv.h -- C ABI of libafminv: GPU (sm_103a) tip-sample force inversion for
+ * dynamic AFM, after Busch, Zou & Ganapathysubramanian, "A near real-time
+ * framework for extracting tip-sample forces in dynamic atomic force
+ * microscopy" (arXiv 1109.0334).
+ *
+ * Problem statement (Sec. 2.2 "FP", Sec. 2.3 "IP"):
+ *   FP  given the cantilever, its base motion and a parametrised tip-sample
+ *       force, compute the tip deflection u(t) (modal reduction Eq. 2 of the
+ *       Euler-Bernoulli beam Eq. 1, RK4 of Sec. 3.2);
+ *   IP  given the cantilever, the base motion and a measured deflection U(t),
+ *       find the force parameters F* minimising J^2 = int (U - u)^2 dt (Eq. 5),
+ *       by particle-swarm optimisation (Sec. 3.4, Eq. 8).
+ *
+ * Conventions
+ *   - Every call returns afm_status and never aborts.  On failure,
+ *     afm_last_error() holds a message for the calling thread.
+ *   - Argument errors are reported as AFM_ERR_INVALID_ARG before any work is
+ *     queued.  CUDA errors are AFM_ERR_CUDA.
+ *   - Host structs are in SI units, double precision.
+ *   - Device arrays are owned by the caller; the library never allocates,
+ *     frees or retains them beyond the call's queued work.  "device" below
+ *     means a pointer usable by kernels on the context's GPU.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous with respect to the host unless their
+ *     name ends in _sync; results land in device memory in stream order.
+ *   - Swarm coordinates x live in the normalised cube [0,1]^D and are stored
+ *     dimension-major: x[d * P + p].
+ *   - Time-major deflection arrays: defl[n * P + p] is particle p's tip
+ *     deflection [nm] after step n + 1 (n = 0 .. n_steps-1).
+ *   - Records U[n] [nm] are samples at the ends of steps 1 .. n_steps.
+ *   - Misfits S are sum_n (U_n - u_n)^2 in nm^2 (Eq. 5 times 1/dt).
+ */
+#ifndef AFMINV_H
+#define AFMINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AFM_MAX_MODES 8
+#define AFM_MAX_PARAMS 5
+#define AFM_MAX_SPC 2048
+
+typedef enum {
+    AFM_OK = 0,
+    AFM_ERR_INVALID_ARG = 1,
+    AFM_ERR_CUDA = 2,
+    AFM_ERR_NONFINITE = 3,   /* a state or misfit became NaN/Inf (flagged, run completed) */
+    AFM_ERR_TIMEOUT = 4,
+    AFM_ERR_UNSUPPORTED = 5
+} afm_status;
+
+/* Cantilever models.  POINT_MASS: one mode, participation 1.  MODAL_EB:
+ * n_modes clamped-free Euler-Bernoulli modes, tip-normalised (Eq. 2, App. B;
+ * mode shapes of Eqs. 6-7).  FE_HERMITE: cubic Hermite beam elements. */
+typedef enum { AFM_POINT_MASS = 0, AFM_MODAL_EB = 1, AFM_FE_HERMITE = 2 } afm_model;
+
+/* Tip-sample laws.  d = gap = Zc + u (u = tip deflection, positive away from
+ * the sample); F > 0 pushes the tip away from the sample.  Parameter slots:
+ *   AFM_LINEAR_SPRING  (k_s [N/m], d_s [m])         F = -k_s (d - d_s)
+ *   AFM_DMT            (E* [Pa], H [J], R [m], a0 [m])
+ *                      F = -H R / (6 d^2)                              d > a0
+ *                      F = 4/3 E* sqrt(R) (a0 - d)^1.5 - H R/(6 a0^2)  d <= a0
+ *   AFM_DMT_KV         DMT slots + eta [Pa s]: adds -eta sqrt(R (a0-d)) d'
+ *                      in contact
+ *   AFM_HOOKE          (k [N/m], h [m])            F = k (h - d) for d < h (Eq. 3)
+ *   AFM_SPRING_DAMPER  (k, h, zeta_s [N s/m])      F = k (h - d) - zeta_s d'
+ *                                                  for d < h (Eq. 4)            */
+typedef enum {
+    AFM_LINEAR_SPRING = 0,
+    AFM_DMT = 1,
+    AFM_DMT_KV = 2,
+    AFM_HOOKE = 3,
+    AFM_SPRING_DAMPER = 4
+} afm_force;
+
+/* Problem descriptor (host, SI). */
+typedef struct {
+    int model;                  /* afm_model                                       */
+    int n_modes;                /* MODAL_EB: 1..AFM_MAX_MODES                      */
+    double f1_hz;               /* first natural frequency; the base is driven here */
+    double k_N_per_m;           /* mode-1 modal stiffness (FE: static 3EI/L^3)     */
+    double Q[AFM_MAX_MODES];    /* quality factor per mode (FE: Q[0] for modes 1,2) */
+    /* FE_HERMITE only */
+    int n_elem;
+    double L_m, E_Pa, rho_kg_m3, newmark_beta;
+    /* drive and set-point */
+    double A0_m;                /* free tip amplitude                              */
+    double Zc_m;                /* rest gap                                        */
+    int steps_per_cycle;        /* 4 .. AFM_MAX_SPC                                */
+    int n_steps;                /* record length in steps                          */
+    /* force law and its parameters */
+    int force;                  /* afm_force                                       */
+    double fixed[AFM_MAX_PARAMS];   /* values of all slots (free ones ignored)     */
+    int n_free;                 /* D: number of free (optimised) parameters        */
+    int slot[AFM_MAX_PARAMS];   /* slot of free dimension d                        */
+    double lo[AFM_MAX_PARAMS];  /* bounds of free dimension d (SI)                 */
+    double hi[AFM_MAX_PARAMS];
+    int log_scale[AFM_MAX_PARAMS];  /* 1: log10-uniform map, 0: linear             */
+} afm_problem;
+
+/* Particle-swarm settings (Sec. 3.4, Eq. 8). */
+typedef struct {
+    int P;                      /* particles                                       */
+    int iters;                  /* position updates (P * (iters+1) forward solves) */
+    double w, c1, c2;           /* inertia and acceleration weights                */
+    uint64_t seed;              /* Philox4x32-10 key                               */
+    uint32_t pixel;             /* counter word 2 (independent pixel streams)      */
+} afm_pso_cfg;
+
+/* Device-resident swarm state (caller-owned, see afm_pso_step). */
+typedef struct {
+    int P, D;
+    float* x;                   /* [D][P]                                          */
+    float* v;                   /* [D][P]                                          */
+    float* pbest_x;             /* [D][P]                                          */
+    float* pbest_S;             /* [P]                                             */
+    unsigned long long* gbest;  /* 1 word: (float bits of S) << 32 | particle      */
+} afm_swarm;
+
+/* Result of one inversion (written to device memory by afm_invert). */
+typedef struct {
+    double x[AFM_MAX_PARAMS];       /* normalised winner                          */
+    double theta[AFM_MAX_PARAMS];   /* all parameter slots, SI                    */
+    double S;                       /* FP32 misfit of the winner [nm^2]           */
+    double S_f64;                   /* FP64 re-evaluation of the winner [nm^2]    */
+    double J_rel;                   /* sqrt(S_f64 / sum U^2)                      */
+    int32_t iters;                  /* updates performed                          */
+    int32_t winner;                 /* particle index of the winner               */
+    int32_t nonfinite;              /* count of non-finite misfits seen           */
+    int32_t status;                 /* afm_status of the device-side run          */
+} afm_result;
+
+typedef struct afm_ctx afm_ctx;
+
+/* ---- context ----------------------------------------------------------- */
+/* Binds a CUDA device (queries its SM count).  Owns no device memory. */
+afm_status afm_ctx_create(int device, afm_ctx** out);
+afm_status afm_ctx_destroy(afm_ctx* ctx);
+/* Message of the last failed call on this thread ("" if none). */
+const char* afm_last_error(void);
+const char* afm_status_string(int status);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int afm_version(void);
+
+/* Kernel timing (tracing aid).  While enabled, the FP32 forward kernel of
+ * afm_forward_batch and each fused iteration kernel of afm_invert are
+ * bracketed by CUDA events on the call's stream.  afm_profile_read waits for
+ * the recorded events and returns the summed device time [ms] and the number
+ * of timed launches since the previous read. */
+afm_status afm_profile_enable(afm_ctx* ctx, int on);
+afm_status afm_profile_read(afm_ctx* ctx, double* ms, int* launches);
+
+/* ---- forward problem FP (Sec. 2.2; Eq. 2; RK4 of Sec. 3.2) --------------
+ * P candidate parameter sets x [D][P] (device, normalised) are integrated for
+ * prob->n_steps steps in FP32.  Outputs (each optional, NULL to skip):
+ *   defl [n_steps][P]  tip deflection after every step (device)
+ *   S    [P]           misfit against U (device; requires U [n_steps])
+ * A misfit that is not finite (a diverging candidate) is stored as +inf. */
+afm_status afm_forward_batch(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
+                             float* defl, const float* U, float* S, void* stream);
+/* The same in FP64 throughout (x, defl, U, S all double). */
+afm_status afm_forward_batch_f64(afm_ctx* ctx, const afm_problem* prob, const double* x,
+                                 int P, double* defl, const double* U, double* S,
+                                 void* stream);
+
+/* ---- cost functional (Eq. 5) -------------------------------------------
+ * S[p] = sum_{n < N} (U[n] - defl[n * P + p])^2, compensated summation.
+ * defl [N][P], U [N], S [P]: device. */
+afm_status afm_misfit(afm_ctx* ctx, const float* defl, const float* U, int N, int P, float* S,
+                      void* stream);
+
+/* ---- particle swarm (Sec. 3.4, Eq. 8) ----------------------------------
+ * afm_pso_init: x ~ U[0,1), v = (U[0,1) - x)/2 from the Philox stream
+ *   (counter (particle, 0, pixel, tag<<16 | d/4), tags 0 and 1), pbest_S =
+ *   +inf, gbest = all ones.
+ * afm_pso_step: given the misfits S_new [P] (device) of the current x,
+ *   (1) personal bests: pbest <- x where S_new < pbest_S (strictly);
+ *   (2) global best = lowest pbest_S, lowest particle index on ties;
+ *   (3) v <- w v + c1 r1 (pbest - x) + c2 r2 (gbest - x), x <- x + v, a
+ *       coordinate leaving [0,1] is clamped and its velocity zeroed; r1, r2
+ *       per particle and dimension from counter (particle, iter, pixel,
+ *       2<<16 | d/2), words 2d mod 4 and 2d+1 mod 4.
+ *   iter = 0 performs (1)-(2) only (the initial evaluation). */
+afm_status afm_pso_init(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw, void* stream);
+afm_status afm_pso_step(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw,
+                        const float* S_new, uint32_t iter, void* stream);
+
+/* ---- inverse problem IP (Sec. 2.3) --------------------------------------
+ * One fused inversion: initial swarm, (iters + 1) fused evaluations (PSO
+ * move + RK4 forward + misfit + personal/global best), then the winner is
+ * re-evaluated in FP64 on the GPU.  U [n_steps] (device).  The caller
+ * provides `workspace` (device, >= afm_invert_workspace_size bytes, 256-byte
+ * aligned) and `result` (device afm_result).  The winner's misfit history
+ * (iters + 1 floats) is written to `history` if non-NULL (device). */
+afm_status afm_invert_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
+                                     size_t* bytes);
+afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
+                      const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
+                      afm_result* result, float* history, void* stream);
+
+/* ---- synthetic records (Sec. 4.1: data made by a different integration) --
+ * For each of n_pix pixels, the truth x* (normalised, [D][n_pix] device
+ * double) is integrated in FP64 at 1/sub of the solver step and sampled
+ * every `sub` fine steps; then Gaussian noise of std sigma_m is added
+ * (Box-Muller on Philox counter (n/2, 0, pixel0 + i, 4<<16), words 0/1).
+ * Records are concatenated: pixel i has n_i = off[i+1] - off[i] samples at
+ * U_cat[off[i] ..] (device; off is a device int64 array [n_pix + 1]). */
+afm_status afm_synth_records(afm_ctx* ctx, const afm_problem* prob, const double* x_truth,
+                             int n_pix, const int64_t* off, int sub, double sigma_m,
+                             uint64_t seed, uint32_t pixel0, float* U_cat, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFMINV_H */

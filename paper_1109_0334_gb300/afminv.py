@@ -1,0 +1,314 @@
+"""Python binding of libafminv (ctypes).  Argument marshalling only: every
+step of the computation runs in the library's CUDA kernels.  PyTorch supplies
+device memory and streams.
+
+The names follow the C ABI in ``include/afminv.h``:
+``forward_batch``, ``forward_batch_f64``, ``misfit``, ``pso_init``,
+``pso_step``, ``invert``, ``synth_records``.
+
+If the shared library is missing this module raises on first use; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libafminv.so")
+
+MAX_MODES, MAX_PARAMS = 8, 5
+POINT_MASS, MODAL_EB, FE_HERMITE = 0, 1, 2
+LINEAR_SPRING, DMT, DMT_KV, HOOKE, SPRING_DAMPER = 0, 1, 2, 3, 4
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
+
+_MODEL = {"point_mass": POINT_MASS, "modal_eb": MODAL_EB, "fe_hermite": FE_HERMITE}
+_FORCE = {"linear_spring": LINEAR_SPRING, "dmt": DMT, "dmt_kv": DMT_KV, "hooke": HOOKE,
+          "spring_damper": SPRING_DAMPER}
+
+
+class Problem(C.Structure):
+    _fields_ = [("model", C.c_int), ("n_modes", C.c_int), ("f1_hz", C.c_double),
+                ("k_N_per_m", C.c_double), ("Q", C.c_double * MAX_MODES),
+                ("n_elem", C.c_int), ("L_m", C.c_double), ("E_Pa", C.c_double),
+                ("rho_kg_m3", C.c_double), ("newmark_beta", C.c_double),
+                ("A0_m", C.c_double), ("Zc_m", C.c_double), ("steps_per_cycle", C.c_int),
+                ("n_steps", C.c_int), ("force", C.c_int), ("fixed", C.c_double * MAX_PARAMS),
+                ("n_free", C.c_int), ("slot", C.c_int * MAX_PARAMS),
+                ("lo", C.c_double * MAX_PARAMS), ("hi", C.c_double * MAX_PARAMS),
+                ("log_scale", C.c_int * MAX_PARAMS)]
+
+
+class PsoCfg(C.Structure):
+    _fields_ = [("P", C.c_int), ("iters", C.c_int), ("w", C.c_double), ("c1", C.c_double),
+                ("c2", C.c_double), ("seed", C.c_uint64), ("pixel", C.c_uint32)]
+
+
+class Swarm(C.Structure):
+    _fields_ = [("P", C.c_int), ("D", C.c_int), ("x", C.c_void_p), ("v", C.c_void_p),
+                ("pbest_x", C.c_void_p), ("pbest_S", C.c_void_p), ("gbest", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("x", C.c_double * MAX_PARAMS), ("theta", C.c_double * MAX_PARAMS),
+                ("S", C.c_double), ("S_f64", C.c_double), ("J_rel", C.c_double),
+                ("iters", C.c_int32), ("winner", C.c_int32), ("nonfinite", C.c_int32),
+                ("status", C.c_int32)]
+
+
+class AfmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+_ctx = {}
+
+
+def lib():
+    """Load libafminv.so (built by ``paper_1109_0334_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libafminv is not built ({LIB_PATH} missing); run "
+                                   "paper_1109_0334_gb300.build.build() first")
+            L = C.CDLL(LIB_PATH)
+            vp, i, u32, u64, d = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_double
+            L.afm_ctx_create.argtypes = [i, C.POINTER(vp)]
+            L.afm_ctx_destroy.argtypes = [vp]
+            L.afm_last_error.restype = C.c_char_p
+            L.afm_status_string.restype = C.c_char_p
+            L.afm_status_string.argtypes = [i]
+            L.afm_profile_enable.argtypes = [vp, i]
+            L.afm_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+            L.afm_forward_batch.argtypes = [vp, C.POINTER(Problem), vp, i, vp, vp, vp, vp]
+            L.afm_forward_batch_f64.argtypes = [vp, C.POINTER(Problem), vp, i, vp, vp, vp, vp]
+            L.afm_misfit.argtypes = [vp, vp, vp, i, i, vp, vp]
+            L.afm_pso_init.argtypes = [vp, C.POINTER(PsoCfg), C.POINTER(Swarm), vp]
+            L.afm_pso_step.argtypes = [vp, C.POINTER(PsoCfg), C.POINTER(Swarm), vp, u32, vp]
+            L.afm_invert_workspace_size.argtypes = [C.POINTER(Problem), C.POINTER(PsoCfg),
+                                                    C.POINTER(C.c_size_t)]
+            L.afm_invert.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), vp,
+                                     C.c_size_t, vp, vp, vp]
+            L.afm_synth_records.argtypes = [vp, C.POINTER(Problem), vp, i, vp, i, d, u64, u32,
+                                            vp, vp]
+            _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != OK:
+        raise AfmError(st, lib().afm_last_error().decode())
+
+
+def context(device: int | None = None):
+    import torch
+    dev = torch.cuda.current_device() if device is None else int(device)
+    with _lock:
+        c = _ctx.get(dev)
+    if c is None:
+        h = C.c_void_p()
+        _check(lib().afm_ctx_create(dev, C.byref(h)))
+        with _lock:
+            _ctx[dev] = h
+        c = h
+    return c
+
+
+def profile_enable(on: bool = True, device=None) -> None:
+    """Bracket the hot kernels with CUDA events (see afm_profile_enable)."""
+    _check(lib().afm_profile_enable(context(device), int(bool(on))))
+
+
+def profile_read(device=None):
+    """(summed device ms, launches) of the timed kernels since the last read."""
+    ms, n = C.c_double(), C.c_int()
+    _check(lib().afm_profile_read(context(device), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# --------------------------------------------------------------------------
+# Problem / swarm descriptors from workload dicts (SI)
+# --------------------------------------------------------------------------
+def make_problem(spec: dict, n_steps: int | None = None) -> Problem:
+    p = Problem()
+    p.model = _MODEL[spec["model"]]
+    p.n_modes = int(spec.get("n_modes", 1))
+    p.f1_hz = float(spec["f1_hz"])
+    p.k_N_per_m = float(spec["k"])
+    q = spec.get("Q", 400.0)
+    qs = list(q) if hasattr(q, "__len__") else [q] * MAX_MODES
+    for k in range(MAX_MODES):
+        p.Q[k] = float(qs[k] if k < len(qs) else qs[-1])
+    p.n_elem = int(spec.get("n_elem", 0))
+    p.L_m = float(spec.get("L", 0.0))
+    p.E_Pa = float(spec.get("E", 0.0))
+    p.rho_kg_m3 = float(spec.get("rho", 0.0))
+    p.newmark_beta = float(spec.get("newmark_beta", 0.25))
+    p.A0_m = float(spec["A0"])
+    p.Zc_m = float(spec["Zc"])
+    p.steps_per_cycle = int(spec["spc"])
+    if n_steps is None:
+        n_steps = int(spec["cycles"]) * int(spec["spc"])
+    p.n_steps = int(n_steps)
+    p.force = _FORCE[spec["force"]]
+    for s in range(MAX_PARAMS):
+        p.fixed[s] = float(spec["fixed"][s])
+    free = spec["free"]
+    p.n_free = len(free)
+    for dd, (slot, lo, hi, lg) in enumerate(free):
+        p.slot[dd] = int(slot)
+        p.lo[dd] = float(lo)
+        p.hi[dd] = float(hi)
+        p.log_scale[dd] = int(bool(lg))
+    return p
+
+
+def make_pso(spec: dict, pixel: int = 0) -> PsoCfg:
+    return PsoCfg(P=int(spec["P"]), iters=int(spec["iters"]), w=float(spec["w"]),
+                  c1=float(spec["c1"]), c2=float(spec["c2"]), seed=int(spec["seed"]),
+                  pixel=int(pixel))
+
+
+# --------------------------------------------------------------------------
+# Entry points
+# --------------------------------------------------------------------------
+def forward_batch(prob: Problem, x, U=None, want_defl: bool = True, want_S: bool = True,
+                  stream=None):
+    """FP for P candidates.  x: float32 CUDA tensor [D, P].  Returns (defl, S):
+    defl [n_steps, P] or None, S [P] or None (needs U [n_steps])."""
+    import torch
+    P = int(x.shape[1]) if x.dim() == 2 else int(x.shape[0])
+    dev = x.device
+    defl = torch.empty((prob.n_steps, P), dtype=torch.float32, device=dev) if want_defl else None
+    S = torch.empty(P, dtype=torch.float32, device=dev) if (want_S and U is not None) else None
+    _check(lib().afm_forward_batch(context(dev.index), C.byref(prob), _ptr(x), P, _ptr(defl),
+                                   _ptr(U), _ptr(S), _stream(stream)))
+    return defl, S
+
+
+def forward_batch_f64(prob: Problem, x, U=None, want_defl: bool = True, want_S: bool = True,
+                      stream=None):
+    import torch
+    P = int(x.shape[1]) if x.dim() == 2 else int(x.shape[0])
+    dev = x.device
+    defl = torch.empty((prob.n_steps, P), dtype=torch.float64, device=dev) if want_defl else None
+    S = torch.empty(P, dtype=torch.float64, device=dev) if (want_S and U is not None) else None
+    _check(lib().afm_forward_batch_f64(context(dev.index), C.byref(prob), _ptr(x), P, _ptr(defl),
+                                       _ptr(U), _ptr(S), _stream(stream)))
+    return defl, S
+
+
+def misfit(defl, U, stream=None):
+    import torch
+    N, P = int(defl.shape[0]), int(defl.shape[1])
+    S = torch.empty(P, dtype=torch.float32, device=defl.device)
+    _check(lib().afm_misfit(context(defl.device.index), _ptr(defl), _ptr(U), N, P, _ptr(S),
+                            _stream(stream)))
+    return S
+
+
+@dataclass
+class SwarmState:
+    x: object
+    v: object
+    pbest_x: object
+    pbest_S: object
+    gbest: object
+
+    def c_struct(self) -> Swarm:
+        D, P = self.x.shape
+        return Swarm(P=P, D=D, x=self.x.data_ptr(), v=self.v.data_ptr(),
+                     pbest_x=self.pbest_x.data_ptr(), pbest_S=self.pbest_S.data_ptr(),
+                     gbest=self.gbest.data_ptr())
+
+
+def pso_init(cfg: PsoCfg, D: int, device=None, stream=None) -> SwarmState:
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    P = cfg.P
+    sw = SwarmState(x=torch.empty((D, P), dtype=torch.float32, device=dev),
+                    v=torch.empty((D, P), dtype=torch.float32, device=dev),
+                    pbest_x=torch.empty((D, P), dtype=torch.float32, device=dev),
+                    pbest_S=torch.empty(P, dtype=torch.float32, device=dev),
+                    gbest=torch.empty(1, dtype=torch.int64, device=dev))
+    cs = sw.c_struct()
+    _check(lib().afm_pso_init(context(dev.index), C.byref(cfg), C.byref(cs), _stream(stream)))
+    return sw
+
+
+def pso_step(cfg: PsoCfg, sw: SwarmState, S_new, it: int, stream=None) -> None:
+    cs = sw.c_struct()
+    _check(lib().afm_pso_step(context(sw.x.device.index), C.byref(cfg), C.byref(cs),
+                              _ptr(S_new), int(it), _stream(stream)))
+
+
+def invert_workspace_size(prob: Problem, cfg: PsoCfg) -> int:
+    n = C.c_size_t()
+    _check(lib().afm_invert_workspace_size(C.byref(prob), C.byref(cfg), C.byref(n)))
+    return int(n.value)
+
+
+def result_dtype_size() -> int:
+    return C.sizeof(Result)
+
+
+def invert(prob: Problem, U, cfg: PsoCfg, workspace=None, result=None, history=None,
+           stream=None):
+    """IP: one fused inversion on the GPU.  U: float32 CUDA tensor [n_steps].
+    Returns (result_tensor_uint8, history) left on the device; decode the
+    result with ``decode_result``."""
+    import torch
+    dev = U.device
+    nbytes = invert_workspace_size(prob, cfg)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    if result is None:
+        result = torch.zeros(C.sizeof(Result), dtype=torch.uint8, device=dev)
+    if history is None:
+        history = torch.empty(cfg.iters + 1, dtype=torch.float32, device=dev)
+    _check(lib().afm_invert(context(dev.index), C.byref(prob), _ptr(U), C.byref(cfg),
+                            _ptr(workspace), C.c_size_t(workspace.numel()), _ptr(result),
+                            _ptr(history), _stream(stream)))
+    return result, history
+
+
+def decode_result(result_bytes) -> dict:
+    """Host copy of an afm_result (uint8 tensor or bytes) as a dict."""
+    raw = bytes(result_bytes.cpu().numpy().tobytes()) if hasattr(result_bytes, "cpu") else bytes(result_bytes)
+    r = Result.from_buffer_copy(raw[:C.sizeof(Result)])
+    return dict(x=np.array(r.x[:]), theta=np.array(r.theta[:]), S=r.S, S_f64=r.S_f64,
+                J_rel=r.J_rel, iters=r.iters, winner=r.winner, nonfinite=r.nonfinite,
+                status=r.status)
+
+
+def synth_records(prob: Problem, x_truth, off, sub: int, sigma_m: float, seed: int,
+                  pixel0: int = 0, stream=None):
+    """Synthetic records (FP32 at dt/sub, sampled every sub steps, plus
+    Philox/Box-Muller noise).  x_truth: float64 CUDA [D, n_pix]; off: int64
+    CUDA [n_pix + 1].  Returns U_cat float32 [off[-1]]."""
+    import torch
+    n_pix = int(off.shape[0]) - 1
+    total = int(off[-1].item())
+    U = torch.empty(total, dtype=torch.float32, device=off.device)
+    _check(lib().afm_synth_records(context(off.device.index), C.byref(prob), _ptr(x_truth),
+                                   n_pix, _ptr(off), int(sub), float(sigma_m), int(seed),
+                                   int(pixel0), _ptr(U), _stream(stream)))
+    return U

@@ -1,0 +1,275 @@
+// afm_device.cuh -- device building blocks of libafminv: the Philox stream,
+// the tip-sample force laws, the parameter map and one classic RK4 step of
+// the modal cantilever (Eq. 2 integrated as in Sec. 3.2), in scaled units
+// (see afm_internal.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "afm_internal.h"
+
+namespace afm {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds; each round
+// multiplies counter words 0 and 2 by the two round multipliers, and the key
+// advances by the two Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t a = 0xD2511F53u, b = 0xCD9E8D57u;
+        uint32_t lo_a = a * c.x, hi_a = __umulhi(a, c.x);
+        uint32_t lo_b = b * c.z, hi_b = __umulhi(b, c.z);
+        c = make_uint4(hi_b ^ c.y ^ k.x, lo_b, hi_a ^ c.w ^ k.y, lo_a);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 philox_draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                                             uint32_t tag, uint32_t block) {
+    return philox4x32_10(make_uint4(c0, c1, c2, (tag << 16) | block),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+__device__ __forceinline__ uint32_t word_of(uint4 w, int i) {
+    return i == 0 ? w.x : i == 1 ? w.y : i == 2 ? w.z : w.w;
+}
+
+// 24-bit uniform on [0, 1): exact in float and double.
+__device__ __forceinline__ float unif24(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+// ---------------------------------------------------------------------------
+// Arithmetic that the compiler may not contract or reorder (Kahan sums).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_fast(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
+__device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
+
+// Drive table g at the 2*spc half-step phases of one period plus a wrap entry.
+template <typename T>
+__device__ __forceinline__ void build_drive_table(const KConst<T>& K, T* tab) {
+    for (int j = threadIdx.x; j <= K.spc2; j += blockDim.x) {
+        int jj = j == K.spc2 ? 0 : j;
+        double ph = 6.283185307179586476925 * (double)jj / (double)K.spc2 + K.drive_phase;
+        tab[j] = (T)(K.drive_amp * sin(ph));
+    }
+}
+
+// Normalised coordinates -> physical slots (SI) -> scaled force coefficients.
+// Computed in double for every precision (once per particle and solve).
+template <typename T, typename X>
+__device__ __forceinline__ Coef<T> make_coef(const KConst<T>& K, const X* xd) {
+    double th[AFM_MAXD];
+#pragma unroll
+    for (int s = 0; s < AFM_MAXD; ++s) th[s] = K.fixed[s];
+    for (int d = 0; d < K.D; ++d) {
+        double v = K.lo[d] + (double)xd[d] * K.span[d];
+        v = K.logs[d] ? exp10(v) : v;
+        th[K.slot[d]] = v;
+    }
+    const double rt = 3.1622776601683794e-5;  // 10^-4.5 = sqrt(1e-9)
+    Coef<T> c;
+    c.c0 = c.c1 = c.c2 = c.c3 = (T)0;
+    switch (K.force) {
+        case F_LINEAR:
+            c.c0 = (T)(th[0] / K.k * K.s1);
+            c.c1 = (T)(th[1] * 1e9);
+            break;
+        case F_DMT:
+        case F_DMT_KV: {
+            double sR = sqrt(th[2]);
+            c.c0 = (T)((4.0 / 3.0) * th[0] * sR * rt / K.k * K.s1);
+            c.c1 = (T)(th[1] * th[2] / (6e-27 * K.k) * K.s1);
+            c.c2 = (T)(th[4] * sR * rt * K.s1 / (K.k * K.tau));
+            c.c3 = (T)(th[3] * 1e9);
+            break;
+        }
+        case F_HOOKE:
+            c.c0 = (T)(th[0] / K.k * K.s1);
+            c.c1 = (T)(th[1] * 1e9);
+            break;
+        case F_SPRING_DAMPER:
+            c.c0 = (T)(th[0] / K.k * K.s1);
+            c.c1 = (T)(th[1] * 1e9);
+            c.c2 = (T)(th[2] * K.s1 / (K.k * K.tau));
+            break;
+    }
+    return c;
+}
+
+template <int FORCE>
+struct UsesRate {
+    static constexpr bool value = FORCE == F_DMT_KV || FORCE == F_SPRING_DAMPER;
+};
+
+// Tip-sample force in scaled units; branch-free for the DMT family: the van
+// der Waals term saturates at d = a0, where it equals the Hertz branch's
+// constant -HR/(6 a0^2), so one expression covers both branches.
+template <int FORCE, typename T>
+__device__ __forceinline__ T tip_force(const Coef<T>& c, T d, T dd) {
+    if (FORCE == F_LINEAR) {
+        return -c.c0 * (d - c.c1);
+    } else if (FORCE == F_DMT || FORCE == F_DMT_KV) {
+        T dm = fmax(d, c.c3);
+        T r = rcp_fast(dm);
+        T fv = c.c1 * (r * r);
+        T del = fmax(c.c3 - d, (T)0);
+        T sq = sqrt_fast(del);
+        T F = c.c0 * (del * sq) - fv;
+        if (FORCE == F_DMT_KV) F = F - c.c2 * (sq * dd);
+        return F;
+    } else if (FORCE == F_HOOKE) {
+        return c.c0 * fmax(c.c1 - d, (T)0);
+    } else {
+        return d < c.c1 ? c.c0 * (c.c1 - d) - c.c2 * dd : (T)0;
+    }
+}
+
+// Modal accelerations (Eq. 2): a_i = tip_i F + gamma_i g - w2_i q_i - wq_i q_i'.
+// Mode 0's stiffness carries a low word (w2lo) so that the resonant mode's
+// frequency is represented to ~1e-15 in FP32 arithmetic.
+template <typename T, int M, int FORCE>
+__device__ __forceinline__ void accel(const KConst<T>& K, const Coef<T>& c, const T* q, const T* v,
+                                      T g, T* a) {
+    T u = q[0];
+#pragma unroll
+    for (int i = 1; i < M; ++i) u += q[i];
+    T dd = (T)0;
+    if (UsesRate<FORCE>::value) {
+        dd = v[0];
+#pragma unroll
+        for (int i = 1; i < M; ++i) dd += v[i];
+    }
+    T F = tip_force<FORCE, T>(c, K.Zc + u, dd);
+    // The force-independent part first, so that F enters each mode's
+    // acceleration through one final operation (shorter dependency chain).
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        T ai = fma(-K.wq[i], v[i], K.gam[i] * g);
+        if (i == 0) ai = fma(-K.w2lo[0], q[0], ai);
+        ai = fma(-K.w2[i], q[i], ai);
+        a[i] = (M <= 4) ? ai + F : fma(K.tip[i], F, ai);
+    }
+}
+
+// Kahan-compensated x += inc.
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& x, T& c, T inc) {
+    T y = sub_rn(inc, c);
+    T t = add_rn(x, y);
+    c = sub_rn(sub_rn(t, x), y);
+    x = t;
+}
+
+// One classic RK4 step (h = 6, h/2 = 3, h/6 = 1 in scaled time) with
+// compensated state update.  g0, gh, g1: drive at t, t + h/2, t + h.
+template <typename T, int M, int FORCE>
+__device__ __forceinline__ void rk4_step(const KConst<T>& K, const Coef<T>& c, T* q, T* v, T* cq,
+                                         T* cv, T g0, T gh, T g1) {
+    T a[M], qs[M], vs[M], Kq[M], Kv[M];
+    accel<T, M, FORCE>(K, c, q, v, g0, a);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        Kq[i] = v[i];
+        Kv[i] = a[i];
+        qs[i] = fma((T)3, v[i], q[i]);
+        vs[i] = fma((T)3, a[i], v[i]);
+    }
+    accel<T, M, FORCE>(K, c, qs, vs, gh, a);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        Kq[i] = fma((T)2, vs[i], Kq[i]);
+        Kv[i] = fma((T)2, a[i], Kv[i]);
+        qs[i] = fma((T)3, vs[i], q[i]);
+        vs[i] = fma((T)3, a[i], v[i]);
+    }
+    accel<T, M, FORCE>(K, c, qs, vs, gh, a);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        Kq[i] = fma((T)2, vs[i], Kq[i]);
+        Kv[i] = fma((T)2, a[i], Kv[i]);
+        qs[i] = fma((T)6, vs[i], q[i]);
+        vs[i] = fma((T)6, a[i], v[i]);
+    }
+    accel<T, M, FORCE>(K, c, qs, vs, g1, a);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        Kq[i] = Kq[i] + vs[i];
+        Kv[i] = Kv[i] + a[i];
+        kahan_add(q[i], cq[i], Kq[i]);
+        kahan_add(v[i], cv[i], Kv[i]);
+    }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void init_state(const KConst<T>& K, T* q, T* v, T* cq, T* cv) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        q[i] = K.q0[i];
+        v[i] = K.v0[i];
+        cq[i] = (T)0;
+        cv[i] = (T)0;
+    }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ T tip_sum(const T* q) {
+    T u = q[0];
+#pragma unroll
+    for (int i = 1; i < M; ++i) u += q[i];
+    return u;
+}
+
+// Forward solve of one particle over n steps, fused with the compensated
+// misfit sum of Eq. 5 (U != nullptr) and the optional time-major output.
+template <typename T, int M, int FORCE, typename TU = T>
+__device__ __forceinline__ T integrate(const KConst<T>& K, const Coef<T>& c, const T* tab,
+                                       const TU* __restrict__ U, T* __restrict__ defl, int P, int p,
+                                       int n) {
+    T q[M], v[M], cq[M], cv[M];
+    init_state<T, M>(K, q, v, cq, cv);
+    T S = (T)0, cS = (T)0;
+    int j = 0;
+    const int spc2 = K.spc2;
+    T Un = (U != nullptr && n > 0) ? (T)U[0] : (T)0;
+    for (int s = 0; s < n; ++s) {
+        T g0 = tab[j], gh = tab[j + 1], g1 = tab[j + 2];
+        j += 2;
+        if (j >= spc2) j = 0;
+        T Unext = (U != nullptr && s + 1 < n) ? (T)U[s + 1] : (T)0;
+        rk4_step<T, M, FORCE>(K, c, q, v, cq, cv, g0, gh, g1);
+        T u = tip_sum<T, M>(q);
+        if (defl != nullptr) defl[(size_t)s * P + p] = u;
+        if (U != nullptr) {
+            T r = Un - u;
+            T y = fma(r, r, -cS);
+            T t = add_rn(S, y);
+            cS = sub_rn(sub_rn(t, S), y);
+            S = t;
+        }
+        Un = Unext;
+    }
+    return S;
+}
+
+}  // namespace afm

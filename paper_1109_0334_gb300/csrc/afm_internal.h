@@ -1,0 +1,50 @@
+// afm_internal.h -- structures shared by the host set-up (afminv_api.cpp) and
+// the CUDA kernels.  Not part of the public ABI.
+//
+// Units inside the kernels ("scaled units"):
+//   length  1 nm
+//   time    tau = h / 6, where h = 1 / (f1 * steps_per_cycle) is the RK4 step,
+//           so that the RK4 constants h/2 = 3, h = 6 and h/6 = 1 are exact
+//           binary numbers (an FP32 rounding of h/6 would detune the resonant
+//           mode against the index-exact drive by ~3e-8 per step, which a
+//           quality factor of 400 amplifies to ~6e-6 of the deflection)
+//   force   k * 1 nm * (omega_1 tau)^2, so the modal equation (Eq. 2) reads
+//             q_i'' = tip_i F + gamma_i g - w2_i q_i - wq_i q_i'
+//           with w2_i = (omega_i tau)^2, wq_i = omega_i tau / Q_i.
+#pragma once
+#include <stdint.h>
+
+#define AFM_MAXM 8
+#define AFM_MAXD 5
+#define AFM_TAB_MAX 4096   // half-step drive phases per period (2 * steps_per_cycle)
+
+namespace afm {
+
+enum ForceKind { F_LINEAR = 0, F_DMT = 1, F_DMT_KV = 2, F_HOOKE = 3, F_SPRING_DAMPER = 4 };
+
+// Force-law coefficients of one particle in scaled units.
+//   LINEAR        F = -c0 (d - c1)
+//   DMT           F = c0 max(c3 - d, 0)^1.5 - c1 / max(d, c3)^2      (c0 = hz, c1 = vdw, c3 = a0)
+//   DMT_KV        DMT - c2 sqrt(max(c3 - d, 0)) d'                    (c2 = kv)
+//   HOOKE         F = c0 max(c1 - d, 0)
+//   SPRING_DAMPER F = (d < c1) ? c0 (c1 - d) - c2 d' : 0
+template <typename T>
+struct Coef {
+    T c0, c1, c2, c3;
+};
+
+// Constants of one problem in the arithmetic type of a kernel (float or
+// double), filled on the host by the per-problem set-up.
+template <typename T>
+struct KConst {
+    T w2[AFM_MAXM], w2lo[AFM_MAXM], wq[AFM_MAXM], gam[AFM_MAXM], tip[AFM_MAXM];
+    T q0[AFM_MAXM], v0[AFM_MAXM];
+    T Zc;
+    double drive_amp, drive_phase;  // g = drive_amp * sin(2 pi j / spc2 + drive_phase)
+    int m, spc2, n_steps, force, D;
+    int slot[AFM_MAXD], logs[AFM_MAXD];
+    double lo[AFM_MAXD], span[AFM_MAXD], fixed[AFM_MAXD];
+    double k, s1, tau;
+};
+
+}  // namespace afm

@@ -1,0 +1,53 @@
+// afm_launch.h -- host-side launchers of the CUDA kernels (C++ linkage,
+// internal to libafminv).  Each returns the cudaError_t of its launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "afm_internal.h"
+
+namespace afm {
+
+struct SwarmPtrs {
+    float* x;                  // [D][P]
+    float* v;                  // [D][P]
+    float* pb[2];              // personal-best positions, double-buffered by iteration parity
+    float* pbS;                // [P]
+    unsigned long long* gkey[2];  // global-best key words (S bits << 32 | particle), by parity
+    int* flags;                // [1] non-finite counter
+};
+
+struct PsoConst {
+    int P, D, iters;
+    float w, c1, c2;
+    uint64_t seed;
+    uint32_t pixel;
+};
+
+// forward + optional misfit
+cudaError_t launch_forward_f32(const KConst<float>& K, const float* x, int P, float* defl,
+                               const float* U, float* S, int* flags, cudaStream_t st);
+cudaError_t launch_forward_f64(const KConst<double>& K, const double* x, int P, double* defl,
+                               const double* U, double* S, int* flags, cudaStream_t st);
+// standalone misfit of a time-major deflection array
+cudaError_t launch_misfit(const float* defl, const float* U, int N, int P, float* S, int num_sms,
+                          cudaStream_t st);
+// synthetic records: FP32 at the fine step of K, sampled every `sub`, plus noise
+cudaError_t launch_synth(const KConst<float>& K, const double* x_truth, int n_pix,
+                         const int64_t* off, int sub, float sigma_nm, uint64_t seed,
+                         uint32_t pixel0, float* U_cat, cudaStream_t st);
+
+// particle swarm
+cudaError_t launch_pso_init(const PsoConst& pc, const SwarmPtrs& sw, cudaStream_t st);
+cudaError_t launch_pso_best(const PsoConst& pc, const SwarmPtrs& sw, const float* S, int it,
+                            cudaStream_t st);
+cudaError_t launch_pso_move(const PsoConst& pc, const SwarmPtrs& sw, int it, cudaStream_t st);
+// fused inversion iteration (it = 0: initial evaluation)
+cudaError_t launch_invert_iter(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
+                               const float* U, float* history, int it, cudaStream_t st);
+// winner re-evaluation in FP64 and result record
+cudaError_t launch_invert_final(const KConst<double>& K, const PsoConst& pc, const SwarmPtrs& sw,
+                                const float* U, float* history, void* result, cudaStream_t st);
+
+}  // namespace afm

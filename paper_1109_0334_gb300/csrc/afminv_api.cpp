@@ -1,0 +1,543 @@
+// afminv_api.cpp -- the C ABI of libafminv: argument validation, the
+// per-problem set-up in double precision on the host (modal constants of
+// Eq. 2, drive and initial state, scaled units), and the launch sequences.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/afminv.h"
+#include "afm_internal.h"
+#include "afm_launch.h"
+
+using afm::KConst;
+
+#include <vector>
+
+struct afm_ctx {
+    int device;
+    int num_sms;
+    // kernel timing (afm_profile_*): events around each fused iteration launch
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;   // reusable events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+afm_status fail(afm_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+afm_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(AFM_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define AFM_CUDA(call, where)                          \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+const double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// Clamped-free beam: i-th root of cos b cosh b + 1 = 0 (Sec. 3.2), by
+// bisection of cos b + sech b on [(2i-1) pi/2 - 1/2, (2i-1) pi/2 + 1/2].
+// ---------------------------------------------------------------------------
+double beam_root(int i) {
+    double lo = (2 * i - 1) * kPi / 2 - 0.5, hi = lo + 1.0;
+    auto f = [](double b) { return std::cos(b) + 1.0 / std::cosh(b); };
+    double flo = f(lo);
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        double mid = 0.5 * (lo + hi), fm = f(mid);
+        if ((fm < 0) == (flo < 0)) {
+            lo = mid;
+            flo = fm;
+        } else {
+            hi = mid;
+        }
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Base participation of the tip-normalised mode i (closed form of
+// <phi,1>/<phi,phi>): 4 sigma_i / (beta_i L) (-1)^(i+1), with sigma_i written
+// in decaying exponentials so that it stays finite for high modes.
+double participation(int i, double b) {
+    double e1 = std::exp(-b), e2 = e1 * e1;
+    double sigma = (1.0 + e2 + 2.0 * e1 * std::cos(b)) / (1.0 - e2 + 2.0 * e1 * std::sin(b));
+    return 4.0 * sigma / b * ((i % 2 == 1) ? 1.0 : -1.0);
+}
+
+struct Setup {
+    int m;
+    double w[AFM_MAXM], gam[AFM_MAXM];
+    double wd, a, psi, h;
+    double q0[AFM_MAXM], v0[AFM_MAXM];  // SI
+};
+
+void modal_setup(const afm_problem& pr, int spc, Setup& s) {
+    std::memset(&s, 0, sizeof(s));
+    s.m = pr.model == AFM_POINT_MASS ? 1 : pr.n_modes;
+    const double w1 = 2.0 * kPi * pr.f1_hz;
+    if (pr.model == AFM_POINT_MASS) {
+        s.w[0] = w1;
+        s.gam[0] = 1.0;
+    } else {
+        const double b1 = beam_root(1);
+        for (int i = 0; i < s.m; ++i) {
+            double b = beam_root(i + 1);
+            s.w[i] = w1 * (b / b1) * (b / b1);
+            s.gam[i] = participation(i + 1, b);
+        }
+    }
+    // Drive at the first resonance; amplitude and phase such that the free
+    // linear steady state at the tip is A0 cos(w t); start on that state.
+    s.wd = w1;
+    std::complex<double> H[AFM_MAXM], Hs(0.0, 0.0);
+    for (int i = 0; i < s.m; ++i) {
+        H[i] = s.gam[i] / std::complex<double>(s.w[i] * s.w[i] - s.wd * s.wd,
+                                                s.wd * s.w[i] / pr.Q[i]);
+        Hs += H[i];
+    }
+    s.a = pr.A0_m / (s.wd * s.wd * std::abs(Hs));
+    s.psi = kPi / 2 - std::arg(Hs);
+    const std::complex<double> rot = std::polar(1.0, s.psi);
+    for (int i = 0; i < s.m; ++i) {
+        std::complex<double> c = s.a * s.wd * s.wd * H[i] * rot;
+        s.q0[i] = c.imag();
+        s.v0[i] = s.wd * c.real();
+    }
+    s.h = 1.0 / (pr.f1_hz * spc);
+}
+
+template <typename T>
+void fill_kconst(const afm_problem& pr, int spc, int n_steps, KConst<T>& K) {
+    Setup s;
+    modal_setup(pr, spc, s);
+    std::memset(&K, 0, sizeof(K));
+    const double tau = s.h / 6.0, nm = 1e-9;
+    const double w1t = s.w[0] * tau;
+    for (int i = 0; i < AFM_MAXM; ++i) {
+        if (i < s.m) {
+            double w2 = (s.w[i] * tau) * (s.w[i] * tau);
+            K.w2[i] = (T)w2;
+            K.w2lo[i] = (T)(w2 - (double)K.w2[i]);
+            K.wq[i] = (T)(s.w[i] * tau / pr.Q[i]);
+            K.gam[i] = (T)s.gam[i];
+            K.tip[i] = (T)1;
+            K.q0[i] = (T)(s.q0[i] / nm);
+            K.v0[i] = (T)(s.v0[i] * tau / nm);
+        }
+    }
+    K.Zc = (T)(pr.Zc_m / nm);
+    K.drive_amp = (s.a / nm) * (s.wd * tau) * (s.wd * tau);
+    K.drive_phase = s.psi;
+    K.m = s.m;
+    K.spc2 = 2 * spc;
+    K.n_steps = n_steps;
+    K.force = pr.force;
+    K.D = pr.n_free;
+    for (int s5 = 0; s5 < AFM_MAXD; ++s5) K.fixed[s5] = pr.fixed[s5];
+    for (int d = 0; d < pr.n_free; ++d) {
+        K.slot[d] = pr.slot[d];
+        K.logs[d] = pr.log_scale[d] ? 1 : 0;
+        if (K.logs[d]) {
+            K.lo[d] = std::log10(pr.lo[d]);
+            K.span[d] = std::log10(pr.hi[d]) - std::log10(pr.lo[d]);
+        } else {
+            K.lo[d] = pr.lo[d];
+            K.span[d] = pr.hi[d] - pr.lo[d];
+        }
+    }
+    K.k = pr.k_N_per_m;
+    K.s1 = w1t * w1t;
+    K.tau = tau;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+afm_status check_problem(const afm_problem* pr) {
+    if (!pr) return fail(AFM_ERR_INVALID_ARG, "problem is NULL");
+    if (pr->model == AFM_FE_HERMITE)
+        return fail(AFM_ERR_UNSUPPORTED, "model FE_HERMITE is not available in this call");
+    if (pr->model != AFM_POINT_MASS && pr->model != AFM_MODAL_EB)
+        return fail(AFM_ERR_INVALID_ARG, "unknown model %d", pr->model);
+    const int m = pr->model == AFM_POINT_MASS ? 1 : pr->n_modes;
+    if (m < 1 || m > AFM_MAX_MODES) return fail(AFM_ERR_INVALID_ARG, "n_modes %d outside 1..8", m);
+    if (!finite_pos(pr->f1_hz)) return fail(AFM_ERR_INVALID_ARG, "f1_hz must be > 0");
+    if (!finite_pos(pr->k_N_per_m)) return fail(AFM_ERR_INVALID_ARG, "k_N_per_m must be > 0");
+    for (int i = 0; i < m; ++i)
+        if (!finite_pos(pr->Q[i])) return fail(AFM_ERR_INVALID_ARG, "Q[%d] must be > 0", i);
+    if (!finite_pos(pr->A0_m)) return fail(AFM_ERR_INVALID_ARG, "A0_m must be > 0");
+    if (!std::isfinite(pr->Zc_m)) return fail(AFM_ERR_INVALID_ARG, "Zc_m must be finite");
+    if (pr->steps_per_cycle < 4 || pr->steps_per_cycle > AFM_TAB_MAX / 2)
+        return fail(AFM_ERR_INVALID_ARG, "steps_per_cycle %d outside 4..%d", pr->steps_per_cycle,
+                    AFM_TAB_MAX / 2);
+    if (pr->n_steps < 1) return fail(AFM_ERR_INVALID_ARG, "n_steps must be >= 1");
+    if (pr->force < AFM_LINEAR_SPRING || pr->force > AFM_SPRING_DAMPER)
+        return fail(AFM_ERR_INVALID_ARG, "unknown force %d", pr->force);
+    if (pr->n_free < 0 || pr->n_free > AFM_MAX_PARAMS)
+        return fail(AFM_ERR_INVALID_ARG, "n_free %d outside 0..5", pr->n_free);
+    int used = 0;
+    for (int d = 0; d < pr->n_free; ++d) {
+        int s = pr->slot[d];
+        if (s < 0 || s >= AFM_MAX_PARAMS || (used >> s) & 1)
+            return fail(AFM_ERR_INVALID_ARG, "slot[%d] = %d invalid or repeated", d, s);
+        used |= 1 << s;
+        if (!std::isfinite(pr->lo[d]) || !std::isfinite(pr->hi[d]) || !(pr->lo[d] < pr->hi[d]))
+            return fail(AFM_ERR_INVALID_ARG, "bounds of dim %d need lo < hi", d);
+        if (pr->log_scale[d] && !(pr->lo[d] > 0))
+            return fail(AFM_ERR_INVALID_ARG, "log-scaled dim %d needs lo > 0", d);
+    }
+    for (int s = 0; s < AFM_MAX_PARAMS; ++s)
+        if (!((used >> s) & 1) && !std::isfinite(pr->fixed[s]))
+            return fail(AFM_ERR_INVALID_ARG, "fixed[%d] must be finite", s);
+    if (pr->force == AFM_DMT || pr->force == AFM_DMT_KV) {
+        // R (slot 2) and a0 (slot 3) must stay positive everywhere in the box
+        for (int s = 2; s <= 3; ++s) {
+            bool ok = true;
+            if ((used >> s) & 1) {
+                for (int d = 0; d < pr->n_free; ++d)
+                    if (pr->slot[d] == s && !(pr->lo[d] > 0)) ok = false;
+            } else if (!(pr->fixed[s] > 0)) {
+                ok = false;
+            }
+            if (!ok) return fail(AFM_ERR_INVALID_ARG, "DMT needs R and a0 > 0");
+        }
+    }
+    return AFM_OK;
+}
+
+afm_status check_ctx(afm_ctx* ctx) {
+    if (!ctx) return fail(AFM_ERR_INVALID_ARG, "context is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return AFM_OK;
+}
+
+afm_status check_pso(const afm_pso_cfg* cfg, int D) {
+    if (!cfg) return fail(AFM_ERR_INVALID_ARG, "pso cfg is NULL");
+    if (cfg->P < 1) return fail(AFM_ERR_INVALID_ARG, "P must be >= 1");
+    if (cfg->iters < 0) return fail(AFM_ERR_INVALID_ARG, "iters must be >= 0");
+    if (!std::isfinite(cfg->w) || !std::isfinite(cfg->c1) || !std::isfinite(cfg->c2))
+        return fail(AFM_ERR_INVALID_ARG, "w, c1, c2 must be finite");
+    if (D < 1) return fail(AFM_ERR_INVALID_ARG, "the swarm needs at least one free parameter");
+    return AFM_OK;
+}
+
+afm::PsoConst pso_const(const afm_pso_cfg& c, int D) {
+    afm::PsoConst pc;
+    pc.P = c.P;
+    pc.D = D;
+    pc.iters = c.iters;
+    pc.w = (float)c.w;
+    pc.c1 = (float)c.c1;
+    pc.c2 = (float)c.c2;
+    pc.seed = c.seed;
+    pc.pixel = c.pixel;
+    return pc;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+cudaError_t take_event(afm_ctx* ctx, cudaEvent_t* e) {
+    if (!ctx->ev_pool.empty()) {
+        *e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreate(e);
+}
+
+// Launch `fn` on stream s, bracketed by timing events when profiling is on.
+template <typename Fn>
+cudaError_t timed_launch(afm_ctx* ctx, cudaStream_t s, Fn&& fn) {
+    if (!ctx->profiling) return fn();
+    cudaEvent_t a, b;
+    cudaError_t e = take_event(ctx, &a);
+    if (e == cudaSuccess) e = take_event(ctx, &b);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(a, s)) != cudaSuccess) return e;
+    if ((e = fn()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b, s)) != cudaSuccess) return e;
+    ctx->ev_pending.emplace_back(a, b);
+    return cudaSuccess;
+}
+
+struct InvLayout {
+    size_t x, v, pb0, pb1, pbS, gkey, flags, total;
+};
+
+InvLayout invert_layout(int P, int D) {
+    InvLayout L;
+    size_t off = 0;
+    const size_t xs = align256(sizeof(float) * (size_t)P * D);
+    L.x = off; off += xs;
+    L.v = off; off += xs;
+    L.pb0 = off; off += xs;
+    L.pb1 = off; off += xs;
+    L.pbS = off; off += align256(sizeof(float) * (size_t)P);
+    L.gkey = off; off += 256;
+    L.flags = off; off += 256;
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int afm_version(void) { return 100; }
+
+const char* afm_last_error(void) { return g_err; }
+
+const char* afm_status_string(int st) {
+    switch (st) {
+        case AFM_OK: return "AFM_OK";
+        case AFM_ERR_INVALID_ARG: return "AFM_ERR_INVALID_ARG";
+        case AFM_ERR_CUDA: return "AFM_ERR_CUDA";
+        case AFM_ERR_NONFINITE: return "AFM_ERR_NONFINITE";
+        case AFM_ERR_TIMEOUT: return "AFM_ERR_TIMEOUT";
+        case AFM_ERR_UNSUPPORTED: return "AFM_ERR_UNSUPPORTED";
+    }
+    return "AFM_ERR_UNKNOWN";
+}
+
+afm_status afm_ctx_create(int device, afm_ctx** out) {
+    g_err[0] = 0;
+    if (!out) return fail(AFM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    AFM_CUDA(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(AFM_ERR_INVALID_ARG, "device %d of %d", device, n);
+    AFM_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    int sms = 0;
+    AFM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "SM count");
+    afm_ctx* c = new (std::nothrow) afm_ctx;
+    if (!c) return fail(AFM_ERR_INVALID_ARG, "out of host memory");
+    c->device = device;
+    c->num_sms = sms;
+    *out = c;
+    return AFM_OK;
+}
+
+afm_status afm_ctx_destroy(afm_ctx* ctx) {
+    if (ctx) {
+        for (auto& pr : ctx->ev_pending) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    }
+    delete ctx;
+    return AFM_OK;
+}
+
+afm_status afm_profile_enable(afm_ctx* ctx, int on) {
+    g_err[0] = 0;
+    if (!ctx) return fail(AFM_ERR_INVALID_ARG, "context is NULL");
+    ctx->profiling = on != 0;
+    return AFM_OK;
+}
+
+afm_status afm_profile_read(afm_ctx* ctx, double* ms, int* launches) {
+    g_err[0] = 0;
+    afm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!ms || !launches) return fail(AFM_ERR_INVALID_ARG, "NULL output");
+    double total = 0.0;
+    int n = 0;
+    for (auto& pr : ctx->ev_pending) {
+        AFM_CUDA(cudaEventSynchronize(pr.second), "cudaEventSynchronize");
+        float t = 0.f;
+        AFM_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second), "cudaEventElapsedTime");
+        total += t;
+        ++n;
+        ctx->ev_pool.push_back(pr.first);
+        ctx->ev_pool.push_back(pr.second);
+    }
+    ctx->ev_pending.clear();
+    *ms = total;
+    *launches = n;
+    return AFM_OK;
+}
+
+afm_status afm_forward_batch(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
+                             float* defl, const float* U, float* S, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if (P < 1) return fail(AFM_ERR_INVALID_ARG, "P must be >= 1");
+    if (prob->n_free > 0 && !x) return fail(AFM_ERR_INVALID_ARG, "x is NULL");
+    if (S && !U) return fail(AFM_ERR_INVALID_ARG, "S requested without a record U");
+    if (!S && !defl) return fail(AFM_ERR_INVALID_ARG, "nothing to compute (defl and S NULL)");
+    KConst<float> K;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_f32(K, x, P, defl, U, S, nullptr, s); }),
+             "forward kernel");
+    return AFM_OK;
+}
+
+afm_status afm_forward_batch_f64(afm_ctx* ctx, const afm_problem* prob, const double* x, int P,
+                                 double* defl, const double* U, double* S, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if (P < 1) return fail(AFM_ERR_INVALID_ARG, "P must be >= 1");
+    if (prob->n_free > 0 && !x) return fail(AFM_ERR_INVALID_ARG, "x is NULL");
+    if (S && !U) return fail(AFM_ERR_INVALID_ARG, "S requested without a record U");
+    if (!S && !defl) return fail(AFM_ERR_INVALID_ARG, "nothing to compute (defl and S NULL)");
+    KConst<double> K;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    AFM_CUDA(afm::launch_forward_f64(K, x, P, defl, U, S, nullptr, s), "forward f64 kernel");
+    return AFM_OK;
+}
+
+afm_status afm_misfit(afm_ctx* ctx, const float* defl, const float* U, int N, int P, float* S,
+                      void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!defl || !U || !S) return fail(AFM_ERR_INVALID_ARG, "NULL array");
+    if (N < 1 || P < 1) return fail(AFM_ERR_INVALID_ARG, "N and P must be >= 1");
+    AFM_CUDA(afm::launch_misfit(defl, U, N, P, S, ctx->num_sms,
+                                reinterpret_cast<cudaStream_t>(stream)),
+             "misfit kernel");
+    return AFM_OK;
+}
+
+static afm_status swarm_ptrs(const afm_swarm* sw, afm::SwarmPtrs& p) {
+    if (!sw || !sw->x || !sw->v || !sw->pbest_x || !sw->pbest_S || !sw->gbest)
+        return fail(AFM_ERR_INVALID_ARG, "swarm has NULL arrays");
+    p.x = sw->x;
+    p.v = sw->v;
+    p.pb[0] = p.pb[1] = sw->pbest_x;
+    p.pbS = sw->pbest_S;
+    p.gkey[0] = p.gkey[1] = sw->gbest;
+    p.flags = nullptr;
+    return AFM_OK;
+}
+
+afm_status afm_pso_init(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!sw) return fail(AFM_ERR_INVALID_ARG, "swarm is NULL");
+    if ((st = check_pso(cfg, sw->D))) return st;
+    if (sw->P != cfg->P || sw->D > AFM_MAX_PARAMS)
+        return fail(AFM_ERR_INVALID_ARG, "swarm shape (P %d, D %d) does not match", sw->P, sw->D);
+    afm::SwarmPtrs p;
+    if ((st = swarm_ptrs(sw, p))) return st;
+    AFM_CUDA(afm::launch_pso_init(pso_const(*cfg, sw->D), p, reinterpret_cast<cudaStream_t>(stream)),
+             "pso init kernel");
+    return AFM_OK;
+}
+
+afm_status afm_pso_step(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw, const float* S_new,
+                        uint32_t iter, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!sw) return fail(AFM_ERR_INVALID_ARG, "swarm is NULL");
+    if ((st = check_pso(cfg, sw->D))) return st;
+    if (sw->P != cfg->P || sw->D > AFM_MAX_PARAMS)
+        return fail(AFM_ERR_INVALID_ARG, "swarm shape (P %d, D %d) does not match", sw->P, sw->D);
+    if (!S_new) return fail(AFM_ERR_INVALID_ARG, "S_new is NULL");
+    if ((int)iter > cfg->iters) return fail(AFM_ERR_INVALID_ARG, "iter %u > iters", iter);
+    afm::SwarmPtrs p;
+    if ((st = swarm_ptrs(sw, p))) return st;
+    const afm::PsoConst pc = pso_const(*cfg, sw->D);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    AFM_CUDA(afm::launch_pso_best(pc, p, S_new, (int)iter, s), "pso best kernel");
+    if ((int)iter < cfg->iters) AFM_CUDA(afm::launch_pso_move(pc, p, (int)iter + 1, s), "pso move kernel");
+    return AFM_OK;
+}
+
+afm_status afm_invert_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
+                                     size_t* bytes) {
+    g_err[0] = 0;
+    if (!bytes) return fail(AFM_ERR_INVALID_ARG, "bytes is NULL");
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_pso(cfg, prob->n_free))) return st;
+    *bytes = invert_layout(cfg->P, prob->n_free).total;
+    return AFM_OK;
+}
+
+afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
+                      const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
+                      afm_result* result, float* history, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if ((st = check_pso(cfg, prob->n_free))) return st;
+    if (!U || !result || !workspace) return fail(AFM_ERR_INVALID_ARG, "NULL U, result or workspace");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256)
+        return fail(AFM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    const int D = prob->n_free, P = cfg->P;
+    const InvLayout L = invert_layout(P, D);
+    if (workspace_bytes < L.total)
+        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, L.total);
+    char* ws = static_cast<char*>(workspace);
+    afm::SwarmPtrs sw;
+    sw.x = reinterpret_cast<float*>(ws + L.x);
+    sw.v = reinterpret_cast<float*>(ws + L.v);
+    sw.pb[0] = reinterpret_cast<float*>(ws + L.pb0);
+    sw.pb[1] = reinterpret_cast<float*>(ws + L.pb1);
+    sw.pbS = reinterpret_cast<float*>(ws + L.pbS);
+    sw.gkey[0] = reinterpret_cast<unsigned long long*>(ws + L.gkey);
+    sw.gkey[1] = sw.gkey[0] + 1;
+    sw.flags = reinterpret_cast<int*>(ws + L.flags);
+    KConst<float> Kf;
+    KConst<double> Kd;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kf);
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kd);
+    const afm::PsoConst pc = pso_const(*cfg, D);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    AFM_CUDA(afm::launch_pso_init(pc, sw, s), "pso init kernel");
+    for (int it = 0; it <= cfg->iters; ++it)
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_invert_iter(Kf, pc, sw, U, history, it, s); }),
+                 "invert iteration kernel");
+    AFM_CUDA(afm::launch_invert_final(Kd, pc, sw, U, history, result, s), "invert final kernel");
+    return AFM_OK;
+}
+
+afm_status afm_synth_records(afm_ctx* ctx, const afm_problem* prob, const double* x_truth,
+                             int n_pix, const int64_t* off, int sub, double sigma_m,
+                             uint64_t seed, uint32_t pixel0, float* U_cat, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if (n_pix < 1 || !off || !U_cat || (prob->n_free > 0 && !x_truth))
+        return fail(AFM_ERR_INVALID_ARG, "n_pix >= 1 and non-NULL off, U_cat, x_truth needed");
+    if (sub < 1 || (long)prob->steps_per_cycle * sub > AFM_TAB_MAX / 2)
+        return fail(AFM_ERR_INVALID_ARG, "sub %d: steps_per_cycle * sub must be <= %d", sub,
+                    AFM_TAB_MAX / 2);
+    if (!(sigma_m >= 0) || !std::isfinite(sigma_m)) return fail(AFM_ERR_INVALID_ARG, "sigma must be >= 0");
+    KConst<float> K;
+    fill_kconst(*prob, prob->steps_per_cycle * sub, prob->n_steps * sub, K);
+    AFM_CUDA(afm::launch_synth(K, x_truth, n_pix, off, sub, (float)(sigma_m / 1e-9), seed, pixel0,
+                               U_cat, reinterpret_cast<cudaStream_t>(stream)),
+             "synth kernel");
+    return AFM_OK;
+}
+
+}  // extern "C"

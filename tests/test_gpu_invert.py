@@ -1,0 +1,133 @@
+"""GPU parity of the particle swarm (Sec. 3.4, Eq. 8) and of the fused
+inversion (IP, Sec. 2.3) against the FP64 oracle, through the C ABI.
+
+Swarm initialisation is bit-exact (24-bit uniforms are exact in FP32).  One
+swarm step agrees to FP32 rounding.  Whole inversions follow the same
+seeded swarm but may part ways after near-ties of FP32 and FP64 misfits, so
+they are compared on what is unique: the optimum misfit (within 1e-4) and
+the parameter combinations the record determines (within 0.5 %); along
+valleys the record does not resolve, the GPU's point must reach the
+oracle's misfit.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1109_0334_gb300 import workloads as W
+from common import NM, identifiable_check, oracle_record
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def afm():
+    from paper_1109_0334_gb300 import build
+    build.build()
+    from paper_1109_0334_gb300 import afminv
+    assert torch.cuda.is_available()
+    return afminv
+
+
+def test_pso_init_bit_exact(orc, afm):
+    for D, P in ((2, 64), (4, 1024), (5, 37)):
+        cfg = afm.PsoCfg(P=P, iters=10, w=0.7, c1=1.5, c2=1.5, seed=1109033402, pixel=7)
+        sw = afm.pso_init(cfg, D)
+        torch.cuda.synchronize()
+        x_ref, v_ref = orc.pso_init(P, D, cfg.seed, cfg.pixel)
+        assert np.array_equal(sw.x.cpu().numpy().astype(np.float64), x_ref)
+        assert np.array_equal(sw.v.cpu().numpy().astype(np.float64), v_ref)
+        assert np.all(np.isinf(sw.pbest_S.cpu().numpy()))
+
+
+def test_pso_step_matches_oracle(orc, afm):
+    """P9: from identical (x, v, pbest, S) the GPU step equals the Eq. 8
+    update of the oracle to FP32 rounding; personal and global bests are
+    exact, ties going to the lowest index."""
+    D, P, it = 4, 301, 5
+    cfg = afm.PsoCfg(P=P, iters=10, w=0.7, c1=1.5, c2=1.5, seed=99, pixel=3)
+    sw = afm.pso_init(cfg, D)
+    rng = np.random.default_rng(0)
+    x = rng.uniform(0, 1, (D, P)).astype(np.float32)
+    v = rng.uniform(-0.3, 0.3, (D, P)).astype(np.float32)
+    pbx = rng.uniform(0, 1, (D, P)).astype(np.float32)
+    pbS = rng.uniform(1, 2, P).astype(np.float32)
+    S = rng.uniform(0.5, 2.5, P).astype(np.float32)
+    S[[17, 40, 200]] = 0.25          # a three-way tie for the global best
+    S[55] = np.nan                   # a diverged candidate never becomes a best
+    for t, a in ((sw.x, x), (sw.v, v), (sw.pbest_x, pbx), (sw.pbest_S, pbS)):
+        t.copy_(torch.from_numpy(a))
+    sw.gbest.fill_(-1)
+    afm.pso_step(cfg, sw, torch.from_numpy(S).cuda(), it)
+    torch.cuda.synchronize()
+    # expected bests from the definition
+    Sd = np.where(np.isnan(S), np.inf, S).astype(np.float64)
+    better = Sd < pbS
+    pb_exp = np.where(better[None, :], x, pbx)
+    pbS_exp = np.where(better, Sd, pbS)
+    g = int(np.argmin(pbS_exp))
+    assert g == 17
+    assert np.array_equal(sw.pbest_S.cpu().numpy(), pbS_exp.astype(np.float32))
+    assert np.array_equal(sw.pbest_x.cpu().numpy(), pb_exp)
+    key = int(sw.gbest.cpu().numpy().view(np.uint64)[0])
+    assert key & 0xFFFFFFFF == 17
+    x_ref, v_ref = orc.pso_update(it + 1, cfg.seed, cfg.pixel, cfg.w, cfg.c1, cfg.c2,
+                                  x.astype(np.float64), v.astype(np.float64),
+                                  pb_exp.astype(np.float64), pb_exp[:, g].astype(np.float64))
+    xg, vg = sw.x.cpu().numpy(), sw.v.cpu().numpy()
+    assert np.max(np.abs(vg - v_ref)) <= 4 * np.finfo(np.float32).eps
+    assert np.max(np.abs(xg - x_ref)) <= 4 * np.finfo(np.float32).eps
+    # clamped coordinates sit on the bound with zero velocity on both sides
+    on_bound = (x_ref == 0.0) | (x_ref == 1.0)
+    assert np.all(vg[on_bound] == 0.0)
+
+
+def _gpu_invert(afm, spec, U32):
+    prob = afm.make_problem(spec)
+    cfg = afm.make_pso(spec)
+    res, hist = afm.invert(prob, torch.from_numpy(U32).cuda(), cfg)
+    torch.cuda.synchronize()
+    return afm.decode_result(res), hist.cpu().numpy()
+
+
+def _check_inversion(orc, spec, U_m, r, x_o, S_o_m, hist):
+    D = len(spec["free"])
+    x_g = r["x"][:D]
+    err, n_id, S_g_orc, widths = identifiable_check(orc, spec, U_m, x_o, S_o_m, x_g)
+    S_o = S_o_m / NM ** 2
+    assert n_id >= 1
+    assert err <= 0.005, (err, widths)
+    # the GPU's optimum is as good as the oracle's
+    assert S_g_orc / NM ** 2 <= S_o * (1 + 1e-4)
+    # FP32 misfit of the winner and its FP64 re-evaluation on the GPU
+    assert abs(r["S"] - S_g_orc / NM ** 2) <= 1e-4 * S_o
+    assert abs(r["S_f64"] - S_g_orc / NM ** 2) <= 1e-9 * S_o
+    assert np.all(np.diff(hist) <= 0)
+    assert r["status"] == 0 and r["nonfinite"] == 0
+
+
+def test_invert_c1_parity(orc, afm):
+    spec = W.get("c1")
+    U32, U_m, xt = oracle_record(orc, spec)
+    r, hist = _gpu_invert(afm, spec, U32)
+    x_o, S_o, _ = orc.invert(orc.make_case(spec), orc.make_pmap(spec), U_m, spec["P"],
+                             spec["iters"], spec["w"], spec["c1"], spec["c2"], spec["seed"])
+    _check_inversion(orc, spec, U_m, r, x_o, S_o, hist)
+    assert r["iters"] == spec["iters"] and len(hist) == spec["iters"] + 1
+
+
+def test_invert_c2_full_size_parity(orc, afm):
+    """The 1024 x 100 inversion of the 3-mode cantilever (25 600 steps)
+    against the oracle's own inversion of the same record, stored by
+    tests/golden/make_golden.py (oracle only)."""
+    with open(os.path.join(GOLDEN, "c2_invert.json")) as f:
+        gold = json.load(f)
+    spec = W.get("c2")
+    U32, U_m, xt = oracle_record(orc, spec)
+    assert abs(float(np.sum(U_m ** 2)) / gold["sumU2_m2"] - 1) < 1e-9
+    r, hist = _gpu_invert(afm, spec, U32)
+    _check_inversion(orc, spec, U_m, r, np.array(gold["x"]), gold["S_m2"], hist)
