@@ -403,6 +403,41 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------------------
+# Small untimed cases for profiler captures
+# ---------------------------------------------------------------------------
+def run_probe(args):
+    """--probe invert: one inversion of the workload with --probe-iters
+    updates; --probe forward: two forward + misfit launches over
+    --probe-particles particles.  Prints the result; no timing."""
+    import torch
+
+    from paper_1109_0334_gb300 import build as B
+    B.build()
+    from paper_1109_0334_gb300 import afminv as A
+    from paper_1109_0334_gb300 import workloads as W
+
+    spec = W.get(args.workload, iters=args.probe_iters)
+    D = len(spec["free"])
+    N = W.n_steps(spec)
+    prob = A.make_problem(spec)
+    off = torch.tensor([0, N], dtype=torch.int64, device="cuda")
+    xt = torch.full((D, 1), 0.5, dtype=torch.float64, device="cuda")
+    U = A.synth_records(prob, xt, off, spec["record_sub"], spec["sigma"], spec["seed"], 0)
+    if args.probe == "invert":
+        res, _ = A.invert(prob, U, A.make_pso(spec))
+        torch.cuda.synchronize()
+        print(json.dumps({k: (v.tolist() if hasattr(v, "tolist") else v)
+                          for k, v in A.decode_result(res).items()}))
+    else:
+        g = torch.Generator(device="cuda").manual_seed(7)
+        x = torch.rand((D, args.probe_particles), dtype=torch.float32, device="cuda", generator=g)
+        for _ in range(2):
+            _, S = A.forward_batch(prob, x, U, want_defl=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"particles": args.probe_particles, "S_mean": float(S.mean())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -412,8 +447,14 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the wide forward launch")
+    ap.add_argument("--probe", choices=["invert", "forward"], default=None,
+                    help="run one small untimed case for a profiler capture and exit")
+    ap.add_argument("--probe-iters", type=int, default=2)
+    ap.add_argument("--probe-particles", type=int, default=32768)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -50,7 +50,7 @@ __global__ void fwd_kernel(const KConst<T> K, const T* __restrict__ x, int P,
     if (S != nullptr) {
         if (!(s < (T)INFINITY)) {
             s = (T)INFINITY;
-            atomicAdd(flags, 1);
+            if (flags != nullptr) atomicAdd(flags, 1);
         }
         S[p] = s;
     }
