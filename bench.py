@@ -116,10 +116,17 @@ def measured_peaks() -> dict:
     return {}
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {
+    "invert_iter_kernel": ["afm_device.cuh", "afm_internal.h", "kern_invert.cu"],
+    "fwd_kernel": ["afm_device.cuh", "afm_internal.h", "kern_forward.cu"],
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the sources a kernel is compiled from (first 16 hex digits)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1109_0334_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1109_0334_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -128,10 +135,10 @@ def ncu_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel sources (profiles/*.md lines 'traffic: <kernel>
     <workload> <bytes> <source-hash>')."""
-    want = kernel_source_hash()
+    want = kernel_source_hash(kernel)
     for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         for line in open(f):
-            parts = line.strip().split()
+            parts = line.strip().strip("`").split()
             if len(parts) == 5 and parts[0] == "traffic:" and parts[1] == kernel \
                     and parts[2] == workload and parts[4] == want:
                 return float(parts[3])
