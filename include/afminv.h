@@ -203,6 +203,30 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
                       const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
                       afm_result* result, float* history, void* stream);
 
+/* ---- inversion without any device allocation ----------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory at all, such as a real-time AFM feedback
+ * loop that forbids allocator calls once scanning has started, or a plug-in
+ * whose host application owns the whole device-memory budget.  It runs the
+ * same fused inversion as afm_invert, but its swarm state lives in a
+ * fixed array of AFM_NOALLOC_SCRATCH_BYTES inside the library's device data
+ * (held by every GPU that loads the library until the process exits)
+ * instead of a caller workspace; the caller still passes U, result and
+ * history.  The swarm must fit: afm_invert_workspace_size() <=
+ * AFM_NOALLOC_SCRATCH_BYTES (about P * D <= 200 000), else
+ * AFM_ERR_INVALID_ARG.  It calls no cudaMalloc/cudaFree.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) once; make that first call before any stream
+ *     capture.
+ *   - All calls share the one array, and it keeps the last call's contents
+ *     (each call re-initialises the swarm state it needs).  Calls whose work
+ *     overlaps on the GPU (different streams or host threads) race on it:
+ *     serialise them. */
+#define AFM_NOALLOC_SCRATCH_BYTES (4u << 20)
+afm_status afm_invert_noalloc(afm_ctx* ctx, const afm_problem* prob, const float* U,
+                              const afm_pso_cfg* cfg, afm_result* result, float* history,
+                              void* stream);
+
 /* ---- synthetic records (Sec. 4.1: data made by a different integration) --
  * For each of n_pix pixels, the truth x* (normalised, [D][n_pix] device
  * double) is integrated in FP64 at 1/sub of the solver step and sampled

@@ -97,6 +97,8 @@ def lib():
                                                     C.POINTER(C.c_size_t)]
             L.afm_invert.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), vp,
                                      C.c_size_t, vp, vp, vp]
+            L.afm_invert_noalloc.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), vp,
+                                             vp, vp]
             L.afm_synth_records.argtypes = [vp, C.POINTER(Problem), vp, i, vp, i, d, u64, u32,
                                             vp, vp]
             _lib = L
@@ -287,6 +289,16 @@ def invert(prob: Problem, U, cfg: PsoCfg, workspace=None, result=None, history=N
     _check(lib().afm_invert(context(dev.index), C.byref(prob), _ptr(U), C.byref(cfg),
                             _ptr(workspace), C.c_size_t(workspace.numel()), _ptr(result),
                             _ptr(history), _stream(stream)))
+    return result, history
+
+
+def invert_noalloc(prob: Problem, U, cfg: PsoCfg, result, history=None, stream=None):
+    """IP without a workspace: the swarm state lives in the library's fixed
+    device scratch (see afm_invert_noalloc), so this call allocates nothing.
+    The caller provides `result` (uint8 CUDA tensor of sizeof(afm_result)
+    bytes) and optionally `history` (float32 [iters + 1])."""
+    _check(lib().afm_invert_noalloc(context(U.device.index), C.byref(prob), _ptr(U), C.byref(cfg),
+                                    _ptr(result), _ptr(history), _stream(stream)))
     return result, history
 
 

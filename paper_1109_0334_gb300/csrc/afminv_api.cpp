@@ -297,6 +297,46 @@ InvLayout invert_layout(int P, int D) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Hooks for other translation units of the library (the allocation-free
+// inversion entry point shares this file's validation and set-up).
+// ---------------------------------------------------------------------------
+namespace afm {
+namespace detail {
+
+afm_status set_error(afm_status st, const char* msg) { return fail(st, "%s", msg); }
+
+afm_status prepare_invert(afm_ctx* ctx, const afm_problem* prob, const afm_pso_cfg* cfg,
+                          KConst<float>* Kf, KConst<double>* Kd, PsoConst* pc,
+                          size_t* scratch_bytes, int* device) {
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if ((st = check_pso(cfg, prob->n_free))) return st;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, *Kf);
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, *Kd);
+    *pc = pso_const(*cfg, prob->n_free);
+    *scratch_bytes = invert_layout(cfg->P, prob->n_free).total;
+    *device = ctx->device;
+    return AFM_OK;
+}
+
+void carve_swarm(void* base, int P, int D, SwarmPtrs* sw) {
+    const InvLayout L = invert_layout(P, D);
+    char* ws = static_cast<char*>(base);
+    sw->x = reinterpret_cast<float*>(ws + L.x);
+    sw->v = reinterpret_cast<float*>(ws + L.v);
+    sw->pb[0] = reinterpret_cast<float*>(ws + L.pb0);
+    sw->pb[1] = reinterpret_cast<float*>(ws + L.pb1);
+    sw->pbS = reinterpret_cast<float*>(ws + L.pbS);
+    sw->gkey[0] = reinterpret_cast<unsigned long long*>(ws + L.gkey);
+    sw->gkey[1] = sw->gkey[0] + 1;
+    sw->flags = reinterpret_cast<int*>(ws + L.flags);
+}
+
+}  // namespace detail
+}  // namespace afm
+
 extern "C" {
 
 int afm_version(void) { return 100; }
