@@ -203,6 +203,29 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
                       const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
                       afm_result* result, float* history, void* stream);
 
+/* ---- many pixel inversions in one launch (image scans) -------------------
+ * n_pix independent IPs, pixel i with record U_cat[off[i] .. off[i+1]) (its
+ * own length; prob->n_steps is only validated, not used) and Philox counter
+ * word 2 = pixel0 + i.  Each pixel runs the same swarm as afm_invert with
+ * cfg->P particles (<= 4096) and cfg->iters updates (cfg->pixel is ignored).
+ * One persistent kernel: blocks pull pixels from a queue, longest record
+ * first, and keep the whole swarm of a pixel on chip; then every winner is
+ * re-evaluated in FP64.  results [n_pix] (device afm_result) are indexed by
+ * pixel.  The launch sequence is captured once into a CUDA graph (cached in
+ * the context per argument set) and replayed on `stream`.
+ * Particles per thread: *particles_per_thread = 1, 2 or 4 forces a choice;
+ * NULL or 0 selects the autotuner, which on the first call for a new (modes,
+ * force, P, D, steps per cycle) times one evaluation of the first wave of
+ * pixels per candidate (synchronous: make that call before any capture of
+ * `stream`) and caches the fastest in the context.  The choice used is
+ * written back to *particles_per_thread if non-NULL.
+ * workspace: device, >= afm_invert_batch_workspace_size(n_pix), 256-aligned. */
+afm_status afm_invert_batch_workspace_size(int n_pix, size_t* bytes);
+afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
+                            const int64_t* off, int n_pix, uint32_t pixel0,
+                            const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
+                            afm_result* results, int* particles_per_thread, void* stream);
+
 /* ---- inversion without any device allocation ----------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory at all, such as a real-time AFM feedback

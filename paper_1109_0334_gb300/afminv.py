@@ -97,6 +97,10 @@ def lib():
                                                     C.POINTER(C.c_size_t)]
             L.afm_invert.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), vp,
                                      C.c_size_t, vp, vp, vp]
+            L.afm_invert_batch_workspace_size.argtypes = [i, C.POINTER(C.c_size_t)]
+            L.afm_invert_batch.argtypes = [vp, C.POINTER(Problem), vp, vp, i, u32,
+                                           C.POINTER(PsoCfg), vp, C.c_size_t, vp,
+                                           C.POINTER(C.c_int), vp]
             L.afm_invert_noalloc.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), vp,
                                              vp, vp]
             L.afm_synth_records.argtypes = [vp, C.POINTER(Problem), vp, i, vp, i, d, u64, u32,
@@ -290,6 +294,39 @@ def invert(prob: Problem, U, cfg: PsoCfg, workspace=None, result=None, history=N
                             _ptr(workspace), C.c_size_t(workspace.numel()), _ptr(result),
                             _ptr(history), _stream(stream)))
     return result, history
+
+
+def invert_batch_workspace_size(n_pix: int) -> int:
+    n = C.c_size_t()
+    _check(lib().afm_invert_batch_workspace_size(int(n_pix), C.byref(n)))
+    return int(n.value)
+
+
+def invert_batch(prob: Problem, U_cat, off, cfg: PsoCfg, pixel0: int = 0,
+                 particles_per_thread: int = 0, workspace=None, results=None, stream=None):
+    """Many pixel inversions in one graph launch.  U_cat float32 CUDA [sum n_i],
+    off int64 CUDA [n_pix + 1].  Returns (results uint8 [n_pix, sizeof(afm_result)],
+    particles per thread used)."""
+    import torch
+    dev = U_cat.device
+    n_pix = int(off.shape[0]) - 1
+    nbytes = invert_batch_workspace_size(n_pix)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    if results is None:
+        results = torch.zeros((n_pix, C.sizeof(Result)), dtype=torch.uint8, device=dev)
+    kp = C.c_int(int(particles_per_thread))
+    _check(lib().afm_invert_batch(context(dev.index), C.byref(prob), _ptr(U_cat), _ptr(off), n_pix,
+                                  int(pixel0), C.byref(cfg), _ptr(workspace),
+                                  C.c_size_t(workspace.numel()), _ptr(results), C.byref(kp),
+                                  _stream(stream)))
+    return results, kp.value
+
+
+def decode_results(results) -> list:
+    """Host copies of an [n_pix] array of afm_result (uint8 tensor)."""
+    raw = results.cpu().numpy().reshape(-1, C.sizeof(Result))
+    return [decode_result(bytes(r.tobytes())) for r in raw]
 
 
 def invert_noalloc(prob: Problem, U, cfg: PsoCfg, result, history=None, stream=None):

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "afm_internal.h"
+#include "afm_launch.h"
 
 namespace afm {
 
@@ -271,5 +272,65 @@ __device__ __forceinline__ T integrate(const KConst<T>& K, const Coef<T>& c, con
     }
     return S;
 }
+
+// K particles per thread sharing the record and drive loads: the K
+// independent RK4 recurrences interleave in one instruction stream, which
+// hides the dependency latency of each.  Arithmetic per particle is the same
+// as integrate() (misfit only).
+template <int M, int FORCE, int K>
+__device__ __forceinline__ void integrate_multi(const KConst<float>& Kc, const Coef<float>* c,
+                                                const float* tab, const float* __restrict__ U,
+                                                int n, float* S_out) {
+    float q[K][M], v[K][M], cq[K][M], cv[K][M];
+    float S[K], cS[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        init_state<float, M>(Kc, q[k], v[k], cq[k], cv[k]);
+        S[k] = 0.f;
+        cS[k] = 0.f;
+    }
+    int j = 0;
+    const int spc2 = Kc.spc2;
+    float Un = n > 0 ? U[0] : 0.f;
+    for (int s = 0; s < n; ++s) {
+        float g0 = tab[j], gh = tab[j + 1], g1 = tab[j + 2];
+        j += 2;
+        if (j >= spc2) j = 0;
+        float Unext = s + 1 < n ? U[s + 1] : 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            rk4_step<float, M, FORCE>(Kc, c[k], q[k], v[k], cq[k], cv[k], g0, gh, g1);
+            float u = tip_sum<float, M>(q[k]);
+            float r = Un - u;
+            float y = fmaf(r, r, -cS[k]);
+            float t = add_rn(S[k], y);
+            cS[k] = sub_rn(sub_rn(t, S[k]), y);
+            S[k] = t;
+        }
+        Un = Unext;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) S_out[k] = S[k];
+}
+
+// Eq. 8 for particle p at iteration it (>= 1): r1, r2 per dimension are words
+// 2d and 2d+1 (mod 4) of counter (p, it, pixel, 2<<16 | d/2).
+__device__ __forceinline__ void pso_move_dev(const PsoConst& pc, float* x, float* v, const float* pb,
+                                         const float* gb, int p, int it) {
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (int d = 0; d < pc.D; ++d) {
+        if ((d & 1) == 0) w = philox_draw(pc.seed, (uint32_t)p, (uint32_t)it, pc.pixel, 2u, (uint32_t)(d >> 1));
+        const int k = (2 * d) & 3;
+        const float r1 = unif24(word_of(w, k)), r2 = unif24(word_of(w, k + 1));
+        // explicit FMAs: the same rounding wherever this is inlined
+        float vn = fmaf(pc.c2 * r2, gb[d] - x[d], fmaf(pc.c1 * r1, pb[d] - x[d], pc.w * v[d]));
+        float xn = x[d] + vn;
+        if (xn < 0.f) { xn = 0.f; vn = 0.f; }
+        if (xn > 1.f) { xn = 1.f; vn = 0.f; }
+        x[d] = xn;
+        v[d] = vn;
+    }
+}
+
 
 }  // namespace afm

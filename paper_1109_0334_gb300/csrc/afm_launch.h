@@ -5,6 +5,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/afminv.h"
 #include "afm_internal.h"
 
 namespace afm {
@@ -37,6 +38,26 @@ cudaError_t launch_misfit(const float* defl, const float* U, int N, int P, float
 cudaError_t launch_synth(const KConst<float>& K, const double* x_truth, int n_pix,
                          const int64_t* off, int sub, float sigma_nm, uint64_t seed,
                          uint32_t pixel0, float* U_cat, cudaStream_t st);
+
+// many independent pixel inversions in one persistent launch
+struct BatchArgs {
+    const float* U;        // concatenated records
+    const int64_t* off;    // [n_pix + 1]
+    const int* order;      // queue order of pixels (longest first) or nullptr
+    int n_pix;
+    uint32_t pixel0;       // Philox counter word 2 of pixel 0
+    int* queue;            // pixel counter (zeroed before the launch)
+    afm_result* res;       // [n_pix]
+};
+int batch_threads(int P, int kp);
+size_t batch_smem(int P, int D, int spc2);
+int batch_sort_max();
+cudaError_t batch_sort(const int64_t* off, int n_pix, int* order, cudaStream_t st);
+cudaError_t batch_occupancy(int m, int force, int kp, int P, int D, int spc2, int* blocks_per_sm);
+cudaError_t launch_batch(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a, int kp,
+                         int grid, cudaStream_t st);
+cudaError_t launch_batch_final(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
+                               cudaStream_t st);
 
 // particle swarm
 cudaError_t launch_pso_init(const PsoConst& pc, const SwarmPtrs& sw, cudaStream_t st);

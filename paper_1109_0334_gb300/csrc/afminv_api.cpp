@@ -7,6 +7,7 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -16,11 +17,25 @@
 
 using afm::KConst;
 
+#include <map>
+#include <tuple>
 #include <vector>
+
+// One instantiated launch graph of afm_invert_batch and the argument bytes it
+// was built from.
+struct afm_batch_graph {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec;
+};
 
 struct afm_ctx {
     int device;
     int num_sms;
+    // afm_invert_batch: particles per thread chosen by the autotuner, per
+    // (modes, force, particles, free parameters, steps per cycle)
+    std::map<std::tuple<int, int, int, int, int>, int> batch_kp;
+    cudaStream_t capture_stream = nullptr;
+    std::vector<afm_batch_graph> batch_graphs;
     // kernel timing (afm_profile_*): events around each fused iteration launch
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;   // reusable events
@@ -295,6 +310,77 @@ InvLayout invert_layout(int P, int D) {
     return L;
 }
 
+struct BatchLayout {
+    size_t order, queue, total;
+};
+
+BatchLayout batch_layout(int n_pix) {
+    BatchLayout L;
+    L.order = 0;
+    L.queue = align256(sizeof(int) * (size_t)n_pix);
+    L.total = L.queue + 256;
+    return L;
+}
+
+template <typename T>
+void append_bytes(std::vector<unsigned char>& v, const T& x) {
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&x);
+    v.insert(v.end(), p, p + sizeof(T));
+}
+
+// Autotuner of afm_invert_batch: times one swarm evaluation of the first wave
+// of pixels for each particles-per-thread choice and keeps the fastest.
+afm_status batch_tune(afm_ctx* ctx, const KConst<float>& Kf, const afm::PsoConst& pc,
+                      const afm::BatchArgs& a, cudaStream_t s, int* kp_out, int* occ_out) {
+    const auto key = std::make_tuple(Kf.m, Kf.force, pc.P, pc.D, Kf.spc2);
+    auto it = ctx->batch_kp.find(key);
+    if (it != ctx->batch_kp.end()) {
+        *kp_out = it->second;
+        AFM_CUDA(afm::batch_occupancy(Kf.m, Kf.force, *kp_out, pc.P, pc.D, Kf.spc2, occ_out),
+                 "batch occupancy");
+        return AFM_OK;
+    }
+    float best_ms = 1e30f;
+    int best_kp = 0, best_occ = 0;
+    cudaEvent_t e0, e1;
+    AFM_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    AFM_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    for (int kp : {1, 2, 4}) {
+        const int threads = afm::batch_threads(pc.P, kp);
+        if (threads > 1024 || (kp > 1 && Kf.m > 3)) continue;
+        int occ = 0;
+        if (afm::batch_occupancy(Kf.m, Kf.force, kp, pc.P, pc.D, Kf.spc2, &occ) != cudaSuccess ||
+            occ < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        afm::PsoConst probe = pc;
+        probe.iters = 0;
+        afm::BatchArgs pa = a;
+        pa.n_pix = std::min(a.n_pix, ctx->num_sms * occ);
+        const int grid = pa.n_pix;
+        AFM_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), s), "cudaMemsetAsync");
+        AFM_CUDA(cudaEventRecord(e0, s), "cudaEventRecord");
+        AFM_CUDA(afm::launch_batch(Kf, probe, pa, kp, grid, s), "batch probe kernel");
+        AFM_CUDA(cudaEventRecord(e1, s), "cudaEventRecord");
+        AFM_CUDA(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float ms = 0.f;
+        AFM_CUDA(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_kp = kp;
+            best_occ = occ;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_kp == 0) return fail(AFM_ERR_UNSUPPORTED, "no batch kernel configuration fits P = %d", pc.P);
+    ctx->batch_kp[key] = best_kp;
+    *kp_out = best_kp;
+    *occ_out = best_occ;
+    return AFM_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -380,6 +466,8 @@ afm_status afm_ctx_destroy(afm_ctx* ctx) {
             cudaEventDestroy(pr.second);
         }
         for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+        for (auto& g : ctx->batch_graphs) cudaGraphExecDestroy(g.exec);
+        if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     }
     delete ctx;
     return AFM_OK;
@@ -556,6 +644,106 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
         AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_invert_iter(Kf, pc, sw, U, history, it, s); }),
                  "invert iteration kernel");
     AFM_CUDA(afm::launch_invert_final(Kd, pc, sw, U, history, result, s), "invert final kernel");
+    return AFM_OK;
+}
+
+afm_status afm_invert_batch_workspace_size(int n_pix, size_t* bytes) {
+    g_err[0] = 0;
+    if (!bytes || n_pix < 1) return fail(AFM_ERR_INVALID_ARG, "n_pix >= 1 and bytes needed");
+    *bytes = batch_layout(n_pix).total;
+    return AFM_OK;
+}
+
+afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
+                            const int64_t* off, int n_pix, uint32_t pixel0,
+                            const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
+                            afm_result* results, int* particles_per_thread, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if ((st = check_pso(cfg, prob->n_free))) return st;
+    if (!U_cat || !off || !results || !workspace || n_pix < 1)
+        return fail(AFM_ERR_INVALID_ARG, "NULL U_cat, off, results or workspace, or n_pix < 1");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256)
+        return fail(AFM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    const BatchLayout L = batch_layout(n_pix);
+    if (workspace_bytes < L.total)
+        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, L.total);
+    if (cfg->P > 4096) return fail(AFM_ERR_INVALID_ARG, "batched swarms hold at most 4096 particles");
+    const size_t smem = afm::batch_smem(cfg->P, prob->n_free, 2 * prob->steps_per_cycle);
+    if (smem > 200 * 1024)
+        return fail(AFM_ERR_INVALID_ARG, "swarm state of %zu bytes exceeds shared memory", smem);
+    char* ws = static_cast<char*>(workspace);
+    KConst<float> Kf;
+    KConst<double> Kd;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kf);
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kd);
+    const afm::PsoConst pc = pso_const(*cfg, prob->n_free);
+    afm::BatchArgs a;
+    a.U = U_cat;
+    a.off = off;
+    a.order = n_pix <= afm::batch_sort_max() ? reinterpret_cast<int*>(ws + L.order) : nullptr;
+    a.n_pix = n_pix;
+    a.pixel0 = pixel0;
+    a.queue = reinterpret_cast<int*>(ws + L.queue);
+    a.res = results;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // queue order (longest record first) is needed by the tuner's probe too
+    if (a.order) AFM_CUDA(afm::batch_sort(off, n_pix, const_cast<int*>(a.order), s), "sort kernel");
+    int kp = 0, occ = 0;
+    const int want = particles_per_thread ? *particles_per_thread : 0;
+    if (want == 1 || want == 2 || want == 4) {
+        if (afm::batch_threads(pc.P, want) > 1024 || (want > 1 && Kf.m > 3))
+            return fail(AFM_ERR_INVALID_ARG, "particles_per_thread %d unsupported here", want);
+        kp = want;
+        AFM_CUDA(afm::batch_occupancy(Kf.m, Kf.force, kp, pc.P, pc.D, Kf.spc2, &occ), "batch occupancy");
+        if (occ < 1) return fail(AFM_ERR_UNSUPPORTED, "batch kernel does not fit (P = %d)", pc.P);
+    } else if (want != 0) {
+        return fail(AFM_ERR_INVALID_ARG, "particles_per_thread must be 0 (tune), 1, 2 or 4");
+    } else if ((st = batch_tune(ctx, Kf, pc, a, s, &kp, &occ))) {
+        return st;
+    }
+    const int grid = std::min(n_pix, ctx->num_sms * occ);
+    if (particles_per_thread) *particles_per_thread = kp;
+    // one graph: zero the queue, sort, persistent swarm kernel, FP64 winners
+    std::vector<unsigned char> key;
+    append_bytes(key, Kf);
+    append_bytes(key, Kd);
+    append_bytes(key, pc);
+    append_bytes(key, a);
+    append_bytes(key, kp);
+    append_bytes(key, grid);
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : ctx->batch_graphs)
+        if (g.key == key) exec = g.exec;
+    if (!exec) {
+        if (!ctx->capture_stream)
+            AFM_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking),
+                     "cudaStreamCreate");
+        cudaStream_t c = ctx->capture_stream;
+        AFM_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), c);
+        if (e == cudaSuccess && a.order) e = afm::batch_sort(off, n_pix, const_cast<int*>(a.order), c);
+        if (e == cudaSuccess) e = afm::launch_batch(Kf, pc, a, kp, grid, c);
+        if (e == cudaSuccess) e = afm::launch_batch_final(Kd, pc, a, c);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(c, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e, "batch graph capture");
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (ctx->batch_graphs.size() >= 8) {
+            cudaGraphExecDestroy(ctx->batch_graphs.front().exec);
+            ctx->batch_graphs.erase(ctx->batch_graphs.begin());
+        }
+        ctx->batch_graphs.push_back({key, exec});
+    }
+    AFM_CUDA(cudaGraphLaunch(exec, s), "cudaGraphLaunch");
     return AFM_OK;
 }
 

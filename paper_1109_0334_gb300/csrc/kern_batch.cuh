@@ -1,0 +1,261 @@
+// kern_batch.cuh -- kernels of the batched pixel inversion (see
+// kern_batch.cu); instantiated per force law in kern_batch_*.cu so that the
+// translation units compile in parallel.
+#pragma once
+#include "../../include/afminv.h"
+#include "afm_device.cuh"
+#include "afm_launch.h"
+
+namespace afm {
+
+namespace batch_detail {
+
+__device__ __forceinline__ unsigned long long bkey(float S, int p) {
+    return ((unsigned long long)__float_as_uint(S) << 32) | (unsigned)p;
+}
+
+__device__ __forceinline__ unsigned long long warp_min(unsigned long long k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_xor_sync(0xffffffffu, k, o);
+        k = other < k ? other : k;
+    }
+    return k;
+}
+
+}  // namespace batch_detail
+
+// ---------------------------------------------------------------------------
+// Persistent swarm kernel.
+// ---------------------------------------------------------------------------
+template <int M, int FORCE, int KP>
+__global__ void __launch_bounds__(1024) batch_kernel(const KConst<float> K, const PsoConst pc,
+                                                     const BatchArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    const int P = pc.P, D = pc.D;
+    float* tab = sm;
+    float* sx = sm + ((K.spc2 + 1 + 3) & ~3);
+    float* sv = sx + D * P;
+    float* spb = sv + D * P;
+    __shared__ unsigned long long wkey[32];
+    __shared__ unsigned long long s_gkey;
+    __shared__ int s_slot, s_bad;
+    build_drive_table(K, tab);
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = T >> 5;
+    for (;;) {
+        __syncthreads();   // table built / previous pixel finished with shared memory
+        if (tid == 0) {
+            s_slot = atomicAdd(a.queue, 1);
+            s_bad = 0;
+        }
+        __syncthreads();
+        const int slot = s_slot;
+        if (slot >= a.n_pix) return;
+        const int pix = a.order != nullptr ? a.order[slot] : slot;
+        const int64_t o = a.off[pix];
+        const int n = (int)(a.off[pix + 1] - o);
+        const float* U = a.U + o;
+        PsoConst pcp = pc;
+        pcp.pixel = a.pixel0 + (uint32_t)pix;
+
+        // initial swarm (tags 0 and 1), as pso_init_kernel
+        float pbS[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const int p = tid + k * T;
+            pbS[k] = INFINITY;
+            if (p >= P) continue;
+            for (int b = 0; b * 4 < D; ++b) {
+                uint4 w0 = philox_draw(pcp.seed, (uint32_t)p, 0u, pcp.pixel, 0u, (uint32_t)b);
+                uint4 w1 = philox_draw(pcp.seed, (uint32_t)p, 0u, pcp.pixel, 1u, (uint32_t)b);
+                for (int q = 0; q < 4 && b * 4 + q < D; ++q) {
+                    const int d = b * 4 + q;
+                    const float u0 = unif24(word_of(w0, q)), u1 = unif24(word_of(w1, q));
+                    sx[d * P + p] = u0;
+                    sv[d * P + p] = (u1 - u0) * 0.5f;
+                }
+            }
+        }
+        for (int it = 0; it <= pc.iters; ++it) {
+            if (it > 0) {
+                const int g = min((int)(s_gkey & 0x7fffffffu), P - 1);
+#pragma unroll
+                for (int k = 0; k < KP; ++k) {
+                    const int p = tid + k * T;
+                    if (p >= P) continue;
+                    float x[AFM_MAXD], v[AFM_MAXD], pb[AFM_MAXD], gb[AFM_MAXD];
+                    for (int d = 0; d < D; ++d) {
+                        x[d] = sx[d * P + p];
+                        v[d] = sv[d * P + p];
+                        pb[d] = spb[d * P + p];
+                        gb[d] = spb[d * P + g];
+                    }
+                    pso_move_dev(pcp, x, v, pb, gb, p, it);
+                    for (int d = 0; d < D; ++d) {
+                        sx[d * P + p] = x[d];
+                        sv[d * P + p] = v[d];
+                    }
+                }
+                __syncthreads();   // every read of the global best precedes any personal-best write
+            }
+            Coef<float> c[KP];
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const int p = min(tid + k * T, P - 1);
+                float x[AFM_MAXD];
+                for (int d = 0; d < D; ++d) x[d] = sx[d * P + p];
+                c[k] = make_coef<float, float>(K, x);
+            }
+            float S[KP];
+            integrate_multi<M, FORCE, KP>(K, c, tab, U, n, S);
+            unsigned long long key = ~0ull;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const int p = tid + k * T;
+                if (p >= P) continue;
+                float s = S[k];
+                if (!(s < INFINITY)) {
+                    atomicAdd(&s_bad, 1);
+                    s = INFINITY;
+                } else if (!(s > 0.f)) {
+                    s = 0.f;
+                }
+                if (s < pbS[k] || it == 0) {
+                    pbS[k] = fminf(s, pbS[k]);
+                    for (int d = 0; d < D; ++d) spb[d * P + p] = sx[d * P + p];
+                }
+                const unsigned long long kk = batch_detail::bkey(pbS[k], p);
+                key = kk < key ? kk : key;
+            }
+            key = batch_detail::warp_min(key);
+            if (lane == 0) wkey[warp] = key;
+            __syncthreads();
+            if (warp == 0) {
+                unsigned long long k2 = lane < nwarps ? wkey[lane] : ~0ull;
+                k2 = batch_detail::warp_min(k2);
+                if (lane == 0) s_gkey = k2;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const int g = min((int)(s_gkey & 0x7fffffffu), P - 1);
+            afm_result* r = a.res + pix;
+            for (int d = 0; d < AFM_MAXD; ++d) r->x[d] = d < D ? (double)spb[d * P + g] : 0.0;
+            r->S = (double)__uint_as_float((uint32_t)(s_gkey >> 32));
+            r->iters = pc.iters;
+            r->winner = g;
+            r->nonfinite = s_bad;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 re-evaluation of every pixel's winner: one thread per pixel, pixels
+// taken in queue order so that a warp holds records of similar length.
+// ---------------------------------------------------------------------------
+template <int M, int FORCE>
+__global__ void batch_final_kernel(const KConst<double> K, const PsoConst pc, const BatchArgs a) {
+    extern __shared__ __align__(16) double smd[];
+    build_drive_table(K, smd);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_pix) return;
+    const int pix = a.order != nullptr ? a.order[i] : i;
+    const int64_t o = a.off[pix];
+    const int n = (int)(a.off[pix + 1] - o);
+    const float* U = a.U + o;
+    afm_result* r = a.res + pix;
+    double xd[AFM_MAXD];
+    for (int d = 0; d < AFM_MAXD; ++d) xd[d] = r->x[d];
+    Coef<double> c = make_coef<double, double>(K, xd);
+    const double S64 = integrate<double, M, FORCE, float>(K, c, smd, U, nullptr, 0, 0, n);
+    double u2 = 0.0;
+    for (int s = 0; s < n; ++s) u2 += (double)U[s] * (double)U[s];
+    double th[AFM_MAXD];
+    for (int s = 0; s < AFM_MAXD; ++s) th[s] = K.fixed[s];
+    for (int d = 0; d < pc.D; ++d) {
+        double v = K.lo[d] + xd[d] * K.span[d];
+        th[K.slot[d]] = K.logs[d] ? exp10(v) : v;
+    }
+    for (int s = 0; s < AFM_MAXD; ++s) r->theta[s] = th[s];
+    r->S_f64 = S64;
+    r->J_rel = u2 > 0.0 ? sqrt(S64 / u2) : 0.0;
+    r->status = (isfinite(S64) && r->nonfinite == 0) ? AFM_OK : AFM_ERR_NONFINITE;
+}
+
+
+// Launch helpers of one force law (explicitly instantiated per force).
+template <int FORCE>
+struct BatchOps {
+    template <typename F>
+    static cudaError_t by_mk(int m, int kp, F&& f) {
+        if (m == 1) {
+            switch (kp) {
+                case 1: return f(std::integral_constant<int, 1>{}, std::integral_constant<int, 1>{});
+                case 2: return f(std::integral_constant<int, 1>{}, std::integral_constant<int, 2>{});
+                case 4: return f(std::integral_constant<int, 1>{}, std::integral_constant<int, 4>{});
+            }
+        } else if (m == 3) {
+            switch (kp) {
+                case 1: return f(std::integral_constant<int, 3>{}, std::integral_constant<int, 1>{});
+                case 2: return f(std::integral_constant<int, 3>{}, std::integral_constant<int, 2>{});
+                case 4: return f(std::integral_constant<int, 3>{}, std::integral_constant<int, 4>{});
+            }
+        } else if (kp == 1) {
+            return f(std::integral_constant<int, AFM_MAXM>{}, std::integral_constant<int, 1>{});
+        }
+        return cudaErrorInvalidValue;
+    }
+
+    static cudaError_t occupancy(int m, int kp, int P, int D, int spc2, int* blocks) {
+        const int threads = batch_threads(P, kp);
+        const size_t smem = batch_smem(P, D, spc2);
+        return by_mk(m, kp, [&](auto Mc, auto Kc) -> cudaError_t {
+            auto kern = batch_kernel<decltype(Mc)::value, FORCE, decltype(Kc)::value>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, threads, smem);
+        });
+    }
+
+    static cudaError_t launch(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a, int kp,
+                              int grid, cudaStream_t st) {
+        const int threads = batch_threads(pc.P, kp);
+        const size_t smem = batch_smem(pc.P, pc.D, K.spc2);
+        return by_mk(K.m, kp, [&](auto Mc, auto Kc) -> cudaError_t {
+            auto kern = batch_kernel<decltype(Mc)::value, FORCE, decltype(Kc)::value>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            kern<<<grid, threads, smem, st>>>(K, pc, a);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t final_(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
+                              cudaStream_t st) {
+        const size_t smem = sizeof(double) * (size_t)(K.spc2 + 1);
+        const int threads = 32;
+        const int blocks = (a.n_pix + threads - 1) / threads;
+        return by_mk(K.m, 1, [&](auto Mc, auto) -> cudaError_t {
+            auto kern = batch_final_kernel<decltype(Mc)::value, FORCE>;
+            if (smem > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(
+                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            kern<<<blocks, threads, smem, st>>>(K, pc, a);
+            return cudaGetLastError();
+        });
+    }
+};
+
+extern template struct BatchOps<F_LINEAR>;
+extern template struct BatchOps<F_DMT>;
+extern template struct BatchOps<F_DMT_KV>;
+extern template struct BatchOps<F_HOOKE>;
+extern template struct BatchOps<F_SPRING_DAMPER>;
+
+}  // namespace afm

@@ -53,24 +53,6 @@ __device__ __forceinline__ void warp_min_atomic(unsigned long long key, unsigned
     if ((threadIdx.x & 31) == 0) atomicMin(dst, key);
 }
 
-// Eq. 8 for particle p at iteration it (>= 1): r1, r2 per dimension are words
-// 2d and 2d+1 (mod 4) of counter (p, it, pixel, 2<<16 | d/2).
-__device__ __forceinline__ void pso_move(const PsoConst& pc, float* x, float* v, const float* pb,
-                                         const float* gb, int p, int it) {
-    uint4 w = make_uint4(0, 0, 0, 0);
-    for (int d = 0; d < pc.D; ++d) {
-        if ((d & 1) == 0) w = philox_draw(pc.seed, (uint32_t)p, (uint32_t)it, pc.pixel, 2u, (uint32_t)(d >> 1));
-        const int k = (2 * d) & 3;
-        const float r1 = unif24(word_of(w, k)), r2 = unif24(word_of(w, k + 1));
-        float vn = pc.w * v[d] + pc.c1 * r1 * (pb[d] - x[d]) + pc.c2 * r2 * (gb[d] - x[d]);
-        float xn = x[d] + vn;
-        if (xn < 0.f) { xn = 0.f; vn = 0.f; }
-        if (xn > 1.f) { xn = 1.f; vn = 0.f; }
-        x[d] = xn;
-        v[d] = vn;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Swarm initialisation: x ~ U[0,1), v = (U[0,1) - x)/2 (tags 0 and 1).
 // ---------------------------------------------------------------------------
@@ -135,7 +117,7 @@ __global__ void pso_move_kernel(const PsoConst pc, SwarmPtrs sw, int it) {
         pb[d] = sw.pb[0][q + p];
         gb[d] = sw.pb[0][q + g];
     }
-    pso_move(pc, x, v, pb, gb, p, it);
+    pso_move_dev(pc, x, v, pb, gb, p, it);
     for (int d = 0; d < pc.D; ++d) {
         sw.x[(size_t)d * pc.P + p] = x[d];
         sw.v[(size_t)d * pc.P + p] = v[d];
@@ -189,7 +171,7 @@ __global__ void invert_iter_kernel(const KConst<float> K, const PsoConst pc, Swa
                 pb[d] = pb_rd[(size_t)d * pc.P + p];
                 gb[d] = pb_rd[(size_t)d * pc.P + g];
             }
-            pso_move(pc, x, v, pb, gb, p, it);
+            pso_move_dev(pc, x, v, pb, gb, p, it);
             for (int d = 0; d < pc.D; ++d) {
                 sw.x[(size_t)d * pc.P + p] = x[d];
                 sw.v[(size_t)d * pc.P + p] = v[d];
