@@ -117,8 +117,10 @@ def measured_peaks() -> dict:
 
 
 KERNEL_SOURCES = {
-    "invert_iter_kernel": ["afm_device.cuh", "afm_internal.h", "kern_invert.cu"],
-    "fwd_kernel": ["afm_device.cuh", "afm_internal.h", "kern_forward.cu"],
+    "invert_iter_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_invert.cu"],
+    "fwd_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_forward.cu"],
+    "batch_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_batch.cuh",
+                     "kern_batch.cu", "kern_batch_dmt.cu"],
 }
 
 
@@ -210,6 +212,59 @@ def oracle_sample(spec, target_cpu_s: float = 12.0, max_evals: int = 50):
             f"OpenMP over particles) = {evals}/{spec['iters'] + 1} of one inversion; "
             f"{wall:.2f} s wall")
     return rate, threads, desc, wall / evals
+
+
+# ---------------------------------------------------------------------------
+# Batched pixel inversions (4096 independent inversions, one graph launch)
+# ---------------------------------------------------------------------------
+def c3_inputs(A, W, dev, n_pix=None, cycles_div=1):
+    """Seeded truths and record lengths (20..200 cycles) of the batched
+    workload, records made on the GPU (FP32 at dt/4 + noise)."""
+    import numpy as np
+    import torch
+    spec = W.get("c3")
+    n_pix = spec["n_pix"] if n_pix is None else n_pix
+    D = len(spec["free"])
+    rng = np.random.default_rng(spec["seed"])
+    cyc = rng.integers(20, 201, size=n_pix) // cycles_div
+    cyc = np.maximum(cyc, 1)
+    lens = cyc * spec["spc"]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    xt = rng.uniform(0.1, 0.9, size=(D, n_pix))
+    prob = A.make_problem(spec, n_steps=int(lens.max()))
+    off_d = torch.from_numpy(off).to(dev)
+    U = A.synth_records(prob, torch.from_numpy(xt).to(dev), off_d, spec["record_sub"],
+                        spec["sigma"], spec["seed"], 0)
+    return spec, prob, U, off_d, int(lens.sum()), xt
+
+
+def run_c3(A, W, dev, peak_ops, flush):
+    import torch
+    spec, prob, U, off, total_steps, _ = c3_inputs(A, W, dev)
+    cfg = A.make_pso(spec)
+    n_pix = spec["n_pix"]
+    res, kp = A.invert_batch(prob, U, off, cfg)   # autotune + graph capture + warm-up
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res, kp = A.invert_batch(prob, U, off, cfg, results=res)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    units = spec["P"] * (spec["iters"] + 1) * total_steps
+    out = A.decode_results(res)
+    ok = sum(1 for r in out if r["status"] == 0)
+    ops = units * fp32_ops_per_step(spec["n_modes"], spec["force"])
+    return {"workload": "c3: 4096 pixels, 20..200 cycles x 256 steps, 256 particles x 60 updates",
+            "pixels": n_pix, "record_steps_total": total_steps, "particle_steps": units,
+            "ms": ms, "value": units / (ms / 1e3), "unit": UNIT,
+            "ms_per_pixel_inversion": ms / n_pix, "particles_per_thread": kp,
+            "pixels_ok": ok,
+            "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e12,
+                         "peak": peak_ops / 1e12, "unit": "T FP32 lane-ops/s",
+                         "frac": ops / (ms / 1e3) / peak_ops,
+                         "note": "whole graph (swarm kernel + FP64 winners), one timed replay"}}
 
 
 # ---------------------------------------------------------------------------
@@ -345,7 +400,11 @@ def run_ours(args):
                    "value": Pb * N / ((ms_b / n_b) / 1e3), "unit": UNIT,
                    "roofline": {"bound": "alu", "achieved": ach_b / 1e12, "peak": peak_ops / 1e12,
                                 "unit": "T FP32 lane-ops/s", "frac": ach_b / peak_ops,
-                                "traffic": ncu_traffic("fwd_kernel", "c2_batched")}}
+                                                "traffic": ncu_traffic("fwd_kernel", "c2_batched")}}
+
+    c3 = None
+    if not args.no_c3:
+        c3 = run_c3(A, W, dev, peak_ops, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -371,6 +430,7 @@ def run_ours(args):
                        "x": list(r["x"][:D]), "x_truth": list(x_truth[:, 0]),
                        "status": r["status"], "theta": list(theta)},
             "batched_forward": batched,
+            "batched_inversion": c3,
         }
         print(json.dumps(out))
     if world > 1:
@@ -424,6 +484,18 @@ def run_probe(args):
     from paper_1109_0334_gb300 import afminv as A
     from paper_1109_0334_gb300 import workloads as W
 
+    if args.probe == "batch":
+        # one wave of pixels with records shortened tenfold, --probe-iters updates
+        props = torch.cuda.get_device_properties(0)
+        spec, prob, U, off, total, _ = c3_inputs(A, W, torch.device("cuda"),
+                                                 n_pix=props.multi_processor_count * 4,
+                                                 cycles_div=10)
+        cfg = A.make_pso(dict(spec, iters=args.probe_iters))
+        res, kp = A.invert_batch(prob, U, off, cfg)
+        torch.cuda.synchronize()
+        out = A.decode_results(res)
+        print(json.dumps({"pixels": len(out), "kp": kp, "ok": sum(r["status"] == 0 for r in out)}))
+        return
     spec = W.get(args.workload, iters=args.probe_iters)
     D = len(spec["free"])
     N = W.n_steps(spec)
@@ -454,7 +526,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the wide forward launch")
-    ap.add_argument("--probe", choices=["invert", "forward"], default=None,
+    ap.add_argument("--no-c3", action="store_true", help="skip the 4096-pixel batched inversion")
+    ap.add_argument("--probe", choices=["invert", "forward", "batch"], default=None,
                     help="run one small untimed case for a profiler capture and exit")
     ap.add_argument("--probe-iters", type=int, default=2)
     ap.add_argument("--probe-particles", type=int, default=32768)
