@@ -203,6 +203,20 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
                       const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
                       afm_result* result, float* history, void* stream);
 
+/* ---- gradient of the misfit (discrete adjoint) --------------------------
+ * For P parameter sets x [D][P] (device, normalised): S [P] (as
+ * afm_forward_batch) and dS_dx [D][P] = d S / d x, the exact derivative of the
+ * FP32 RK4 recurrence (Eq. 2, Sec. 3.2) and compensated sum (Eq. 5), by the
+ * discrete adjoint: the state is checkpointed every 32 steps and each
+ * 32-step segment is recomputed during the reverse sweep.  The Kahan
+ * compensation is treated as exact addition.  workspace: device,
+ * >= afm_adjoint_workspace_size (the checkpoints: ceil(n_steps/32) x 4 x
+ * modes x P floats). */
+afm_status afm_adjoint_workspace_size(const afm_problem* prob, int P, size_t* bytes);
+afm_status afm_adjoint(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
+                       const float* U, float* S, float* dS_dx, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
 /* ---- many pixel inversions in one launch (image scans) -------------------
  * n_pix independent IPs, pixel i with record U_cat[off[i] .. off[i+1]) (its
  * own length; prob->n_steps is only validated, not used) and Philox counter

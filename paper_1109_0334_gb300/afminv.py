@@ -97,6 +97,8 @@ def lib():
                                                     C.POINTER(C.c_size_t)]
             L.afm_invert.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), vp,
                                      C.c_size_t, vp, vp, vp]
+            L.afm_adjoint_workspace_size.argtypes = [C.POINTER(Problem), i, C.POINTER(C.c_size_t)]
+            L.afm_adjoint.argtypes = [vp, C.POINTER(Problem), vp, i, vp, vp, vp, vp, C.c_size_t, vp]
             L.afm_invert_batch_workspace_size.argtypes = [i, C.POINTER(C.c_size_t)]
             L.afm_invert_batch.argtypes = [vp, C.POINTER(Problem), vp, vp, i, u32,
                                            C.POINTER(PsoCfg), vp, C.c_size_t, vp,
@@ -294,6 +296,61 @@ def invert(prob: Problem, U, cfg: PsoCfg, workspace=None, result=None, history=N
                             _ptr(workspace), C.c_size_t(workspace.numel()), _ptr(result),
                             _ptr(history), _stream(stream)))
     return result, history
+
+
+def adjoint_workspace_size(prob: Problem, P: int) -> int:
+    n = C.c_size_t()
+    _check(lib().afm_adjoint_workspace_size(C.byref(prob), int(P), C.byref(n)))
+    return int(n.value)
+
+
+def adjoint(prob: Problem, x, U, workspace=None, stream=None):
+    """Misfit S [P] and its gradient dS/dx [D, P] for x float32 CUDA [D, P]
+    (discrete adjoint of the FP32 RK4 + compensated misfit)."""
+    import torch
+    D, P = int(x.shape[0]), int(x.shape[1])
+    dev = x.device
+    nbytes = adjoint_workspace_size(prob, P)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    S = torch.empty(P, dtype=torch.float32, device=dev)
+    G = torch.empty((D, P), dtype=torch.float32, device=dev)
+    _check(lib().afm_adjoint(context(dev.index), C.byref(prob), _ptr(x), P, _ptr(U), _ptr(S),
+                             _ptr(G), _ptr(workspace), C.c_size_t(workspace.numel()),
+                             _stream(stream)))
+    return S, G
+
+
+def _misfit_function():
+    import torch
+
+    class Misfit(torch.autograd.Function):
+        """S(x) with the adjoint gradient: forward runs afm_adjoint (misfit and
+        gradient in one pass), backward scales the stored gradient."""
+
+        @staticmethod
+        def forward(ctx, x, prob, U):
+            S, G = adjoint(prob, x.detach().contiguous(), U)
+            ctx.save_for_backward(G)
+            return S
+
+        @staticmethod
+        def backward(ctx, gS):
+            (G,) = ctx.saved_tensors
+            return G * gS.unsqueeze(0), None, None
+
+    return Misfit
+
+
+_MISFIT = None
+
+
+def misfit_autograd(prob: Problem, x, U):
+    """Differentiable misfit S(x) [P] for x [D, P] (torch.autograd)."""
+    global _MISFIT
+    if _MISFIT is None:
+        _MISFIT = _misfit_function()
+    return _MISFIT.apply(x, prob, U)
 
 
 def invert_batch_workspace_size(n_pix: int) -> int:

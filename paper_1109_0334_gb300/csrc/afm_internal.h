@@ -17,6 +17,7 @@
 #define AFM_MAXM 8
 #define AFM_MAXD 5
 #define AFM_TAB_MAX 4096   // half-step drive phases per period (2 * steps_per_cycle)
+#define AFM_SEG 32         // adjoint checkpoint interval (RK4 steps)
 
 namespace afm {
 

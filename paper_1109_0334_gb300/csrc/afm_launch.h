@@ -59,6 +59,11 @@ cudaError_t launch_batch(const KConst<float>& K, const PsoConst& pc, const Batch
 cudaError_t launch_batch_final(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
                                cudaStream_t st);
 
+// discrete adjoint (gradient of the misfit wrt the normalised parameters)
+size_t adjoint_ckpt_floats(int m, int n_steps, int P);
+cudaError_t launch_adjoint(const KConst<float>& K, const float* x, int P, const float* U, float* S,
+                           float* G, float* ckpt, cudaStream_t st);
+
 // particle swarm
 cudaError_t launch_pso_init(const PsoConst& pc, const SwarmPtrs& sw, cudaStream_t st);
 cudaError_t launch_pso_best(const PsoConst& pc, const SwarmPtrs& sw, const float* S, int it,

@@ -647,6 +647,40 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
     return AFM_OK;
 }
 
+afm_status afm_adjoint_workspace_size(const afm_problem* prob, int P, size_t* bytes) {
+    g_err[0] = 0;
+    if (!bytes || P < 1) return fail(AFM_ERR_INVALID_ARG, "P >= 1 and bytes needed");
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    const int m = prob->model == AFM_POINT_MASS ? 1 : prob->n_modes;
+    *bytes = align256(sizeof(float) * afm::adjoint_ckpt_floats(m, prob->n_steps, P));
+    return AFM_OK;
+}
+
+afm_status afm_adjoint(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
+                       const float* U, float* S, float* dS_dx, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if (P < 1 || prob->n_free < 1) return fail(AFM_ERR_INVALID_ARG, "P >= 1 and n_free >= 1 needed");
+    if (!x || !U || !S || !dS_dx || !workspace)
+        return fail(AFM_ERR_INVALID_ARG, "NULL x, U, S, dS_dx or workspace");
+    size_t need = 0;
+    if ((st = afm_adjoint_workspace_size(prob, P, &need))) return st;
+    if (workspace_bytes < need)
+        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, need);
+    KConst<float> K;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    AFM_CUDA(timed_launch(ctx, s, [&] {
+                 return afm::launch_adjoint(K, x, P, U, S, dS_dx, static_cast<float*>(workspace), s);
+             }),
+             "adjoint kernel");
+    return AFM_OK;
+}
+
 afm_status afm_invert_batch_workspace_size(int n_pix, size_t* bytes) {
     g_err[0] = 0;
     if (!bytes || n_pix < 1) return fail(AFM_ERR_INVALID_ARG, "n_pix >= 1 and bytes needed");
