@@ -217,6 +217,28 @@ afm_status afm_adjoint(afm_ctx* ctx, const afm_problem* prob, const float* x, in
                        const float* U, float* S, float* dS_dx, void* workspace,
                        size_t workspace_bytes, void* stream);
 
+/* ---- gradient polish ------------------------------------------------------
+ * K candidates x [D][K] (device, in/out) take `steps` projected steepest-
+ * descent steps in the normalised cube: gradient g by afm_adjoint, direction
+ * -g / max_d |g_d|, trial points clamp(x + a_j dir) with a_j = 0.05 * 0.5^j
+ * (j < n_cand), all evaluated in one batched forward launch; the largest step
+ * with S(x_j) <= S(x) + 1e-4 g.(x_j - x) is taken, else x stays.  S [K]
+ * (device) receives the final misfits.  workspace >= afm_polish_workspace_size.
+ * afm_invert_polished: the inversion of afm_invert (cfg->iters updates), then
+ * the polish_k particles of lowest personal-best misfit are polished for
+ * polish_steps steps and the best of them is re-evaluated in FP64 into
+ * `result` (result->winner = its swarm index).  history as afm_invert. */
+afm_status afm_polish_workspace_size(const afm_problem* prob, int K, int n_cand, size_t* bytes);
+afm_status afm_polish(afm_ctx* ctx, const afm_problem* prob, const float* U, float* x, float* S,
+                      int K, int steps, int n_cand, void* workspace, size_t workspace_bytes,
+                      void* stream);
+afm_status afm_invert_polished_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
+                                              int polish_k, int n_cand, size_t* bytes);
+afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const float* U,
+                               const afm_pso_cfg* cfg, int polish_k, int polish_steps, int n_cand,
+                               void* workspace, size_t workspace_bytes, afm_result* result,
+                               float* history, void* stream);
+
 /* ---- many pixel inversions in one launch (image scans) -------------------
  * n_pix independent IPs, pixel i with record U_cat[off[i] .. off[i+1]) (its
  * own length; prob->n_steps is only validated, not used) and Philox counter

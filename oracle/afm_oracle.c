@@ -563,6 +563,21 @@ static double complex cmisfit(const orc_case* c, const orc_modal* md,
     return S;
 }
 
+static void grad_cs_serial(const orc_case* c, const orc_modal* md, const orc_pmap* pm,
+                           const double* x, const double* U, int n, double* S, double* grad)
+{
+    const double h = 1e-30;
+    int D = pm->D;
+    for (int d = 0; d < D; ++d) {
+        double complex xc[5], th[5];
+        for (int e = 0; e < D; ++e) xc[e] = x[e] + (e == d ? I * h : 0.0);
+        cmap(pm, xc, th);
+        double complex Sc = cmisfit(c, md, th, U, n);
+        grad[d] = cimag(Sc) / h;
+        if (d == 0) *S = creal(Sc);
+    }
+}
+
 /* dS/dx_d = Im S(x + i h e_d) / h with h = 1e-30 (no subtractive error). */
 int orc_grad_cs(const orc_case* c, const orc_pmap* pm, const double* x,
                 const double* U, int n, double* S, double* grad)
@@ -584,5 +599,72 @@ int orc_grad_cs(const orc_case* c, const orc_pmap* pm, const double* x,
         if (d == 0) Sr = creal(Sc);
     }
     *S = Sr;
+    return 0;
+}
+
+/* ======================================================================== */
+/* Gradient polish of K candidates (reading R14): projected steepest descent */
+/* in the normalised cube.  Per step and candidate: g = dS/dx (complex step), */
+/* direction -g / max|g_d|, trial points clamp(x + alpha_j dir) for           */
+/* alpha_j = alpha0 shrink^j (j < n_cand); the largest step meeting the       */
+/* Armijo condition S(x_j) <= S(x) + sigma g.(x_j - x) is taken, else x stays.*/
+/* x is [D][K]; S [K] receives the final misfits.                             */
+/* ======================================================================== */
+int orc_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, double* x, int K,
+               int steps, int n_cand, double alpha0, double shrink, double sigma, double* S)
+{
+    orc_modal md;
+    if (orc_setup(c, &md)) return -1;
+    int D = pm->D;
+    double* g = (double*)malloc(sizeof(double) * (size_t)D * K);
+    double* Xc = (double*)malloc(sizeof(double) * (size_t)D * K * n_cand);
+    double* Sc = (double*)malloc(sizeof(double) * (size_t)K * n_cand);
+    int KJ = K * n_cand;
+    for (int st = 0; st <= steps; ++st) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+#endif
+        for (int k = 0; k < K; ++k) {
+            double xk[5], gk[5], Sk = 0.0;
+            for (int d = 0; d < D; ++d) xk[d] = x[(size_t)d * K + k];
+            grad_cs_serial(c, &md, pm, xk, U, n, &Sk, gk);
+            S[k] = Sk;
+            for (int d = 0; d < D; ++d) g[(size_t)d * K + k] = gk[d];
+        }
+        if (st == steps) break;
+        for (int k = 0; k < K; ++k) {
+            double gmax = 0.0;
+            for (int d = 0; d < D; ++d) gmax = fmax(gmax, fabs(g[(size_t)d * K + k]));
+            for (int j = 0; j < n_cand; ++j) {
+                double alpha = alpha0 * pow(shrink, j);
+                for (int d = 0; d < D; ++d) {
+                    double xd = x[(size_t)d * K + k];
+                    double step = gmax > 0.0 ? -alpha * g[(size_t)d * K + k] / gmax : 0.0;
+                    double xn = xd + step;
+                    if (xn < 0.0) xn = 0.0;
+                    if (xn > 1.0) xn = 1.0;
+                    Xc[(size_t)d * KJ + (size_t)k * n_cand + j] = xn;
+                }
+            }
+        }
+        orc_misfit_batch(c, pm, Xc, KJ, U, n, Sc);
+        for (int k = 0; k < K; ++k) {
+            for (int j = 0; j < n_cand; ++j) {
+                double lin = 0.0;
+                for (int d = 0; d < D; ++d)
+                    lin += g[(size_t)d * K + k] *
+                           (Xc[(size_t)d * KJ + (size_t)k * n_cand + j] - x[(size_t)d * K + k]);
+                double Sj = Sc[(size_t)k * n_cand + j];
+                if (Sj <= S[k] + sigma * lin && lin < 0.0) {
+                    for (int d = 0; d < D; ++d)
+                        x[(size_t)d * K + k] = Xc[(size_t)d * KJ + (size_t)k * n_cand + j];
+                    break;
+                }
+            }
+        }
+    }
+    free(g);
+    free(Xc);
+    free(Sc);
     return 0;
 }

@@ -26,6 +26,8 @@
  *   orc_record             pinned (noise statistics, truth interior, sub-step
  *                                  convergence)
  *   orc_grad_cs            pinned (central differences of orc_misfit_x)
+ *   orc_polish             pinned (monotone descent, Armijo sufficient decrease,
+ *                                  stationarity at an interior optimum)
  */
 #ifndef AFM_ORACLE_H
 #define AFM_ORACLE_H
@@ -141,6 +143,8 @@ int orc_record(const orc_case* c, const orc_pmap* pm, const double* x, int n,
 /* ---- gradients ---------------------------------------------------------- */
 int orc_grad_cs(const orc_case* c, const orc_pmap* pm, const double* x,
                 const double* U, int n, double* S, double* grad);
+int orc_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, double* x, int K,
+               int steps, int n_cand, double alpha0, double shrink, double sigma, double* S);
 
 void orc_set_threads(int n);
 int orc_get_threads(void);

@@ -112,6 +112,8 @@ def lib():
                                      C.c_double, C.c_uint64, C.c_uint32, _dp]
             L.orc_grad_cs.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, _dp, C.c_int,
                                       C.POINTER(C.c_double), _dp]
+            L.orc_polish.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int, _dp, C.c_int,
+                                     C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -307,3 +309,17 @@ def grad_cs(case: Case, pm: Pmap, x, U):
     lib().orc_grad_cs(C.byref(case), C.byref(pm), np.ascontiguousarray(x, dtype=np.float64),
                       U, len(U), C.byref(S), g)
     return S.value, g
+
+
+def polish(case: Case, pm: Pmap, U, x_dk, steps: int, n_cand: int = 16, alpha0: float = 0.05,
+           shrink: float = 0.5, sigma: float = 1e-4):
+    """Projected-gradient polish with batched Armijo candidates; returns (x, S)."""
+    x = np.array(x_dk, dtype=np.float64, order="C")
+    D, K = x.shape
+    S = np.zeros(K)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    rc = lib().orc_polish(C.byref(case), C.byref(pm), U, len(U), x, K, steps, n_cand, alpha0,
+                          shrink, sigma, S)
+    if rc:
+        raise ValueError("orc_polish failed")
+    return x, S

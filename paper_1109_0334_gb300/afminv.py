@@ -99,6 +99,12 @@ def lib():
                                      C.c_size_t, vp, vp, vp]
             L.afm_adjoint_workspace_size.argtypes = [C.POINTER(Problem), i, C.POINTER(C.c_size_t)]
             L.afm_adjoint.argtypes = [vp, C.POINTER(Problem), vp, i, vp, vp, vp, vp, C.c_size_t, vp]
+            L.afm_polish_workspace_size.argtypes = [C.POINTER(Problem), i, i, C.POINTER(C.c_size_t)]
+            L.afm_polish.argtypes = [vp, C.POINTER(Problem), vp, vp, vp, i, i, i, vp, C.c_size_t, vp]
+            L.afm_invert_polished_workspace_size.argtypes = [C.POINTER(Problem), C.POINTER(PsoCfg),
+                                                             i, i, C.POINTER(C.c_size_t)]
+            L.afm_invert_polished.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), i, i,
+                                              i, vp, C.c_size_t, vp, vp, vp]
             L.afm_invert_batch_workspace_size.argtypes = [i, C.POINTER(C.c_size_t)]
             L.afm_invert_batch.argtypes = [vp, C.POINTER(Problem), vp, vp, i, u32,
                                            C.POINTER(PsoCfg), vp, C.c_size_t, vp,
@@ -351,6 +357,57 @@ def misfit_autograd(prob: Problem, x, U):
     if _MISFIT is None:
         _MISFIT = _misfit_function()
     return _MISFIT.apply(x, prob, U)
+
+
+def polish_workspace_size(prob: Problem, K: int, n_cand: int = 16) -> int:
+    n = C.c_size_t()
+    _check(lib().afm_polish_workspace_size(C.byref(prob), int(K), int(n_cand), C.byref(n)))
+    return int(n.value)
+
+
+def invert_polished_workspace_size(prob: Problem, cfg: PsoCfg, polish_k: int = 32,
+                                   n_cand: int = 16) -> int:
+    n = C.c_size_t()
+    _check(lib().afm_invert_polished_workspace_size(C.byref(prob), C.byref(cfg), int(polish_k),
+                                                    int(n_cand), C.byref(n)))
+    return int(n.value)
+
+
+def polish(prob: Problem, U, x, steps: int, n_cand: int = 16, stream=None):
+    """Projected-gradient polish of candidates x float32 CUDA [D, K] (in
+    place); returns their misfits S [K]."""
+    import torch
+    D, K = int(x.shape[0]), int(x.shape[1])
+    n = C.c_size_t()
+    _check(lib().afm_polish_workspace_size(C.byref(prob), K, int(n_cand), C.byref(n)))
+    ws = torch.empty(int(n.value), dtype=torch.uint8, device=x.device)
+    S = torch.empty(K, dtype=torch.float32, device=x.device)
+    _check(lib().afm_polish(context(x.device.index), C.byref(prob), _ptr(U), _ptr(x), _ptr(S), K,
+                            int(steps), int(n_cand), _ptr(ws), C.c_size_t(ws.numel()),
+                            _stream(stream)))
+    return S
+
+
+def invert_polished(prob: Problem, U, cfg: PsoCfg, polish_k: int = 32, polish_steps: int = 20,
+                    n_cand: int = 16, workspace=None, result=None, history=None, stream=None):
+    """PSO (cfg) then gradient polish of the best polish_k particles; returns
+    (result uint8 tensor, history)."""
+    import torch
+    dev = U.device
+    n = C.c_size_t()
+    _check(lib().afm_invert_polished_workspace_size(C.byref(prob), C.byref(cfg), int(polish_k),
+                                                    int(n_cand), C.byref(n)))
+    if workspace is None or workspace.numel() < n.value:
+        workspace = torch.empty(int(n.value), dtype=torch.uint8, device=dev)
+    if result is None:
+        result = torch.zeros(C.sizeof(Result), dtype=torch.uint8, device=dev)
+    if history is None:
+        history = torch.empty(cfg.iters + 1, dtype=torch.float32, device=dev)
+    _check(lib().afm_invert_polished(context(dev.index), C.byref(prob), _ptr(U), C.byref(cfg),
+                                     int(polish_k), int(polish_steps), int(n_cand),
+                                     _ptr(workspace), C.c_size_t(workspace.numel()), _ptr(result),
+                                     _ptr(history), _stream(stream)))
+    return result, history
 
 
 def invert_batch_workspace_size(n_pix: int) -> int:

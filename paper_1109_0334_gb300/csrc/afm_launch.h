@@ -64,6 +64,17 @@ size_t adjoint_ckpt_floats(int m, int n_steps, int P);
 cudaError_t launch_adjoint(const KConst<float>& K, const float* x, int P, const float* U, float* S,
                            float* G, float* ckpt, cudaStream_t st);
 
+// gradient polish
+cudaError_t launch_polish_cand(int D, int K, int J, const float* x, const float* G, double alpha0,
+                               double shrink, float* Xc, cudaStream_t st);
+cudaError_t launch_polish_select(int D, int K, int J, float sigma, float* x, const float* G,
+                                 float* S, const float* Xc, const float* Sc, cudaStream_t st);
+cudaError_t launch_topk(const float* pbS, const float* pb, int P, int D, int K, float* xk, int* idx,
+                        cudaStream_t st);
+cudaError_t launch_polish_final(const KConst<double>& K, int Kn, int iters, const float* x,
+                                const float* S, const int* idx, const float* U, const int* flags,
+                                void* result, cudaStream_t st);
+
 // particle swarm
 cudaError_t launch_pso_init(const PsoConst& pc, const SwarmPtrs& sw, cudaStream_t st);
 cudaError_t launch_pso_best(const PsoConst& pc, const SwarmPtrs& sw, const float* S, int it,

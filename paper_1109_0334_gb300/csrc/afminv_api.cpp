@@ -681,6 +681,143 @@ afm_status afm_adjoint(afm_ctx* ctx, const afm_problem* prob, const float* x, in
     return AFM_OK;
 }
 
+// Polish workspace: gradient [D][K], candidates [D][K*J], their misfits
+// [K*J], adjoint checkpoints of K particles.
+struct PolishLayout {
+    size_t G, Xc, Sc, ckpt, total;
+};
+
+PolishLayout polish_layout(const afm_problem& pr, int K, int J) {
+    PolishLayout L;
+    const int D = pr.n_free;
+    const int m = pr.model == AFM_POINT_MASS ? 1 : pr.n_modes;
+    size_t off = 0;
+    L.G = off; off += align256(sizeof(float) * (size_t)D * K);
+    L.Xc = off; off += align256(sizeof(float) * (size_t)D * K * J);
+    L.Sc = off; off += align256(sizeof(float) * (size_t)K * J);
+    L.ckpt = off; off += align256(sizeof(float) * afm::adjoint_ckpt_floats(m, pr.n_steps, K));
+    L.total = off;
+    return L;
+}
+
+const double kPolishAlpha0 = 0.05, kPolishShrink = 0.5, kPolishSigma = 1e-4;
+
+afm_status polish_run(afm_ctx* ctx, const afm_problem& pr, const KConst<float>& K, const float* U,
+                      float* x, float* S, int Kn, int steps, int J, char* ws, cudaStream_t s) {
+    const PolishLayout L = polish_layout(pr, Kn, J);
+    float* G = reinterpret_cast<float*>(ws + L.G);
+    float* Xc = reinterpret_cast<float*>(ws + L.Xc);
+    float* Sc = reinterpret_cast<float*>(ws + L.Sc);
+    float* ck = reinterpret_cast<float*>(ws + L.ckpt);
+    const int D = pr.n_free;
+    for (int st = 0; st < steps; ++st) {
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_adjoint(K, x, Kn, U, S, G, ck, s); }),
+                 "adjoint kernel");
+        AFM_CUDA(afm::launch_polish_cand(D, Kn, J, x, G, kPolishAlpha0, kPolishShrink, Xc, s),
+                 "polish candidate kernel");
+        AFM_CUDA(afm::launch_forward_f32(K, Xc, Kn * J, nullptr, U, Sc, nullptr, s), "forward kernel");
+        AFM_CUDA(afm::launch_polish_select(D, Kn, J, (float)kPolishSigma, x, G, S, Xc, Sc, s),
+                 "polish select kernel");
+    }
+    if (steps == 0)
+        AFM_CUDA(afm::launch_forward_f32(K, x, Kn, nullptr, U, S, nullptr, s), "forward kernel");
+    return AFM_OK;
+}
+
+afm_status afm_polish_workspace_size(const afm_problem* prob, int K, int n_cand, size_t* bytes) {
+    g_err[0] = 0;
+    if (!bytes || K < 1 || n_cand < 1 || n_cand > 64)
+        return fail(AFM_ERR_INVALID_ARG, "K >= 1, 1 <= n_cand <= 64 and bytes needed");
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    *bytes = polish_layout(*prob, K, n_cand).total;
+    return AFM_OK;
+}
+
+afm_status afm_polish(afm_ctx* ctx, const afm_problem* prob, const float* U, float* x, float* S,
+                      int K, int steps, int n_cand, void* workspace, size_t workspace_bytes,
+                      void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if (!U || !x || !S || !workspace || K < 1 || steps < 0 || prob->n_free < 1)
+        return fail(AFM_ERR_INVALID_ARG, "NULL array, K < 1, steps < 0 or no free parameter");
+    size_t need = 0;
+    if ((st = afm_polish_workspace_size(prob, K, n_cand, &need))) return st;
+    if (workspace_bytes < need || reinterpret_cast<uintptr_t>(workspace) % 256)
+        return fail(AFM_ERR_INVALID_ARG, "workspace too small (%zu < %zu) or misaligned",
+                    workspace_bytes, need);
+    KConst<float> K32;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K32);
+    return polish_run(ctx, *prob, K32, U, x, S, K, steps, n_cand, static_cast<char*>(workspace),
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+afm_status afm_invert_polished_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
+                                              int polish_k, int n_cand, size_t* bytes) {
+    g_err[0] = 0;
+    if (!bytes) return fail(AFM_ERR_INVALID_ARG, "bytes is NULL");
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_pso(cfg, prob->n_free))) return st;
+    if (polish_k < 1 || polish_k > cfg->P || n_cand < 1 || n_cand > 64)
+        return fail(AFM_ERR_INVALID_ARG, "1 <= polish_k <= P and 1 <= n_cand <= 64 needed");
+    const size_t inv = invert_layout(cfg->P, prob->n_free).total;
+    const size_t xk = align256(sizeof(float) * (size_t)prob->n_free * polish_k);
+    const size_t sk = align256(sizeof(float) * (size_t)polish_k);
+    const size_t ik = align256(sizeof(int) * (size_t)polish_k);
+    *bytes = inv + xk + sk + ik + polish_layout(*prob, polish_k, n_cand).total;
+    return AFM_OK;
+}
+
+afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const float* U,
+                               const afm_pso_cfg* cfg, int polish_k, int polish_steps, int n_cand,
+                               void* workspace, size_t workspace_bytes, afm_result* result,
+                               float* history, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if ((st = check_pso(cfg, prob->n_free))) return st;
+    if (!U || !result || !workspace || polish_steps < 0)
+        return fail(AFM_ERR_INVALID_ARG, "NULL U, result or workspace, or polish_steps < 0");
+    if (cfg->P > 8192) return fail(AFM_ERR_INVALID_ARG, "polished inversion supports P <= 8192");
+    size_t need = 0;
+    if ((st = afm_invert_polished_workspace_size(prob, cfg, polish_k, n_cand, &need))) return st;
+    if (workspace_bytes < need || reinterpret_cast<uintptr_t>(workspace) % 256)
+        return fail(AFM_ERR_INVALID_ARG, "workspace too small (%zu < %zu) or misaligned",
+                    workspace_bytes, need);
+    const int D = prob->n_free, P = cfg->P;
+    char* ws = static_cast<char*>(workspace);
+    const InvLayout L = invert_layout(P, D);
+    afm::SwarmPtrs sw;
+    afm::detail::carve_swarm(ws, P, D, &sw);
+    char* pol = ws + L.total;
+    float* xk = reinterpret_cast<float*>(pol);
+    pol += align256(sizeof(float) * (size_t)D * polish_k);
+    float* sk = reinterpret_cast<float*>(pol);
+    pol += align256(sizeof(float) * (size_t)polish_k);
+    int* ik = reinterpret_cast<int*>(pol);
+    pol += align256(sizeof(int) * (size_t)polish_k);
+    KConst<float> Kf;
+    KConst<double> Kd;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kf);
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kd);
+    const afm::PsoConst pc = pso_const(*cfg, D);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    AFM_CUDA(afm::launch_pso_init(pc, sw, s), "pso init kernel");
+    for (int it = 0; it <= cfg->iters; ++it)
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_invert_iter(Kf, pc, sw, U, history, it, s); }),
+                 "invert iteration kernel");
+    const int fin = (cfg->iters + 1) & 1;
+    AFM_CUDA(afm::launch_topk(sw.pbS, sw.pb[fin], P, D, polish_k, xk, ik, s), "top-k kernel");
+    if ((st = polish_run(ctx, *prob, Kf, U, xk, sk, polish_k, polish_steps, n_cand, pol, s))) return st;
+    AFM_CUDA(afm::launch_polish_final(Kd, polish_k, cfg->iters, xk, sk, ik, U, sw.flags, result, s),
+             "polish final kernel");
+    return AFM_OK;
+}
+
 afm_status afm_invert_batch_workspace_size(int n_pix, size_t* bytes) {
     g_err[0] = 0;
     if (!bytes || n_pix < 1) return fail(AFM_ERR_INVALID_ARG, "n_pix >= 1 and bytes needed");

@@ -534,3 +534,31 @@ def test_pso_vs_grid_search(orc, c1_problem):
     assert np.all(np.diff(hist) <= 0)           # global best never worsens
     # the recovered optimum explains the record to the noise level
     assert bS / n == pytest.approx(w["sigma"] ** 2, rel=0.1)
+
+
+def test_polish_descends_to_a_stationary_point(orc):
+    """Gradient polish (reading R14): the misfit never increases with more
+    steps, the first steps remove the stiff error (misfit down by >100x,
+    gradient down by >100x, the stiff coordinate at the optimum), and the
+    slow valley direction keeps improving (steepest descent)."""
+    w = W.get("c2", force="linear_spring", cycles=10,
+              free=[(0, 2.0, 20.0, False), (1, 10e-9, 20e-9, False)], fixed=[0.0] * 5)
+    c, pm = orc.make_case(w), orc.make_pmap(w)
+    n = W.n_steps(w)
+    xt = np.array([0.4, 0.6])
+    U = orc.record(c, pm, xt, n, 1, 0.0, w["seed"])       # exact data: optimum at xt
+    x0 = np.array([[0.43, 0.38], [0.57, 0.63]])           # [D][K], two starts
+    S0 = orc.misfit_batch(c, pm, x0, U)
+    g0 = np.array([orc.grad_cs(c, pm, x0[:, k], U)[1] for k in range(2)])
+    prev = S0
+    for steps in (5, 10, 20, 40):
+        xs, Ss = orc.polish(c, pm, U, x0, steps=steps, n_cand=16)
+        assert np.all(Ss <= prev)
+        prev = Ss
+        if steps == 5:
+            assert np.all(Ss < 1e-2 * S0)
+            g = np.array([orc.grad_cs(c, pm, xs[:, k], U)[1] for k in range(2)])
+            assert np.all(np.max(np.abs(g), axis=1) < 1e-2 * np.max(np.abs(g0), axis=1))
+            np.testing.assert_allclose(xs[0], xt[0], atol=1e-3)
+    # the valley coordinate moves towards the optimum
+    assert np.all(np.abs(xs[1] - xt[1]) < np.abs(x0[1] - xt[1]))
