@@ -268,6 +268,64 @@ def run_c3(A, W, dev, peak_ops, flush):
 
 
 # ---------------------------------------------------------------------------
+# Gradient-polished inversion against plain PSO (Kelvin-Voigt workload)
+# ---------------------------------------------------------------------------
+def ident_errors(theta, truth):
+    """Relative errors of the combinations the DMT(+KV) law depends on:
+    H R, E* sqrt(R), a0, eta sqrt(R)."""
+    import math
+
+    def comb(t):
+        return [t[1] * t[2], t[0] * math.sqrt(t[2]), t[3], t[4] * math.sqrt(t[2])]
+    a, b = comb(theta), comb(truth)
+    return [abs(x / y - 1) if y else abs(x) for x, y in zip(a, b)]
+
+
+def run_c4(A, W, dev, flush):
+    import numpy as np
+    import torch
+    spec = W.get("c4")
+    D = len(spec["free"])
+    N = W.n_steps(spec)
+    rng = np.random.default_rng(spec["seed"])
+    xt = rng.uniform(0.1, 0.9, size=(D, 1))
+    prob = A.make_problem(spec)
+    off = torch.tensor([0, N], dtype=torch.int64, device=dev)
+    U = A.synth_records(prob, torch.from_numpy(xt).to(dev), off, spec["record_sub"], spec["sigma"],
+                        spec["seed"], 0)
+    th_true = [0.0] * 5
+    for d, (slot, lo, hi, lg) in enumerate(spec["free"]):
+        th_true[slot] = 10 ** (np.log10(lo) + xt[d, 0] * (np.log10(hi) - np.log10(lo))) if lg \
+            else lo + xt[d, 0] * (hi - lo)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1), A.decode_result(r[0])
+
+    cfg = A.make_pso(spec)
+    ms_pol, r_pol = timed(lambda: A.invert_polished(prob, U, cfg, spec["polish_k"],
+                                                    spec["polish_steps"]))
+    plain = A.make_pso(dict(spec, iters=100))
+    ms_pso, r_pso = timed(lambda: A.invert(prob, U, plain))
+    return {"workload": "c4: 3-mode DMT + Kelvin-Voigt, 5 unknowns, 100 cycles x 256 steps",
+            "polished": {"config": "1024 particles x 40 updates + 20 adjoint-gradient polish "
+                                   "steps on the best 32 (16 Armijo candidates per step)",
+                         "ms_per_inversion": ms_pol, "S_f64_nm2": r_pol["S_f64"],
+                         "ident_rel_err_vs_truth": ident_errors(list(r_pol["theta"]), th_true)},
+            "plain_pso": {"config": "1024 particles x 100 updates",
+                          "ms_per_inversion": ms_pso, "S_f64_nm2": r_pso["S_f64"],
+                          "ident_rel_err_vs_truth": ident_errors(list(r_pso["theta"]), th_true)},
+            "ident": "H R, E* sqrt(R), a0, eta sqrt(R)"}
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -405,6 +463,9 @@ def run_ours(args):
     c3 = None
     if not args.no_c3:
         c3 = run_c3(A, W, dev, peak_ops, flush)
+    c4 = None
+    if not args.no_c4:
+        c4 = run_c4(A, W, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -431,6 +492,7 @@ def run_ours(args):
                        "status": r["status"], "theta": list(theta)},
             "batched_forward": batched,
             "batched_inversion": c3,
+            "polished_inversion": c4,
         }
         print(json.dumps(out))
     if world > 1:
@@ -496,6 +558,21 @@ def run_probe(args):
         out = A.decode_results(res)
         print(json.dumps({"pixels": len(out), "kp": kp, "ok": sum(r["status"] == 0 for r in out)}))
         return
+    if args.probe == "adjoint":
+        # gradient of 32 particles of the Kelvin-Voigt workload (one polish step's adjoint)
+        spec = W.get("c4")
+        D, N = len(spec["free"]), W.n_steps(spec)
+        prob = A.make_problem(spec)
+        off = torch.tensor([0, N], dtype=torch.int64, device="cuda")
+        xt = torch.full((D, 1), 0.5, dtype=torch.float64, device="cuda")
+        U = A.synth_records(prob, xt, off, spec["record_sub"], spec["sigma"], spec["seed"], 0)
+        g = torch.Generator(device="cuda").manual_seed(7)
+        x = torch.rand((D, 32), dtype=torch.float32, device="cuda", generator=g)
+        for _ in range(2):
+            S, G = A.adjoint(prob, x, U)
+        torch.cuda.synchronize()
+        print(json.dumps({"S_mean": float(S.mean()), "G_absmax": float(G.abs().max())}))
+        return
     spec = W.get(args.workload, iters=args.probe_iters)
     D = len(spec["free"])
     N = W.n_steps(spec)
@@ -527,7 +604,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the wide forward launch")
     ap.add_argument("--no-c3", action="store_true", help="skip the 4096-pixel batched inversion")
-    ap.add_argument("--probe", choices=["invert", "forward", "batch"], default=None,
+    ap.add_argument("--no-c4", action="store_true", help="skip the polished-inversion comparison")
+    ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint"], default=None,
                     help="run one small untimed case for a profiler capture and exit")
     ap.add_argument("--probe-iters", type=int, default=2)
     ap.add_argument("--probe-particles", type=int, default=32768)
