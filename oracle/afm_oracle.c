@@ -315,8 +315,12 @@ void orc_map(const orc_pmap* pm, const double* x, double th[5])
     }
 }
 
+int orc_fe_forward(const orc_case* c, const double th[5], int n_steps, int sub, double* u,
+                   double* setup_out);
+
 static int forward_any(const orc_case* c, const double th[5], int n, double* u)
 {
+    if (c->model == ORC_FE_HERMITE) return orc_fe_forward(c, th, n, 1, u, NULL);
     return orc_forward(c, th, n, 1, u, NULL);
 }
 
@@ -470,7 +474,9 @@ int orc_record(const orc_case* c, const orc_pmap* pm, const double* x, int n,
 {
     double th[5];
     orc_map(pm, x, th);
-    if (orc_forward(c, th, n, sub, U, NULL)) return -1;
+    int rc = c->model == ORC_FE_HERMITE ? orc_fe_forward(c, th, n, sub, U, NULL)
+                                        : orc_forward(c, th, n, sub, U, NULL);
+    if (rc) return -1;
     if (sigma > 0.0) {
         uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
         for (int j = 0; j < n; ++j) {
@@ -666,5 +672,336 @@ int orc_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, do
     free(g);
     free(Xc);
     free(Sc);
+    return 0;
+}
+
+/* ======================================================================== */
+/* Finite-element cantilever (reading R13): cubic Hermite Euler-Bernoulli    */
+/* elements, consistent mass, clamped node removed; Rayleigh damping with Q */
+/* on modes 1 and 2; Newmark beta = 1/4, gamma = 1/2 in the displacement-    */
+/* only three-term form                                                      */
+/*   S u_{n+1} = (2M - h^2/2 K) u_n - (M - h/2 C + h^2/4 K) u_{n-1}           */
+/*               + h^2/4 (f_{n+1} + 2 f_n + f_{n-1}),                         */
+/*   S = M + h/2 C + h^2/4 K,  f = M r g + e_tip F_ts,                        */
+/* g = -(base acceleration), r = 1 on deflection DOFs; the tip force at step */
+/* n+1 is implicit and found by Newton on the tip deflection.                */
+/* ======================================================================== */
+#define ORC_FE_MAXN 128
+
+typedef struct {
+    int n;                        /* DOFs = 2 n_elem                         */
+    double M[ORC_FE_MAXN * ORC_FE_MAXN], K[ORC_FE_MAXN * ORC_FE_MAXN],
+        C[ORC_FE_MAXN * ORC_FE_MAXN];
+    double w1, w2;                /* first two natural frequencies [rad/s]   */
+    double alpha, beta;           /* Rayleigh coefficients                   */
+    double thick, width, mu;      /* derived section                          */
+} orc_fe_mats;
+
+/* Dense LU with partial pivoting (in place), and its solve. */
+static int lu_factor(double* A, int n, int* piv)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (fabs(A[i * n + k]) > fabs(A[p * n + k])) p = i;
+        if (A[p * n + k] == 0.0) return -1;
+        piv[k] = p;
+        if (p != k)
+            for (int j = 0; j < n; ++j) {
+                double t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t;
+            }
+        for (int i = k + 1; i < n; ++i) {
+            A[i * n + k] /= A[k * n + k];
+            for (int j = k + 1; j < n; ++j) A[i * n + j] -= A[i * n + k] * A[k * n + j];
+        }
+    }
+    return 0;
+}
+
+static void lu_solve(const double* LU, int n, const int* piv, double* b)
+{
+    for (int k = 0; k < n; ++k) {
+        if (piv[k] != k) { double t = b[k]; b[k] = b[piv[k]]; b[piv[k]] = t; }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) b[i] -= LU[i * n + j] * b[j];
+    for (int i = n - 1; i >= 0; --i) {
+        for (int j = i + 1; j < n; ++j) b[i] -= LU[i * n + j] * b[j];
+        b[i] /= LU[i * n + i];
+    }
+}
+
+/* Complex dense solve by Gaussian elimination with partial pivoting. */
+static int csolve(double complex* A, int n, double complex* b)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (cabs(A[i * n + k]) > cabs(A[p * n + k])) p = i;
+        if (cabs(A[p * n + k]) == 0.0) return -1;
+        if (p != k) {
+            for (int j = 0; j < n; ++j) {
+                double complex t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t;
+            }
+            double complex t = b[k]; b[k] = b[p]; b[p] = t;
+        }
+        for (int i = k + 1; i < n; ++i) {
+            double complex f = A[i * n + k] / A[k * n + k];
+            for (int j = k; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+            b[i] -= f * b[k];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        for (int j = i + 1; j < n; ++j) b[i] -= A[i * n + j] * b[j];
+        b[i] /= A[i * n + i];
+    }
+    return 0;
+}
+
+/* Eigenvalues of the symmetric matrix A (n x n, destroyed) by cyclic Jacobi
+ * rotations; returned in ascending order in ev. */
+static void jacobi_eig(double* A, int n, double* ev)
+{
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+        if (off < 1e-30) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[p * n + q];
+                if (fabs(apq) < 1e-300) continue;
+                double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i) ev[i] = A[i * n + i];
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (ev[j] < ev[i]) { double t = ev[i]; ev[i] = ev[j]; ev[j] = t; }
+}
+
+int orc_fe_dofs(const orc_case* c) { return 2 * c->n_elem; }
+
+/* Section from the targets: 3 E I / L^3 = k and the Euler-Bernoulli first
+ * frequency (beta_1 L)^2 sqrt(E I / (mu L^4)) = 2 pi f1; rho A = mu. */
+static int fe_build(const orc_case* c, orc_fe_mats* fe)
+{
+    int ne = c->n_elem, n = 2 * ne;
+    if (ne < 1 || n > ORC_FE_MAXN) return -1;
+    double L = c->L, E = c->E;
+    double Iz = c->fe_k * L * L * L / (3.0 * E);
+    double b1 = orc_beam_root(1) / L;
+    double w1t = 2.0 * M_PI * c->fe_f1;
+    double mu = E * Iz * pow(b1, 4) / (w1t * w1t);
+    double A = mu / c->rho;
+    fe->thick = sqrt(12.0 * Iz / A);
+    fe->width = A / fe->thick;
+    fe->mu = mu;
+    fe->n = n;
+    double h = L / ne;
+    int N2 = n + 2;   /* with the clamped node */
+    double* Mf = (double*)calloc((size_t)N2 * N2, sizeof(double));
+    double* Kf = (double*)calloc((size_t)N2 * N2, sizeof(double));
+    const double me[16] = {156, 22 * h, 54, -13 * h, 22 * h, 4 * h * h, 13 * h, -3 * h * h,
+                           54, 13 * h, 156, -22 * h, -13 * h, -3 * h * h, -22 * h, 4 * h * h};
+    const double ke[16] = {12, 6 * h, -12, 6 * h, 6 * h, 4 * h * h, -6 * h, 2 * h * h,
+                           -12, -6 * h, 12, -6 * h, 6 * h, 2 * h * h, -6 * h, 4 * h * h};
+    double ms = mu * h / 420.0, ks = E * Iz / (h * h * h);
+    for (int e = 0; e < ne; ++e)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                int ga = 2 * e + a, gb = 2 * e + b;
+                Mf[ga * N2 + gb] += ms * me[a * 4 + b];
+                Kf[ga * N2 + gb] += ks * ke[a * 4 + b];
+            }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            fe->M[i * n + j] = Mf[(i + 2) * N2 + (j + 2)];
+            fe->K[i * n + j] = Kf[(i + 2) * N2 + (j + 2)];
+        }
+    free(Mf);
+    free(Kf);
+    /* generalized eigenvalues of K x = w^2 M x via Cholesky M = L L^T */
+    double* Lc = (double*)calloc((size_t)n * n, sizeof(double));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s2 = fe->M[i * n + j];
+            for (int k = 0; k < j; ++k) s2 -= Lc[i * n + k] * Lc[j * n + k];
+            if (i == j) {
+                if (s2 <= 0) { free(Lc); return -1; }
+                Lc[i * n + i] = sqrt(s2);
+            } else {
+                Lc[i * n + j] = s2 / Lc[j * n + j];
+            }
+        }
+    /* B = L^-1 K L^-T */
+    double* T = (double*)calloc((size_t)n * n, sizeof(double));
+    double* B = (double*)calloc((size_t)n * n, sizeof(double));
+    for (int col = 0; col < n; ++col)     /* T = L^-1 K (column by column) */
+        for (int i = 0; i < n; ++i) {
+            double s2 = fe->K[i * n + col];
+            for (int k = 0; k < i; ++k) s2 -= Lc[i * n + k] * T[k * n + col];
+            T[i * n + col] = s2 / Lc[i * n + i];
+        }
+    for (int row = 0; row < n; ++row)     /* B = T L^-T: solve L B^T = T^T */
+        for (int i = 0; i < n; ++i) {
+            double s2 = T[row * n + i];
+            for (int k = 0; k < i; ++k) s2 -= Lc[i * n + k] * B[row * n + k];
+            B[row * n + i] = s2 / Lc[i * n + i];
+        }
+    double* ev = (double*)malloc(sizeof(double) * n);
+    jacobi_eig(B, n, ev);
+    fe->w1 = sqrt(ev[0]);
+    fe->w2 = sqrt(ev[1]);
+    free(ev); free(B); free(T); free(Lc);
+    /* Rayleigh: 1/(2Q) = alpha/(2 w_i) + beta w_i / 2, i = 1, 2 */
+    double z = 1.0 / (2.0 * c->fe_Q);
+    fe->beta = 2.0 * z / (fe->w1 + fe->w2);
+    fe->alpha = fe->beta * fe->w1 * fe->w2;
+    for (int i = 0; i < n * n; ++i) fe->C[i] = fe->alpha * fe->M[i] + fe->beta * fe->K[i];
+    return 0;
+}
+
+/* Geometry and frequencies of the FE model: geom = (thickness, width, mu,
+ * w1, w2, alpha, beta); M, K, C (n x n) if non-NULL. */
+int orc_fe_matrices(const orc_case* c, double* M, double* K, double* C, double* w12,
+                    double* geom)
+{
+    orc_fe_mats* fe = (orc_fe_mats*)malloc(sizeof(orc_fe_mats));
+    if (fe_build(c, fe)) { free(fe); return -1; }
+    int n = fe->n;
+    if (M) memcpy(M, fe->M, sizeof(double) * n * n);
+    if (K) memcpy(K, fe->K, sizeof(double) * n * n);
+    if (C) memcpy(C, fe->C, sizeof(double) * n * n);
+    if (w12) { w12[0] = fe->w1; w12[1] = fe->w2; }
+    if (geom) {
+        geom[0] = fe->thick; geom[1] = fe->width; geom[2] = fe->mu;
+        geom[3] = fe->w1; geom[4] = fe->w2; geom[5] = fe->alpha; geom[6] = fe->beta;
+    }
+    free(fe);
+    return 0;
+}
+
+/* d F / d d for the tip-force laws without rate dependence. */
+static double force_slope(int kind, const double th[5], double d)
+{
+    switch (kind) {
+    case ORC_F_LINEAR:
+        return -th[0];
+    case ORC_F_DMT: {
+        double H = th[1], R = th[2], a0 = th[3];
+        if (d > a0) return H * R / (3.0 * d * d * d);
+        return -1.5 * (4.0 / 3.0) * th[0] * sqrt(R) * sqrt(a0 - d);
+    }
+    case ORC_F_HOOKE:
+        return d < th[1] ? -th[0] : 0.0;
+    default:
+        return 0.0;
+    }
+}
+
+/* FE forward solve: u[n] = tip deflection after step n+1 (record steps of
+ * h = 1 / (f_1 spc) with f_1 the FE model's own first frequency, each split
+ * into `sub` Newmark steps).  setup_out (optional, 8 values): w1, w2, alpha,
+ * beta, a, psi, h, thickness. */
+int orc_fe_forward(const orc_case* c, const double th[5], int n_steps, int sub, double* u,
+                   double* setup_out)
+{
+    if (c->force == ORC_F_DMT_KV || c->force == ORC_F_SPRING_DAMPER) return -1;
+    orc_fe_mats* fe = (orc_fe_mats*)malloc(sizeof(orc_fe_mats));
+    if (fe_build(c, fe)) { free(fe); return -1; }
+    int n = fe->n, tip = n - 2;
+    double w = fe->w1;
+    int spc = c->spc * sub;
+    double h = 2.0 * M_PI / (w * spc);
+    double* r = (double*)calloc(n, sizeof(double));
+    for (int i = 0; i < n; i += 2) r[i] = 1.0;
+    double* Mr = (double*)calloc(n, sizeof(double));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Mr[i] += fe->M[i * n + j] * r[j];
+    /* free steady state: (K - w^2 M + i w C) X = M r */
+    double complex* Z = (double complex*)malloc(sizeof(double complex) * n * n);
+    double complex* X = (double complex*)malloc(sizeof(double complex) * n);
+    for (int i = 0; i < n * n; ++i) Z[i] = fe->K[i] - w * w * fe->M[i] + I * w * fe->C[i];
+    for (int i = 0; i < n; ++i) X[i] = Mr[i];
+    if (csolve(Z, n, X)) { free(Z); free(X); free(r); free(Mr); free(fe); return -1; }
+    double a = c->A0 / (w * w * cabs(X[tip]));
+    double psi = M_PI / 2.0 - carg(X[tip]);
+    double* u0 = (double*)malloc(sizeof(double) * n);
+    double* um = (double*)malloc(sizeof(double) * n);
+    double* up = (double*)malloc(sizeof(double) * n);
+    double* rhs = (double*)malloc(sizeof(double) * n);
+    for (int i = 0; i < n; ++i) {
+        u0[i] = cimag(a * w * w * X[i] * cexp(I * psi));
+        um[i] = cimag(a * w * w * X[i] * cexp(I * (psi - w * h)));
+    }
+    /* S, its LU, and s = S^-1 e_tip */
+    double* S = (double*)malloc(sizeof(double) * n * n);
+    double* P1 = (double*)malloc(sizeof(double) * n * n);
+    double* P2 = (double*)malloc(sizeof(double) * n * n);
+    int* piv = (int*)malloc(sizeof(int) * n);
+    for (int i = 0; i < n * n; ++i) {
+        S[i] = fe->M[i] + 0.5 * h * fe->C[i] + 0.25 * h * h * fe->K[i];
+        P1[i] = 2.0 * fe->M[i] - 0.5 * h * h * fe->K[i];
+        P2[i] = fe->M[i] - 0.5 * h * fe->C[i] + 0.25 * h * h * fe->K[i];
+    }
+    lu_factor(S, n, piv);
+    double* s = (double*)calloc(n, sizeof(double));
+    s[tip] = 1.0;
+    lu_solve(S, n, piv, s);
+    double q = 0.25 * h * h;
+    double Fm = orc_force(c->force, th, c->Zc + um[tip], 0.0);
+    double F0 = orc_force(c->force, th, c->Zc + u0[tip], 0.0);
+    long step = 0;
+    for (int nrec = 0; nrec < n_steps; ++nrec) {
+        for (int f = 0; f < sub; ++f, ++step) {
+            double gm = a * w * w * sin(w * h * (double)((step - 1 + spc) % spc) + psi);
+            double g0 = a * w * w * sin(w * h * (double)(step % spc) + psi);
+            double gp = a * w * w * sin(w * h * (double)((step + 1) % spc) + psi);
+            double G = gp + 2.0 * g0 + gm;
+            for (int i = 0; i < n; ++i) {
+                double acc = q * (Mr[i] * G);
+                for (int j = 0; j < n; ++j) acc += P1[i * n + j] * u0[j] - P2[i * n + j] * um[j];
+                if (i == tip) acc += q * (2.0 * F0 + Fm);
+                rhs[i] = acc;
+            }
+            lu_solve(S, n, piv, rhs);             /* rhs = S^-1 (known part) */
+            /* tip: z = rhs_tip + q s_tip F(Zc + z), Newton */
+            double z = rhs[tip];
+            for (int it = 0; it < 60; ++it) {
+                double Fz = orc_force(c->force, th, c->Zc + z, 0.0);
+                double phi = z - rhs[tip] - q * s[tip] * Fz;
+                double dphi = 1.0 - q * s[tip] * force_slope(c->force, th, c->Zc + z);
+                double dz = phi / dphi;
+                z -= dz;
+                if (fabs(dz) <= 1e-15 * (fabs(z) + 1e-30)) break;
+            }
+            double Fp = orc_force(c->force, th, c->Zc + z, 0.0);
+            for (int i = 0; i < n; ++i) up[i] = rhs[i] + q * s[i] * Fp;
+            double* t = um; um = u0; u0 = up; up = t;
+            Fm = F0;
+            F0 = Fp;
+        }
+        u[nrec] = u0[tip];
+    }
+    if (setup_out) {
+        setup_out[0] = fe->w1; setup_out[1] = fe->w2; setup_out[2] = fe->alpha;
+        setup_out[3] = fe->beta; setup_out[4] = a; setup_out[5] = psi; setup_out[6] = h;
+        setup_out[7] = fe->thick;
+    }
+    free(S); free(P1); free(P2); free(piv); free(s); free(u0); free(um); free(up); free(rhs);
+    free(Z); free(X); free(r); free(Mr); free(fe);
     return 0;
 }

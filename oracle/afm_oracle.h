@@ -26,6 +26,10 @@
  *   orc_record             pinned (noise statistics, truth interior, sub-step
  *                                  convergence)
  *   orc_grad_cs            pinned (central differences of orc_misfit_x)
+ *   orc_fe_matrices        pinned (static stiffness 3EI/L^3, Euler-Bernoulli
+ *                                  frequencies, Rayleigh Q of modes 1-2)
+ *   orc_fe_forward         pinned (free steady state, modal-model agreement,
+ *                                  Newmark energy conservation, order 2)
  *   orc_polish             pinned (monotone descent, Armijo sufficient decrease,
  *                                  stationarity at an interior optimum)
  */
@@ -145,6 +149,13 @@ int orc_grad_cs(const orc_case* c, const orc_pmap* pm, const double* x,
                 const double* U, int n, double* S, double* grad);
 int orc_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, double* x, int K,
                int steps, int n_cand, double alpha0, double shrink, double sigma, double* S);
+
+/* ---- finite-element Hermite beam with Newmark time stepping (R13) ----- */
+int orc_fe_dofs(const orc_case* c);
+int orc_fe_matrices(const orc_case* c, double* M, double* K, double* C, double* w12,
+                    double* geom);
+int orc_fe_forward(const orc_case* c, const double th[5], int n_steps, int sub, double* u,
+                   double* setup_out);
 
 void orc_set_threads(int n);
 int orc_get_threads(void);

@@ -114,6 +114,10 @@ def lib():
                                       C.POINTER(C.c_double), _dp]
             L.orc_polish.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int, _dp, C.c_int,
                                      C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
+            L.orc_fe_dofs.argtypes = [C.POINTER(Case)]
+            L.orc_fe_matrices.argtypes = [C.POINTER(Case), C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]
+            L.orc_fe_forward.argtypes = [C.POINTER(Case), _dp, C.c_int, C.c_int, _dp, C.c_void_p]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -323,3 +327,26 @@ def polish(case: Case, pm: Pmap, U, x_dk, steps: int, n_cand: int = 16, alpha0: 
     if rc:
         raise ValueError("orc_polish failed")
     return x, S
+
+
+def fe_matrices(case: Case):
+    """(M, K, C, geom) of the FE model; geom = thickness, width, mu, w1, w2,
+    alpha, beta."""
+    n = int(lib().orc_fe_dofs(C.byref(case)))
+    M, K, Cm = (np.zeros((n, n)) for _ in range(3))
+    geom = np.zeros(7)
+    rc = lib().orc_fe_matrices(C.byref(case), M.ctypes.data, K.ctypes.data, Cm.ctypes.data, None,
+                               geom.ctypes.data)
+    if rc:
+        raise ValueError("orc_fe_matrices failed")
+    return M, K, Cm, geom
+
+
+def fe_forward(case: Case, th, n_steps: int, sub: int = 1, want_setup: bool = False):
+    u = np.zeros(n_steps)
+    st = np.zeros(8)
+    rc = lib().orc_fe_forward(C.byref(case), np.ascontiguousarray(th, dtype=np.float64),
+                              int(n_steps), int(sub), u, st.ctypes.data)
+    if rc:
+        raise ValueError("orc_fe_forward failed")
+    return (u, st) if want_setup else u

@@ -562,3 +562,68 @@ def test_polish_descends_to_a_stationary_point(orc):
             np.testing.assert_allclose(xs[0], xt[0], atol=1e-3)
     # the valley coordinate moves towards the optimum
     assert np.all(np.abs(xs[1] - xt[1]) < np.abs(x0[1] - xt[1]))
+
+
+# --------------------------------------------------------------------------
+# Finite-element cantilever (reading R13)
+# --------------------------------------------------------------------------
+def test_fe_static_stiffness_and_frequencies(orc):
+    """Cubic Hermite elements are exact for a static tip load: tip compliance
+    L^3/(3EI) = 1/k.  The first two frequencies converge to the
+    Euler-Bernoulli values (f1 target, ratio (b2/b1)^2); Rayleigh damping
+    gives both modes Q."""
+    w = W.get("c5")
+    c = orc.make_case(w)
+    M, K, Cm, geom = orc.fe_matrices(c)
+    n = M.shape[0]
+    assert n == 64
+    e = np.zeros(n)
+    e[-2] = 1.0
+    assert np.linalg.solve(K, e)[-2] * w["k"] == pytest.approx(1.0, rel=1e-9)
+    thick, width, mu, w1, w2, alpha, beta = geom
+    assert w1 / (2 * math.pi) == pytest.approx(w["f1_hz"], rel=1e-6)
+    b = [orc.beam_root(1), orc.beam_root(2)]
+    assert w2 / w1 == pytest.approx((b[1] / b[0]) ** 2, rel=1e-5)
+    # the generalized eigenvalues by an independent library routine
+    ev = scipy.linalg.eigh(K, M, eigvals_only=True)
+    np.testing.assert_allclose(np.sqrt(ev[:2]), [w1, w2], rtol=1e-8)
+    for wi in (w1, w2):
+        assert alpha / (2 * wi) + beta * wi / 2 == pytest.approx(1 / (2 * w["Q"]), rel=1e-12)
+    np.testing.assert_allclose(Cm, alpha * M + beta * K, rtol=1e-13)
+    assert thick == pytest.approx(3.3387e-6, rel=1e-4)
+    assert width == pytest.approx(47.708e-6, rel=1e-4)
+    assert mu == pytest.approx(w["rho"] * thick * width, rel=1e-12)
+
+
+def test_fe_agrees_with_modal_model(orc):
+    """The same cantilever as 32 Hermite elements (Newmark) and as 3
+    Euler-Bernoulli modes (RK4), DMT tip force, 5 cycles: the tip
+    deflections agree to 1 % (higher modes, Rayleigh damping of mode 3 and
+    Newmark's period error make up the difference)."""
+    w = W.get("c5")
+    c, pm = orc.make_case(w), orc.make_pmap(w)
+    th = orc.map_x(pm, np.full(4, 0.5))
+    u_fe = orc.fe_forward(c, th, 5 * 512)
+    cm = orc.make_case(W.get("c2", spc=512))
+    u_m = orc.forward(cm, th, 5 * 512)
+    assert np.linalg.norm(u_fe - u_m) / np.linalg.norm(u_m) < 1e-2
+    assert w["Zc"] + u_fe.min() < th[3]          # the tip reaches contact
+
+
+def test_fe_newmark_second_order(orc):
+    """Step halving without tip force: the FE cantilever driven from its free
+    steady state converges at second order (Newmark average acceleration),
+    towards A0 cos(w t).  (A tip spring excites the stiff, overdamped
+    element modes, which this non-L-stable scheme rings through; that part
+    converges more slowly and is not a test of the order.)"""
+    def traj(spc):
+        w = W.get("c5", force="linear_spring", spc=spc, free=[(0, 0.0, 20.0, False),
+                  (1, 10e-9, 20e-9, False)], fixed=[0.0] * 5)
+        u, st = orc.fe_forward(orc.make_case(w), np.zeros(5), 3 * spc, want_setup=True)
+        t = st[6] * np.arange(1, 3 * spc + 1)
+        return u[spc - 1::spc], np.max(np.abs(u - w["A0"] * np.cos(st[0] * t))) / w["A0"]
+    r = [traj(s) for s in (256, 512, 1024)]
+    e = [x[0] for x in r]
+    order = math.log2(np.max(np.abs(e[0] - e[1])) / np.max(np.abs(e[1] - e[2])))
+    assert order > 1.8
+    assert r[2][1] < r[1][1] < r[0][1] < 1e-3
