@@ -48,4 +48,26 @@ struct KConst {
     double k, s1, tau;
 };
 
+// Finite-element cantilever (cubic Hermite elements, clamped node removed)
+// advanced by Newmark's average-acceleration scheme in increment form:
+//   delta_{n+1} = delta_n + B1 u_n + D2 delta_n + b G_n + c (F_{n+1} + 2F_n + F_{n-1})
+//   u_{n+1}     = u_n + delta_{n+1}
+// with B1 = -h^2 S^-1 K, D2 = -h S^-1 C, S = M + h/2 C + h^2/4 K, b = S^-1 M r
+// (G_n = table_{n+1} + 2 table_n + table_{n-1}, the table holding
+// h^2/4 g in nm) and c = (h^2/4) k S^-1 e_tip (force in units of k * 1 nm).
+// B1, D2, b, c are built on the device, per block, in FP64.
+#define AFM_FE_MAXN 64      // DOFs (2 per node)
+#define AFM_FE_BATCH 64     // particles per block of the FP32 / TF32 kernels
+
+struct FeConst {
+    int ne, n, spc, n_steps, tip;
+    double mu, EI, he;          // mass per length, bending stiffness, element length (SI)
+    double alpha, beta, h;      // Rayleigh coefficients, Newmark step (s)
+    double cscale;              // (h^2 / 4) k
+    double Zc;                  // rest gap [nm]
+    double drive_amp, drive_phase;   // table_j = drive_amp sin(2 pi j / spc + phase)
+    double u0[AFM_FE_MAXN], d0[AFM_FE_MAXN];   // u_0 and u_0 - u_{-1} [nm]
+    KConst<float> pm;           // force law and parameter map (s1 = 1)
+};
+
 }  // namespace afm

@@ -75,6 +75,16 @@ cudaError_t launch_polish_final(const KConst<double>& K, int Kn, int iters, cons
                                 const float* S, const int* idx, const float* U, const int* flags,
                                 void* result, cudaStream_t st);
 
+// finite-element cantilever
+cudaError_t launch_fe_forward_f32(const FeConst& F, const float* x, int P, float* defl,
+                                  const float* U, float* S, cudaStream_t st);
+cudaError_t launch_fe_forward_f64(const FeConst& F, const double* x, int P, double* defl,
+                                  const double* U, double* S, cudaStream_t st);
+cudaError_t launch_fe_invert_iter(const FeConst& F, const PsoConst& pc, const SwarmPtrs& sw,
+                                  const float* U, float* history, int it, cudaStream_t st);
+cudaError_t launch_fe_invert_final(const FeConst& F, const PsoConst& pc, const SwarmPtrs& sw,
+                                   const float* U, float* history, void* result, cudaStream_t st);
+
 // particle swarm
 cudaError_t launch_pso_init(const PsoConst& pc, const SwarmPtrs& sw, cudaStream_t st);
 cudaError_t launch_pso_best(const PsoConst& pc, const SwarmPtrs& sw, const float* S, int it,

@@ -183,13 +183,215 @@ void fill_kconst(const afm_problem& pr, int spc, int n_steps, KConst<T>& K) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
+// ---------------------------------------------------------------------------
+// Finite-element set-up (host, FP64): section from the targets, element
+// assembly, the two lowest frequencies (Householder tridiagonalisation and
+// Sturm bisection of L^-1 K L^-T), Rayleigh damping, the free steady state
+// (complex solve) as initial state, and the drive table scale.
+// ---------------------------------------------------------------------------
+void householder_tridiag(std::vector<double>& A, int n, std::vector<double>& d,
+                         std::vector<double>& e) {
+    std::vector<double> v(n), p(n), q(n);
+    for (int k = 0; k + 2 < n; ++k) {
+        double alpha = 0.0;
+        for (int i = k + 1; i < n; ++i) alpha += A[i * n + k] * A[i * n + k];
+        alpha = std::sqrt(alpha);
+        if (alpha == 0.0) continue;
+        if (A[(k + 1) * n + k] > 0) alpha = -alpha;
+        for (int i = 0; i < n; ++i) v[i] = i <= k ? 0.0 : A[i * n + k];
+        v[k + 1] -= alpha;
+        double vn2 = 0.0;
+        for (int i = 0; i < n; ++i) vn2 += v[i] * v[i];
+        if (vn2 == 0.0) continue;
+        for (int i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int j = 0; j < n; ++j) t += A[i * n + j] * v[j];
+            p[i] = 2.0 * t / vn2;
+        }
+        double K = 0.0;
+        for (int i = 0; i < n; ++i) K += v[i] * p[i];
+        K /= vn2;
+        for (int i = 0; i < n; ++i) q[i] = p[i] - K * v[i];
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) A[i * n + j] -= v[i] * q[j] + q[i] * v[j];
+    }
+    d.assign(n, 0.0);
+    e.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) d[i] = A[i * n + i];
+    for (int i = 0; i + 1 < n; ++i) e[i] = A[(i + 1) * n + i];
+}
+
+int sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+    int cnt = 0;
+    double q = d[0] - x;
+    if (q < 0) ++cnt;
+    for (size_t i = 1; i < d.size(); ++i) {
+        if (q == 0.0) q = 1e-300;
+        q = d[i] - x - e[i - 1] * e[i - 1] / q;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+double kth_eigenvalue(const std::vector<double>& d, const std::vector<double>& e, int k) {
+    double lo = 1e300, hi = -1e300;
+    const int n = (int)d.size();
+    for (int i = 0; i < n; ++i) {
+        double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(e[i]) : 0.0);
+        lo = std::min(lo, d[i] - r);
+        hi = std::max(hi, d[i] + r);
+    }
+    for (int it = 0; it < 300; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(d, e, mid) > k) hi = mid; else lo = mid;
+        if (hi - lo <= 1e-15 * std::fabs(hi)) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+afm_status fe_setup(const afm_problem& pr, int spc, int n_steps, afm::FeConst& F) {
+    std::memset(&F, 0, sizeof(F));
+    const int ne = pr.n_elem, n = 2 * ne;
+    const double L = pr.L_m, E = pr.E_Pa, k = pr.k_N_per_m;
+    const double I = k * L * L * L / (3.0 * E);
+    const double b1 = beam_root(1) / L;
+    const double w1t = 2.0 * kPi * pr.f1_hz;
+    const double mu = E * I * b1 * b1 * b1 * b1 / (w1t * w1t);
+    const double he = L / ne;
+    std::vector<double> M((size_t)n * n, 0.0), K((size_t)n * n, 0.0);
+    const double me[16] = {156, 22 * he, 54, -13 * he, 22 * he, 4 * he * he, 13 * he, -3 * he * he,
+                           54, 13 * he, 156, -22 * he, -13 * he, -3 * he * he, -22 * he, 4 * he * he};
+    const double ke[16] = {12, 6 * he, -12, 6 * he, 6 * he, 4 * he * he, -6 * he, 2 * he * he,
+                           -12, -6 * he, 12, -6 * he, 6 * he, 2 * he * he, -6 * he, 4 * he * he};
+    const double ms = mu * he / 420.0, ks = E * I / (he * he * he);
+    for (int e = 0; e < ne; ++e)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                const int i = 2 * e + a - 2, j = 2 * e + b - 2;   // drop the clamped node
+                if (i < 0 || j < 0) continue;
+                M[(size_t)i * n + j] += ms * me[a * 4 + b];
+                K[(size_t)i * n + j] += ks * ke[a * 4 + b];
+            }
+    // two lowest eigenvalues of K x = w^2 M x
+    std::vector<double> Lc((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s2 = M[(size_t)i * n + j];
+            for (int q = 0; q < j; ++q) s2 -= Lc[(size_t)i * n + q] * Lc[(size_t)j * n + q];
+            if (i == j) {
+                if (!(s2 > 0)) return fail(AFM_ERR_INVALID_ARG, "FE mass matrix not positive definite");
+                Lc[(size_t)i * n + i] = std::sqrt(s2);
+            } else {
+                Lc[(size_t)i * n + j] = s2 / Lc[(size_t)j * n + j];
+            }
+        }
+    std::vector<double> T((size_t)n * n), B((size_t)n * n);
+    for (int col = 0; col < n; ++col)
+        for (int i = 0; i < n; ++i) {
+            double s2 = K[(size_t)i * n + col];
+            for (int q = 0; q < i; ++q) s2 -= Lc[(size_t)i * n + q] * T[(size_t)q * n + col];
+            T[(size_t)i * n + col] = s2 / Lc[(size_t)i * n + i];
+        }
+    for (int row = 0; row < n; ++row)
+        for (int i = 0; i < n; ++i) {
+            double s2 = T[(size_t)row * n + i];
+            for (int q = 0; q < i; ++q) s2 -= Lc[(size_t)i * n + q] * B[(size_t)row * n + q];
+            B[(size_t)row * n + i] = s2 / Lc[(size_t)i * n + i];
+        }
+    std::vector<double> d, e;
+    householder_tridiag(B, n, d, e);
+    const double w1 = std::sqrt(kth_eigenvalue(d, e, 0));
+    const double w2 = n > 1 ? std::sqrt(kth_eigenvalue(d, e, 1)) : 3.0 * w1;
+    const double zeta = 1.0 / (2.0 * pr.Q[0]);
+    const double beta = 2.0 * zeta / (w1 + w2), alpha = beta * w1 * w2;
+    const double w = w1, h = 2.0 * kPi / (w * spc);
+    const int tip = n - 2;
+    // free steady state: (K - w^2 M + i w C) X = M r
+    std::vector<std::complex<double>> Z((size_t)n * n), X(n);
+    for (int i = 0; i < n; ++i) {
+        double mr = 0.0;
+        for (int j = 0; j < n; j += 2) mr += M[(size_t)i * n + j];
+        X[i] = mr;
+        for (int j = 0; j < n; ++j) {
+            const double m_ = M[(size_t)i * n + j], k_ = K[(size_t)i * n + j];
+            Z[(size_t)i * n + j] = std::complex<double>(k_ - w * w * m_, w * (alpha * m_ + beta * k_));
+        }
+    }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int i = c + 1; i < n; ++i)
+            if (std::abs(Z[(size_t)i * n + c]) > std::abs(Z[(size_t)piv * n + c])) piv = i;
+        if (piv != c) {
+            for (int j = 0; j < n; ++j) std::swap(Z[(size_t)c * n + j], Z[(size_t)piv * n + j]);
+            std::swap(X[c], X[piv]);
+        }
+        for (int i = c + 1; i < n; ++i) {
+            const std::complex<double> f = Z[(size_t)i * n + c] / Z[(size_t)c * n + c];
+            for (int j = c; j < n; ++j) Z[(size_t)i * n + j] -= f * Z[(size_t)c * n + j];
+            X[i] -= f * X[c];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        for (int j = i + 1; j < n; ++j) X[i] -= Z[(size_t)i * n + j] * X[j];
+        X[i] /= Z[(size_t)i * n + i];
+    }
+    const double a = pr.A0_m / (w * w * std::abs(X[tip]));
+    const double psi = kPi / 2 - std::arg(X[tip]);
+    for (int i = 0; i < AFM_FE_MAXN; ++i) {
+        if (i < n) {
+            const double u0 = (a * w * w * X[i] * std::polar(1.0, psi)).imag() / 1e-9;
+            const double um = (a * w * w * X[i] * std::polar(1.0, psi - w * h)).imag() / 1e-9;
+            F.u0[i] = u0;
+            F.d0[i] = u0 - um;
+        }
+    }
+    F.ne = ne;
+    F.n = n;
+    F.spc = spc;
+    F.n_steps = n_steps;
+    F.tip = tip;
+    F.mu = mu;
+    F.EI = E * I;
+    F.he = he;
+    F.alpha = alpha;
+    F.beta = beta;
+    F.h = h;
+    F.cscale = 0.25 * h * h * k;
+    F.Zc = pr.Zc_m / 1e-9;
+    F.drive_amp = 0.25 * h * h * a * w * w / 1e-9;
+    F.drive_phase = psi;
+    KConst<float>& P = F.pm;
+    std::memset(&P, 0, sizeof(P));
+    P.force = pr.force;
+    P.D = pr.n_free;
+    for (int s5 = 0; s5 < AFM_MAXD; ++s5) P.fixed[s5] = pr.fixed[s5];
+    for (int dd = 0; dd < pr.n_free; ++dd) {
+        P.slot[dd] = pr.slot[dd];
+        P.logs[dd] = pr.log_scale[dd] ? 1 : 0;
+        P.lo[dd] = P.logs[dd] ? std::log10(pr.lo[dd]) : pr.lo[dd];
+        P.span[dd] = P.logs[dd] ? std::log10(pr.hi[dd]) - std::log10(pr.lo[dd]) : pr.hi[dd] - pr.lo[dd];
+    }
+    P.k = k;
+    P.s1 = 1.0;
+    P.tau = 1.0;
+    return AFM_OK;
+}
+
 afm_status check_problem(const afm_problem* pr) {
     if (!pr) return fail(AFM_ERR_INVALID_ARG, "problem is NULL");
-    if (pr->model == AFM_FE_HERMITE)
-        return fail(AFM_ERR_UNSUPPORTED, "model FE_HERMITE is not available in this call");
-    if (pr->model != AFM_POINT_MASS && pr->model != AFM_MODAL_EB)
+    if (pr->model != AFM_POINT_MASS && pr->model != AFM_MODAL_EB && pr->model != AFM_FE_HERMITE)
         return fail(AFM_ERR_INVALID_ARG, "unknown model %d", pr->model);
-    const int m = pr->model == AFM_POINT_MASS ? 1 : pr->n_modes;
+    if (pr->model == AFM_FE_HERMITE) {
+        if (pr->n_elem < 1 || 2 * pr->n_elem > AFM_FE_MAXN)
+            return fail(AFM_ERR_INVALID_ARG, "n_elem %d outside 1..%d", pr->n_elem, AFM_FE_MAXN / 2);
+        if (!finite_pos(pr->L_m) || !finite_pos(pr->E_Pa) || !finite_pos(pr->rho_kg_m3))
+            return fail(AFM_ERR_INVALID_ARG, "FE beam needs L_m, E_Pa, rho_kg_m3 > 0");
+        if (pr->newmark_beta != 0.25)
+            return fail(AFM_ERR_UNSUPPORTED, "only Newmark beta = 1/4 (average acceleration)");
+        if (pr->force != AFM_LINEAR_SPRING && pr->force != AFM_DMT && pr->force != AFM_HOOKE)
+            return fail(AFM_ERR_UNSUPPORTED, "FE beam supports rate-independent force laws only");
+    }
+    const int m = pr->model == AFM_POINT_MASS ? 1 : (pr->model == AFM_FE_HERMITE ? 1 : pr->n_modes);
     if (m < 1 || m > AFM_MAX_MODES) return fail(AFM_ERR_INVALID_ARG, "n_modes %d outside 1..8", m);
     if (!finite_pos(pr->f1_hz)) return fail(AFM_ERR_INVALID_ARG, "f1_hz must be > 0");
     if (!finite_pos(pr->k_N_per_m)) return fail(AFM_ERR_INVALID_ARG, "k_N_per_m must be > 0");
@@ -232,6 +434,12 @@ afm_status check_problem(const afm_problem* pr) {
             if (!ok) return fail(AFM_ERR_INVALID_ARG, "DMT needs R and a0 > 0");
         }
     }
+    return AFM_OK;
+}
+
+afm_status modal_only(const afm_problem* pr, const char* what) {
+    if (pr->model == AFM_FE_HERMITE)
+        return fail(AFM_ERR_UNSUPPORTED, "%s: the FE beam runs in afm_forward_batch(_f64) and afm_invert", what);
     return AFM_OK;
 }
 
@@ -397,6 +605,7 @@ afm_status prepare_invert(afm_ctx* ctx, const afm_problem* prob, const afm_pso_c
                           size_t* scratch_bytes, int* device) {
     afm_status st = check_problem(prob);
     if (st) return st;
+    if ((st = modal_only(prob, "afm_invert_noalloc"))) return st;
     if ((st = check_ctx(ctx))) return st;
     if ((st = check_pso(cfg, prob->n_free))) return st;
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, *Kf);
@@ -512,9 +721,16 @@ afm_status afm_forward_batch(afm_ctx* ctx, const afm_problem* prob, const float*
     if (prob->n_free > 0 && !x) return fail(AFM_ERR_INVALID_ARG, "x is NULL");
     if (S && !U) return fail(AFM_ERR_INVALID_ARG, "S requested without a record U");
     if (!S && !defl) return fail(AFM_ERR_INVALID_ARG, "nothing to compute (defl and S NULL)");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (prob->model == AFM_FE_HERMITE) {
+        afm::FeConst F;
+        if ((st = fe_setup(*prob, prob->steps_per_cycle, prob->n_steps, F))) return st;
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_fe_forward_f32(F, x, P, defl, U, S, s); }),
+                 "FE forward kernel");
+        return AFM_OK;
+    }
     KConst<float> K;
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_f32(K, x, P, defl, U, S, nullptr, s); }),
              "forward kernel");
     return AFM_OK;
@@ -530,9 +746,15 @@ afm_status afm_forward_batch_f64(afm_ctx* ctx, const afm_problem* prob, const do
     if (prob->n_free > 0 && !x) return fail(AFM_ERR_INVALID_ARG, "x is NULL");
     if (S && !U) return fail(AFM_ERR_INVALID_ARG, "S requested without a record U");
     if (!S && !defl) return fail(AFM_ERR_INVALID_ARG, "nothing to compute (defl and S NULL)");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (prob->model == AFM_FE_HERMITE) {
+        afm::FeConst F;
+        if ((st = fe_setup(*prob, prob->steps_per_cycle, prob->n_steps, F))) return st;
+        AFM_CUDA(afm::launch_fe_forward_f64(F, x, P, defl, U, S, s), "FE forward f64 kernel");
+        return AFM_OK;
+    }
     KConst<double> K;
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     AFM_CUDA(afm::launch_forward_f64(K, x, P, defl, U, S, nullptr, s), "forward f64 kernel");
     return AFM_OK;
 }
@@ -633,12 +855,22 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
     sw.gkey[0] = reinterpret_cast<unsigned long long*>(ws + L.gkey);
     sw.gkey[1] = sw.gkey[0] + 1;
     sw.flags = reinterpret_cast<int*>(ws + L.flags);
+    const afm::PsoConst pc = pso_const(*cfg, D);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (prob->model == AFM_FE_HERMITE) {
+        afm::FeConst F;
+        if ((st = fe_setup(*prob, prob->steps_per_cycle, prob->n_steps, F))) return st;
+        AFM_CUDA(afm::launch_pso_init(pc, sw, s), "pso init kernel");
+        for (int it = 0; it <= cfg->iters; ++it)
+            AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_fe_invert_iter(F, pc, sw, U, history, it, s); }),
+                     "FE invert iteration kernel");
+        AFM_CUDA(afm::launch_fe_invert_final(F, pc, sw, U, history, result, s), "FE invert final kernel");
+        return AFM_OK;
+    }
     KConst<float> Kf;
     KConst<double> Kd;
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kf);
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kd);
-    const afm::PsoConst pc = pso_const(*cfg, D);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     AFM_CUDA(afm::launch_pso_init(pc, sw, s), "pso init kernel");
     for (int it = 0; it <= cfg->iters; ++it)
         AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_invert_iter(Kf, pc, sw, U, history, it, s); }),
@@ -663,6 +895,7 @@ afm_status afm_adjoint(afm_ctx* ctx, const afm_problem* prob, const float* x, in
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
+    if ((st = modal_only(prob, "afm_adjoint"))) return st;
     if ((st = check_ctx(ctx))) return st;
     if (P < 1 || prob->n_free < 1) return fail(AFM_ERR_INVALID_ARG, "P >= 1 and n_free >= 1 needed");
     if (!x || !U || !S || !dS_dx || !workspace)
@@ -740,6 +973,7 @@ afm_status afm_polish(afm_ctx* ctx, const afm_problem* prob, const float* U, flo
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
+    if ((st = modal_only(prob, "afm_polish"))) return st;
     if ((st = check_ctx(ctx))) return st;
     if (!U || !x || !S || !workspace || K < 1 || steps < 0 || prob->n_free < 1)
         return fail(AFM_ERR_INVALID_ARG, "NULL array, K < 1, steps < 0 or no free parameter");
@@ -778,6 +1012,7 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
+    if ((st = modal_only(prob, "afm_invert_polished"))) return st;
     if ((st = check_ctx(ctx))) return st;
     if ((st = check_pso(cfg, prob->n_free))) return st;
     if (!U || !result || !workspace || polish_steps < 0)
@@ -832,6 +1067,7 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
+    if ((st = modal_only(prob, "afm_invert_batch"))) return st;
     if ((st = check_ctx(ctx))) return st;
     if ((st = check_pso(cfg, prob->n_free))) return st;
     if (!U_cat || !off || !results || !workspace || n_pix < 1)
@@ -924,6 +1160,7 @@ afm_status afm_synth_records(afm_ctx* ctx, const afm_problem* prob, const double
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
+    if ((st = modal_only(prob, "afm_synth_records"))) return st;
     if ((st = check_ctx(ctx))) return st;
     if (n_pix < 1 || !off || !U_cat || (prob->n_free > 0 && !x_truth))
         return fail(AFM_ERR_INVALID_ARG, "n_pix >= 1 and non-NULL off, U_cat, x_truth needed");
