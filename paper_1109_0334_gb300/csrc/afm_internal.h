@@ -49,24 +49,30 @@ struct KConst {
 };
 
 // Finite-element cantilever (cubic Hermite elements, clamped node removed)
-// advanced by Newmark's average-acceleration scheme in increment form:
-//   delta_{n+1} = delta_n + B1 u_n + D2 delta_n + b G_n + c (F_{n+1} + 2F_n + F_{n-1})
-//   u_{n+1}     = u_n + delta_{n+1}
-// with B1 = -h^2 S^-1 K, D2 = -h S^-1 C, S = M + h/2 C + h^2/4 K, b = S^-1 M r
-// (G_n = table_{n+1} + 2 table_n + table_{n-1}, the table holding
-// h^2/4 g in nm) and c = (h^2/4) k S^-1 e_tip (force in units of k * 1 nm).
-// B1, D2, b, c are built on the device, per block, in FP64.
-#define AFM_FE_MAXN 64      // DOFs (2 per node)
-#define AFM_FE_BATCH 64     // particles per block of the FP32 / TF32 kernels
+// advanced by Newmark's average-acceleration scheme (beta = 1/4, gamma = 1/2)
+// with the tip force implicit.  With Rayleigh damping, M, K and C are
+// diagonal in the M-orthonormal eigenbasis (u = Phi z, Phi^T M Phi = I), so
+// the scheme decouples exactly into one scalar recursion per mode, written in
+// increment form (delta = z_n - z_{n-1}):
+//   delta_{n+1} = delta_n + b1_i z_n + d2_i delta_n + g_i G_n
+//                 + f_i (F_{n+1} + 2 F_n + F_{n-1}),   z_{n+1} = z_n + delta_{n+1}
+// with s_i = 1 + h/2 c_i + h^2/4 lambda_i, b1_i = -h^2 lambda_i / s_i,
+// d2_i = -h c_i / s_i (c_i = alpha + beta lambda_i), g_i = (phi_i^T M r) / s_i
+// (G_n = table_{n+1} + 2 table_n + table_{n-1}, table = h^2/4 g in nm) and
+// f_i = (h^2/4) k phi_i(tip) / s_i (force in units of k * 1 nm); the tip
+// deflection is sum_i phi_i(tip) z_i.
+#define AFM_FE_MAXN 64      // DOFs = modes (2 per node)
+#define AFM_FE_LANES 8      // lanes per particle in the FE kernels
 
 struct FeConst {
-    int ne, n, spc, n_steps, tip;
-    double mu, EI, he;          // mass per length, bending stiffness, element length (SI)
-    double alpha, beta, h;      // Rayleigh coefficients, Newmark step (s)
-    double cscale;              // (h^2 / 4) k
+    int ne, n, spc, n_steps;
+    double h;                   // Newmark step (s)
     double Zc;                  // rest gap [nm]
     double drive_amp, drive_phase;   // table_j = drive_amp sin(2 pi j / spc + phase)
-    double u0[AFM_FE_MAXN], d0[AFM_FE_MAXN];   // u_0 and u_0 - u_{-1} [nm]
+    double b1[AFM_FE_MAXN], d2[AFM_FE_MAXN], g[AFM_FE_MAXN], f[AFM_FE_MAXN], pt[AFM_FE_MAXN];
+    double z0[AFM_FE_MAXN], dz0[AFM_FE_MAXN];   // initial modal state and increment
+    double ctip;                // sum_i pt_i f_i: tip response to the step's own tip force
+    double utip0, utipm;        // tip deflection at steps 0 and -1 [nm]
     KConst<float> pm;           // force law and parameter map (s1 = 1)
 };
 

@@ -189,23 +189,27 @@ bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 // Sturm bisection of L^-1 K L^-T), Rayleigh damping, the free steady state
 // (complex solve) as initial state, and the drive table scale.
 // ---------------------------------------------------------------------------
+// Householder reduction of the symmetric A (row-major, destroyed) to
+// tridiagonal (d, e), accumulating the orthogonal Q with A_orig = Q T Q^T.
 void householder_tridiag(std::vector<double>& A, int n, std::vector<double>& d,
-                         std::vector<double>& e) {
+                         std::vector<double>& e, std::vector<double>& Q) {
     std::vector<double> v(n), p(n), q(n);
+    Q.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
     for (int k = 0; k + 2 < n; ++k) {
         double alpha = 0.0;
-        for (int i = k + 1; i < n; ++i) alpha += A[i * n + k] * A[i * n + k];
+        for (int i = k + 1; i < n; ++i) alpha += A[(size_t)i * n + k] * A[(size_t)i * n + k];
         alpha = std::sqrt(alpha);
         if (alpha == 0.0) continue;
-        if (A[(k + 1) * n + k] > 0) alpha = -alpha;
-        for (int i = 0; i < n; ++i) v[i] = i <= k ? 0.0 : A[i * n + k];
+        if (A[(size_t)(k + 1) * n + k] > 0) alpha = -alpha;
+        for (int i = 0; i < n; ++i) v[i] = i <= k ? 0.0 : A[(size_t)i * n + k];
         v[k + 1] -= alpha;
         double vn2 = 0.0;
         for (int i = 0; i < n; ++i) vn2 += v[i] * v[i];
         if (vn2 == 0.0) continue;
         for (int i = 0; i < n; ++i) {
             double t = 0.0;
-            for (int j = 0; j < n; ++j) t += A[i * n + j] * v[j];
+            for (int j = 0; j < n; ++j) t += A[(size_t)i * n + j] * v[j];
             p[i] = 2.0 * t / vn2;
         }
         double K = 0.0;
@@ -213,12 +217,19 @@ void householder_tridiag(std::vector<double>& A, int n, std::vector<double>& d,
         K /= vn2;
         for (int i = 0; i < n; ++i) q[i] = p[i] - K * v[i];
         for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) A[i * n + j] -= v[i] * q[j] + q[i] * v[j];
+            for (int j = 0; j < n; ++j) A[(size_t)i * n + j] -= v[i] * q[j] + q[i] * v[j];
+        // Q <- Q H, H = I - 2 v v^T / |v|^2
+        for (int i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int j = 0; j < n; ++j) t += Q[(size_t)i * n + j] * v[j];
+            t *= 2.0 / vn2;
+            for (int j = 0; j < n; ++j) Q[(size_t)i * n + j] -= t * v[j];
+        }
     }
     d.assign(n, 0.0);
     e.assign(n, 0.0);
-    for (int i = 0; i < n; ++i) d[i] = A[i * n + i];
-    for (int i = 0; i + 1 < n; ++i) e[i] = A[(i + 1) * n + i];
+    for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
+    for (int i = 0; i + 1 < n; ++i) e[i] = A[(size_t)(i + 1) * n + i];
 }
 
 int sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
@@ -233,6 +244,7 @@ int sturm_count(const std::vector<double>& d, const std::vector<double>& e, doub
     return cnt;
 }
 
+// k-th smallest eigenvalue of the tridiagonal (d, e) by Sturm bisection.
 double kth_eigenvalue(const std::vector<double>& d, const std::vector<double>& e, int k) {
     double lo = 1e300, hi = -1e300;
     const int n = (int)d.size();
@@ -241,12 +253,56 @@ double kth_eigenvalue(const std::vector<double>& d, const std::vector<double>& e
         lo = std::min(lo, d[i] - r);
         hi = std::max(hi, d[i] + r);
     }
-    for (int it = 0; it < 300; ++it) {
+    for (int it = 0; it < 400; ++it) {
         const double mid = 0.5 * (lo + hi);
         if (sturm_count(d, e, mid) > k) hi = mid; else lo = mid;
-        if (hi - lo <= 1e-15 * std::fabs(hi)) break;
+        if (hi - lo <= 1e-16 * std::fabs(hi)) break;
     }
     return 0.5 * (lo + hi);
+}
+
+// Eigenvector of the tridiagonal (d, e) for eigenvalue lam, by two steps of
+// inverse iteration (tridiagonal elimination with partial pivoting).
+void tridiag_eigvec(const std::vector<double>& d, const std::vector<double>& e, double lam,
+                    std::vector<double>& x) {
+    const int n = (int)d.size();
+    const double shift = lam + 1e-13 * std::fabs(lam) + 1e-300;
+    x.assign(n, 1.0);
+    for (int iter = 0; iter < 3; ++iter) {
+        // rows: (sub, diag, sup, sup2) after pivoting
+        std::vector<double> a(n, 0.0), b(n), c(n, 0.0), c2(n, 0.0), r = x;
+        for (int i = 0; i < n; ++i) {
+            a[i] = i > 0 ? e[i - 1] : 0.0;
+            b[i] = d[i] - shift;
+            c[i] = i + 1 < n ? e[i] : 0.0;
+        }
+        for (int i = 0; i + 1 < n; ++i) {
+            // eliminate a[i+1] using row i, pivoting rows i and i+1 if needed
+            if (std::fabs(a[i + 1]) > std::fabs(b[i])) {
+                std::swap(b[i], a[i + 1]);
+                std::swap(c[i], b[i + 1]);
+                std::swap(c2[i], c[i + 1]);
+                std::swap(r[i], r[i + 1]);
+            }
+            if (b[i] == 0.0) b[i] = 1e-300;
+            const double m = a[i + 1] / b[i];
+            a[i + 1] = 0.0;
+            b[i + 1] -= m * c[i];
+            c[i + 1] -= m * c2[i];
+            r[i + 1] -= m * r[i];
+        }
+        if (b[n - 1] == 0.0) b[n - 1] = 1e-300;
+        for (int i = n - 1; i >= 0; --i) {
+            double t = r[i];
+            if (i + 1 < n) t -= c[i] * x[i + 1];
+            if (i + 2 < n) t -= c2[i] * x[i + 2];
+            x[i] = t / b[i];
+        }
+        double nrm = 0.0;
+        for (double v : x) nrm += v * v;
+        nrm = std::sqrt(nrm);
+        for (double& v : x) v /= nrm;
+    }
 }
 
 afm_status fe_setup(const afm_problem& pr, int spc, int n_steps, afm::FeConst& F) {
@@ -272,7 +328,8 @@ afm_status fe_setup(const afm_problem& pr, int spc, int n_steps, afm::FeConst& F
                 M[(size_t)i * n + j] += ms * me[a * 4 + b];
                 K[(size_t)i * n + j] += ks * ke[a * 4 + b];
             }
-    // two lowest eigenvalues of K x = w^2 M x
+    // M-orthonormal eigenvectors: M = Lc Lc^T, B = Lc^-1 K Lc^-T = Q T Q^T,
+    // T y = lambda y, phi = Lc^-T Q y
     std::vector<double> Lc((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i)
         for (int j = 0; j <= i; ++j) {
@@ -298,65 +355,71 @@ afm_status fe_setup(const afm_problem& pr, int spc, int n_steps, afm::FeConst& F
             for (int q = 0; q < i; ++q) s2 -= Lc[(size_t)i * n + q] * B[(size_t)row * n + q];
             B[(size_t)row * n + i] = s2 / Lc[(size_t)i * n + i];
         }
-    std::vector<double> d, e;
-    householder_tridiag(B, n, d, e);
-    const double w1 = std::sqrt(kth_eigenvalue(d, e, 0));
-    const double w2 = n > 1 ? std::sqrt(kth_eigenvalue(d, e, 1)) : 3.0 * w1;
+    std::vector<double> d, e, Q;
+    householder_tridiag(B, n, d, e, Q);
+    std::vector<double> lam(n), Phi((size_t)n * n);   // Phi[i * n + mode]
+    std::vector<double> y, wv(n);
+    for (int md = 0; md < n; ++md) {
+        lam[md] = kth_eigenvalue(d, e, md);
+        tridiag_eigvec(d, e, lam[md], y);
+        for (int i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int j = 0; j < n; ++j) t += Q[(size_t)i * n + j] * y[j];
+            wv[i] = t;
+        }
+        for (int i = n - 1; i >= 0; --i) {   // Lc^T phi = w
+            double t = wv[i];
+            for (int j = i + 1; j < n; ++j) t -= Lc[(size_t)j * n + i] * Phi[(size_t)j * n + md];
+            Phi[(size_t)i * n + md] = t / Lc[(size_t)i * n + i];
+        }
+    }
+    const double wA = std::sqrt(lam[0]), wB = n > 1 ? std::sqrt(lam[1]) : 3.0 * wA;
     const double zeta = 1.0 / (2.0 * pr.Q[0]);
-    const double beta = 2.0 * zeta / (w1 + w2), alpha = beta * w1 * w2;
-    const double w = w1, h = 2.0 * kPi / (w * spc);
+    const double beta = 2.0 * zeta / (wA + wB), alpha = beta * wA * wB;
+    const double w = wA, h = 2.0 * kPi / (w * spc);
     const int tip = n - 2;
-    // free steady state: (K - w^2 M + i w C) X = M r
-    std::vector<std::complex<double>> Z((size_t)n * n), X(n);
-    for (int i = 0; i < n; ++i) {
-        double mr = 0.0;
-        for (int j = 0; j < n; j += 2) mr += M[(size_t)i * n + j];
-        X[i] = mr;
-        for (int j = 0; j < n; ++j) {
-            const double m_ = M[(size_t)i * n + j], k_ = K[(size_t)i * n + j];
-            Z[(size_t)i * n + j] = std::complex<double>(k_ - w * w * m_, w * (alpha * m_ + beta * k_));
-        }
+    // modal drive participation (M r), free steady state per mode, tip shape
+    std::vector<double> Mr(n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; j += 2) Mr[i] += M[(size_t)i * n + j];
+    std::complex<double> Htip(0.0, 0.0);
+    std::vector<std::complex<double>> Hm(n);
+    std::vector<double> Gam(n);
+    for (int md = 0; md < n; ++md) {
+        double gm = 0.0;
+        for (int i = 0; i < n; ++i) gm += Phi[(size_t)i * n + md] * Mr[i];
+        Gam[md] = gm;
+        const double cm = alpha + beta * lam[md];
+        Hm[md] = gm / std::complex<double>(lam[md] - w * w, w * cm);   // z = Hm a w^2 e^{i(wt+psi)}
+        Htip += Phi[(size_t)tip * n + md] * Hm[md];
     }
-    for (int c = 0; c < n; ++c) {
-        int piv = c;
-        for (int i = c + 1; i < n; ++i)
-            if (std::abs(Z[(size_t)i * n + c]) > std::abs(Z[(size_t)piv * n + c])) piv = i;
-        if (piv != c) {
-            for (int j = 0; j < n; ++j) std::swap(Z[(size_t)c * n + j], Z[(size_t)piv * n + j]);
-            std::swap(X[c], X[piv]);
-        }
-        for (int i = c + 1; i < n; ++i) {
-            const std::complex<double> f = Z[(size_t)i * n + c] / Z[(size_t)c * n + c];
-            for (int j = c; j < n; ++j) Z[(size_t)i * n + j] -= f * Z[(size_t)c * n + j];
-            X[i] -= f * X[c];
-        }
+    const double a = pr.A0_m / (w * w * std::abs(Htip));
+    const double psi = kPi / 2 - std::arg(Htip);
+    double ctip = 0.0;
+    for (int md = 0; md < AFM_FE_MAXN; ++md) {
+        if (md >= n) continue;
+        const double cm = alpha + beta * lam[md];
+        const double sm = 1.0 + 0.5 * h * cm + 0.25 * h * h * lam[md];
+        const double pt = Phi[(size_t)tip * n + md];
+        F.b1[md] = -h * h * lam[md] / sm;
+        F.d2[md] = -h * cm / sm;
+        F.g[md] = Gam[md] / sm;
+        F.f[md] = 0.25 * h * h * k * pt / sm;
+        F.pt[md] = pt;
+        ctip += pt * F.f[md];
+        const std::complex<double> z0 = a * w * w * Hm[md] * std::polar(1.0, psi) / 1e-9;
+        const std::complex<double> zm = a * w * w * Hm[md] * std::polar(1.0, psi - w * h) / 1e-9;
+        F.z0[md] = z0.imag();
+        F.dz0[md] = z0.imag() - zm.imag();
+        F.utip0 += pt * z0.imag();
+        F.utipm += pt * zm.imag();
     }
-    for (int i = n - 1; i >= 0; --i) {
-        for (int j = i + 1; j < n; ++j) X[i] -= Z[(size_t)i * n + j] * X[j];
-        X[i] /= Z[(size_t)i * n + i];
-    }
-    const double a = pr.A0_m / (w * w * std::abs(X[tip]));
-    const double psi = kPi / 2 - std::arg(X[tip]);
-    for (int i = 0; i < AFM_FE_MAXN; ++i) {
-        if (i < n) {
-            const double u0 = (a * w * w * X[i] * std::polar(1.0, psi)).imag() / 1e-9;
-            const double um = (a * w * w * X[i] * std::polar(1.0, psi - w * h)).imag() / 1e-9;
-            F.u0[i] = u0;
-            F.d0[i] = u0 - um;
-        }
-    }
+    F.ctip = ctip;
     F.ne = ne;
     F.n = n;
     F.spc = spc;
     F.n_steps = n_steps;
-    F.tip = tip;
-    F.mu = mu;
-    F.EI = E * I;
-    F.he = he;
-    F.alpha = alpha;
-    F.beta = beta;
     F.h = h;
-    F.cscale = 0.25 * h * h * k;
     F.Zc = pr.Zc_m / 1e-9;
     F.drive_amp = 0.25 * h * h * a * w * w / 1e-9;
     F.drive_phase = psi;
