@@ -70,6 +70,8 @@ struct FeConst {
     double Zc;                  // rest gap [nm]
     double drive_amp, drive_phase;   // table_j = drive_amp sin(2 pi j / spc + phase)
     double b1[AFM_FE_MAXN], d2[AFM_FE_MAXN], g[AFM_FE_MAXN], f[AFM_FE_MAXN], pt[AFM_FE_MAXN];
+    // b1 of the lowest AFM_FE_LANES modes carries a low word in FP32 (the
+    // resonant mode's frequency must be represented to ~1e-12)
     double z0[AFM_FE_MAXN], dz0[AFM_FE_MAXN];   // initial modal state and increment
     double ctip;                // sum_i pt_i f_i: tip response to the step's own tip force
     double utip0, utipm;        // tip deflection at steps 0 and -1 [nm]

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
     T* cg = cd2 + FEN;
     T* cf = cg + FEN;
     T* cpt = cf + FEN;
-    T* tab = cpt + FEN;
+    T* cb1lo = cpt + FEN;
+    T* tab = cb1lo + FEN;
     const int tid = threadIdx.x, lane = tid & (FEL - 1), grp = tid / FEL;
     for (int i = tid; i < FEN; i += blockDim.x) {
         cb1[i] = (T)F.b1[i];
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
         cg[i] = (T)F.g[i];
         cf[i] = (T)F.f[i];
         cpt[i] = (T)F.pt[i];
+        cb1lo[i] = (T)(F.b1[i] - (double)cb1[i]);
     }
     fe_table<T>(F, tab);
     const int D = F.pm.D;
@@ -186,6 +188,7 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
         for (int j = 0; j < FEM; ++j) {
             const int i = lane + FEL * j;
             T inc = fma(cb1[i], z[j], cd2[i] * dz[j]);
+            if (j == 0) inc = fma(cb1lo[i], z[j], inc);
             inc = fma(cg[i], G, inc);
             inc = fma(cf[i], Fo, inc);
             dk[j] = dz[j] + inc;
@@ -288,7 +291,7 @@ cudaError_t fe_dispatch(int force, Fn&& f) {
 
 template <typename T>
 size_t fe_smem(const FeConst& F) {
-    return sizeof(T) * (5 * (size_t)FEN + (size_t)F.spc);
+    return sizeof(T) * (6 * (size_t)FEN + (size_t)F.spc);
 }
 
 template <typename T, typename TU, int MODE, typename... Args>

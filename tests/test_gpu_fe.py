@@ -93,7 +93,17 @@ def test_fe_invert_parity(orc, afm):
     S_g = orc.misfit_batch(c, pm, r["x"][:D].reshape(-1, 1), U_m)[0]
     assert r["status"] == 0
     assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2
-    assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2
+    # FP64 re-evaluation: |S_gpu - S_oracle| <= |u_gpu - u_oracle| |2U - u_gpu - u_oracle|
+    # (Cauchy-Schwarz), with the trajectories' difference pinned at 1e-7 above
+    xw = r["x"][:D].reshape(-1, 1)
+    d64, _ = afm.forward_batch_f64(prob, torch.from_numpy(xw.copy()).cuda(), None)
+    torch.cuda.synchronize()
+    u_g = d64.cpu().numpy()[:, 0]
+    u_o = orc.fe_forward(c, orc.map_x(pm, xw[:, 0]), len(U32)) / NM
+    assert np.linalg.norm(u_g - u_o) <= 1e-7 * np.linalg.norm(u_o)
+    U = U32.astype(np.float64)
+    bound = np.linalg.norm(u_g - u_o) * np.linalg.norm(2 * U - u_g - u_o)
+    assert abs(r["S_f64"] - S_g / NM ** 2) <= bound + 1e-12 * S_g / NM ** 2
     assert np.all(np.diff(hist) <= 0)
     # a short swarm need not converge: require the GPU's optimum to be as good
     # as the oracle's to the misfit tolerance, or identical where it stopped
