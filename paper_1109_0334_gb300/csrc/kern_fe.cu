@@ -162,13 +162,14 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
     __syncthreads();
 
     // ---- modal state of this lane
-    T z[FEM], dz[FEM], cz[FEM];
+    T z[FEM], dz[FEM], cz[FEM], cdz[FEM];
 #pragma unroll
     for (int j = 0; j < FEM; ++j) {
         const int i = lane + FEL * j;
         z[j] = (T)F.z0[i];
         dz[j] = (T)F.dz0[i];
         cz[j] = (T)0;
+        cdz[j] = (T)0;
     }
     const T Zc = (T)F.Zc, ctip = (T)F.ctip;
     T Fn, Fm, dF;
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
         const int jp = jn + 1 == spc ? 0 : jn + 1, jm = jn == 0 ? spc - 1 : jn - 1;
         const T G = tab[jp] + (T)2 * tab[jn] + tab[jm];
         const T Fo = (T)2 * Fn + Fm;
-        T dk[FEM];
+        T incs[FEM];
         T tsum = (T)0;
 #pragma unroll
         for (int j = 0; j < FEM; ++j) {
@@ -191,19 +192,19 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
             if (j == 0) inc = fma(cb1lo[i], z[j], inc);
             inc = fma(cg[i], G, inc);
             inc = fma(cf[i], Fo, inc);
-            dk[j] = dz[j] + inc;
-            tsum = fma(cpt[i], z[j] + (dk[j] - cz[j]), tsum);
+            incs[j] = inc;
+            tsum = fma(cpt[i], z[j] + ((dz[j] + inc) - cz[j]), tsum);
         }
 #pragma unroll
         for (int o = FEL / 2; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
         T Fp;
         fe_newton<FORCE, T>(cfc, Zc, tsum, ctip, newton_it, Fp);
+        // compensated updates of both the increment and the modal coordinate
 #pragma unroll
         for (int j = 0; j < FEM; ++j) {
             const int i = lane + FEL * j;
-            const T dn = fma(cf[i], Fp, dk[j]);
-            kahan_add(z[j], cz[j], dn);
-            dz[j] = dn;
+            kahan_add(dz[j], cdz[j], fma(cf[i], Fp, incs[j]));
+            kahan_add(z[j], cz[j], dz[j]);
         }
         Fm = Fn;
         Fn = Fp;
