@@ -326,6 +326,56 @@ def run_c4(A, W, dev, flush):
 
 
 # ---------------------------------------------------------------------------
+# Finite-element cantilever inversion (32 Hermite elements, Newmark)
+# ---------------------------------------------------------------------------
+def run_c5(A, W, dev, peak_ops, flush, iters=None):
+    """One full FE inversion (8192 particles x 61 evaluations x 25 600 steps).
+    The record is the library's FE forward of a seeded truth at dt/4, sampled
+    every 4th step, plus seeded Gaussian noise (input generation only)."""
+    import numpy as np
+    import torch
+    spec = W.get("c5") if iters is None else W.get("c5", iters=iters)
+    D = len(spec["free"])
+    N = W.n_steps(spec)
+    rng = np.random.default_rng(spec["seed"])
+    xt = rng.uniform(0.1, 0.9, size=(D, 1)).astype(np.float32)
+    fine = A.make_problem(dict(spec, spc=spec["spc"] * 4), n_steps=N * 4)
+    defl, _ = A.forward_batch(fine, torch.from_numpy(xt).to(dev), None)
+    gen = torch.Generator(device=dev).manual_seed(spec["seed"])
+    U = (defl[3::4, 0] + (spec["sigma"] / 1e-9) * torch.randn(N, device=dev, generator=gen)).contiguous()
+    prob = A.make_problem(spec)
+    cfg = A.make_pso(spec)
+    A.invert(prob, U, A.make_pso(dict(spec, iters=1)))     # warm-up
+    torch.cuda.synchronize()
+    flush.zero_()
+    A.profile_enable(True)
+    A.profile_read()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res, _ = A.invert(prob, U, cfg)
+    e1.record()
+    e1.synchronize()
+    kms, kn = A.profile_read()
+    A.profile_enable(False)
+    ms = e0.elapsed_time(e1)
+    r = A.decode_result(res)
+    units = spec["P"] * (spec["iters"] + 1) * N
+    # FP32 lane-ops per particle-step of the FE kernel: 8 lanes x (8 modes x 13
+    # + tip sum/shuffles 6 + Newton 3 x 12 + misfit 5)
+    ops_ps = 8 * (8 * 13 + 6 + 36 + 5)
+    ach = spec["P"] * N * ops_ps / ((kms / max(kn, 1)) / 1e3)
+    return {"workload": "c5: 32-element Hermite FE cantilever, Newmark beta=1/4, DMT 4 unknowns, "
+                        "8192 particles x 60 updates, 50 cycles x 512 steps",
+            "ms_per_inversion": ms, "value": units / (ms / 1e3), "unit": UNIT,
+            "kernel_ms_per_launch": kms / max(kn, 1), "launches": kn,
+            "S_f64_nm2": r["S_f64"], "J_rel": r["J_rel"], "status": r["status"],
+            "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "T FP32 lane-ops/s", "frac": ach / peak_ops,
+                         "ops_per_particle_step": ops_ps,
+                         "note": "modal-basis Newmark kernel (no dense propagator)"}}
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -466,6 +516,9 @@ def run_ours(args):
     c4 = None
     if not args.no_c4:
         c4 = run_c4(A, W, dev, flush)
+    c5 = None
+    if not args.no_c5:
+        c5 = run_c5(A, W, dev, peak_ops, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -493,6 +546,7 @@ def run_ours(args):
             "batched_forward": batched,
             "batched_inversion": c3,
             "polished_inversion": c4,
+            "fe_inversion": c5,
         }
         print(json.dumps(out))
     if world > 1:
@@ -558,6 +612,19 @@ def run_probe(args):
         out = A.decode_results(res)
         print(json.dumps({"pixels": len(out), "kp": kp, "ok": sum(r["status"] == 0 for r in out)}))
         return
+    if args.probe == "fe":
+        # one FE swarm evaluation (8192 particles) of a 10-cycle record
+        spec = W.get("c5", cycles=10)
+        D, N = len(spec["free"]), W.n_steps(spec)
+        prob = A.make_problem(spec)
+        g = torch.Generator(device="cuda").manual_seed(7)
+        x = torch.rand((D, spec["P"]), dtype=torch.float32, device="cuda", generator=g)
+        U = torch.zeros(N, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            _, S = A.forward_batch(prob, x, U, want_defl=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"S_mean": float(S.mean())}))
+        return
     if args.probe == "adjoint":
         # gradient of 32 particles of the Kelvin-Voigt workload (one polish step's adjoint)
         spec = W.get("c4")
@@ -605,7 +672,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the wide forward launch")
     ap.add_argument("--no-c3", action="store_true", help="skip the 4096-pixel batched inversion")
     ap.add_argument("--no-c4", action="store_true", help="skip the polished-inversion comparison")
-    ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint"], default=None,
+    ap.add_argument("--no-c5", action="store_true", help="skip the finite-element inversion")
+    ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint", "fe"], default=None,
                     help="run one small untimed case for a profiler capture and exit")
     ap.add_argument("--probe-iters", type=int, default=2)
     ap.add_argument("--probe-particles", type=int, default=32768)
