@@ -23,10 +23,13 @@
 namespace afm {
 
 constexpr int FEN = AFM_FE_MAXN;
-constexpr int FEL = AFM_FE_LANES;
-constexpr int FEM = AFM_FE_MAXN / AFM_FE_LANES;   // modes per lane
 constexpr int FE_THREADS = 256;
-constexpr int FE_PPB = FE_THREADS / FEL;          // particles per block
+// lanes per particle: AFM_FE_LANES in FP32 (throughput), a whole warp in FP64
+// (latency: one trajectory, the FP64 re-evaluation)
+template <typename T>
+struct FeLanes {
+    static constexpr int value = sizeof(T) == 8 ? 32 : AFM_FE_LANES;
+};
 
 template <typename T>
 __device__ __forceinline__ void fe_table(const FeConst& F, T* tab) {
@@ -34,7 +37,9 @@ __device__ __forceinline__ void fe_table(const FeConst& F, T* tab) {
         tab[j] = (T)(F.drive_amp * sin(6.283185307179586476925 * (double)j / (double)F.spc + F.drive_phase));
 }
 
-// Tip force and its slope in the gap (laws without rate dependence).
+// Tip force and its slope in the gap (laws without rate dependence); the
+// FP32 instantiation uses the hardware reciprocal and square root (sqrt_fast,
+// rcp_fast resolve to the exact FP64 operations for double).
 template <int FORCE, typename T>
 __device__ __forceinline__ void fe_force(const Coef<T>& c, T d, T& Fv, T& dF) {
     if (FORCE == F_LINEAR) {
@@ -42,12 +47,13 @@ __device__ __forceinline__ void fe_force(const Coef<T>& c, T d, T& Fv, T& dF) {
         dF = -c.c0;
     } else if (FORCE == F_DMT) {
         if (d > c.c3) {
-            const T r = (T)1 / d;
-            Fv = -c.c1 * r * r;
-            dF = (T)2 * c.c1 * r * r * r;
+            const T r = rcp_fast(d);
+            const T r2 = r * r;
+            Fv = -c.c1 * r2;
+            dF = (T)2 * c.c1 * r2 * r;
         } else {
-            const T del = c.c3 - d, sq = sqrt(del);
-            const T r = (T)1 / c.c3;
+            const T del = c.c3 - d, sq = sqrt_fast(del);
+            const T r = rcp_fast(c.c3);
             Fv = c.c0 * del * sq - c.c1 * r * r;
             dF = (T)(-1.5) * c.c0 * sq;
         }
@@ -69,7 +75,7 @@ __device__ __forceinline__ T fe_newton(const Coef<T>& c, T Zc, T base, T cz, int
     for (int it = 0; it < iters; ++it) {
         fe_force<FORCE, T>(c, Zc + z, Fz, dF);
         const T phi = z - base - cz * Fz;
-        z = z - phi / ((T)1 - cz * dF);
+        z = z - phi * rcp_fast((T)1 - cz * dF);
     }
     fe_force<FORCE, T>(c, Zc + z, Fz, dF);
     return z;
@@ -85,6 +91,9 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
     const FeConst F, const PsoConst pc, SwarmPtrs sw, const T* __restrict__ xin, int P,
     T* __restrict__ defl, const TU* __restrict__ U, T* __restrict__ S_out,
     float* __restrict__ history, int it, afm_result* __restrict__ res) {
+    constexpr int FEL = FeLanes<T>::value;
+    constexpr int FEM = FEN / FEL;               // modes per lane
+    constexpr int FE_PPB = FE_THREADS / FEL;     // particles per block
     extern __shared__ __align__(16) unsigned char fe_smem[];
     T* cb1 = reinterpret_cast<T*>(fe_smem);
     T* cd2 = cb1 + FEN;
@@ -106,7 +115,6 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
     const int D = F.pm.D;
     int p = blockIdx.x * FE_PPB + grp;
     const bool active = MODE == 2 ? (blockIdx.x == 0 && grp == 0) : p < P;
-    const unsigned gmask = 0xffu << ((tid & 31) & ~(FEL - 1));   // this group's lanes
     // ---- coordinates of this group's particle
     T x[AFM_MAXD];
     for (int d = 0; d < AFM_MAXD; ++d) x[d] = (T)0.5;
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
     fe_force<FORCE, T>(cfc, Zc + (T)F.utipm, Fm, dF);
     T S = (T)0, cS = (T)0, u2 = (T)0;
     const int spc = F.spc;
-    const int newton_it = sizeof(T) == 8 ? 6 : 3;
+    const int newton_it = 3;   // the tip coupling is a contraction of ~1e-4: 3 steps are exact
     int jn = 0;
     for (int n = 0; n < F.n_steps; ++n) {
         const int jp = jn + 1 == spc ? 0 : jn + 1, jm = jn == 0 ? spc - 1 : jn - 1;
@@ -223,7 +231,6 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
         }
         jn = jp;
     }
-    (void)gmask;
     // ---- outputs
     if (MODE == 0) {
         if (lane == 0 && active && S_out != nullptr) S_out[p] = (S < (T)INFINITY) ? S : (T)INFINITY;
@@ -297,6 +304,7 @@ size_t fe_smem(const FeConst& F) {
 
 template <typename T, typename TU, int MODE, typename... Args>
 cudaError_t fe_launch(const FeConst& F, int blocks, cudaStream_t st, Args... args) {
+    const int threads = MODE == 2 ? 32 : FE_THREADS;   // the FP64 re-evaluation: one warp
     const size_t smem = fe_smem<T>(F);
     return fe_dispatch(F.pm.force, [&](auto Fc) -> cudaError_t {
         auto kern = fe_modal_kernel<T, TU, decltype(Fc)::value, MODE>;
@@ -304,7 +312,7 @@ cudaError_t fe_launch(const FeConst& F, int blocks, cudaStream_t st, Args... arg
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        kern<<<blocks, FE_THREADS, smem, st>>>(F, args...);
+        kern<<<blocks, threads, smem, st>>>(F, args...);
         return cudaGetLastError();
     });
 }
@@ -315,7 +323,8 @@ cudaError_t launch_fe_forward_f32(const FeConst& F, const float* x, int P, float
                                   const float* U, float* S, cudaStream_t st) {
     PsoConst pc{};
     SwarmPtrs sw{};
-    return fe_launch<float, float, 0>(F, (P + FE_PPB - 1) / FE_PPB, st, pc, sw, x, P, defl, U, S,
+    constexpr int ppb = FE_THREADS / FeLanes<float>::value;
+    return fe_launch<float, float, 0>(F, (P + ppb - 1) / ppb, st, pc, sw, x, P, defl, U, S,
                                       (float*)nullptr, 0, (afm_result*)nullptr);
 }
 
@@ -323,13 +332,15 @@ cudaError_t launch_fe_forward_f64(const FeConst& F, const double* x, int P, doub
                                   const double* U, double* S, cudaStream_t st) {
     PsoConst pc{};
     SwarmPtrs sw{};
-    return fe_launch<double, double, 0>(F, (P + FE_PPB - 1) / FE_PPB, st, pc, sw, x, P, defl, U,
+    constexpr int ppb = FE_THREADS / FeLanes<double>::value;
+    return fe_launch<double, double, 0>(F, (P + ppb - 1) / ppb, st, pc, sw, x, P, defl, U,
                                         S, (float*)nullptr, 0, (afm_result*)nullptr);
 }
 
 cudaError_t launch_fe_invert_iter(const FeConst& F, const PsoConst& pc, const SwarmPtrs& sw,
                                   const float* U, float* history, int it, cudaStream_t st) {
-    return fe_launch<float, float, 1>(F, (pc.P + FE_PPB - 1) / FE_PPB, st, pc, sw,
+    constexpr int ppb = FE_THREADS / FeLanes<float>::value;
+    return fe_launch<float, float, 1>(F, (pc.P + ppb - 1) / ppb, st, pc, sw,
                                       (const float*)nullptr, pc.P, (float*)nullptr, U,
                                       (float*)nullptr, history, it, (afm_result*)nullptr);
 }
