@@ -538,9 +538,12 @@ def run_ours(args):
                        "force": spec["force"], "per_rank": "one pixel inversion per step",
                        "l2": "flushed between steps (256 MiB write)"},
             "ms_per_inversion": T_ms / args.steps / 1.0,
-            "gpu_launches": (iters + 3) * args.steps,
+            # init + (iters + 1) fused iterations + the FP64 re-evaluation
+            # (pick, guess, 2 x (segment pass + join correction), final pass, result)
+            "gpu_launches": (iters + 2 + (8 if r["segments"] > 0 else 1)) * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "result": {"S_nm2": r["S"], "S_f64_nm2": r["S_f64"], "J_rel": r["J_rel"],
+                       "S_f64_segments": r["segments"], "S_f64_join_defect": r["defect"],
                        "x": list(r["x"][:D]), "x_truth": list(x_truth[:, 0]),
                        "status": r["status"], "theta": list(theta)},
             "batched_forward": batched,

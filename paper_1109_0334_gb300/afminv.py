@@ -57,7 +57,8 @@ class Result(C.Structure):
     _fields_ = [("x", C.c_double * MAX_PARAMS), ("theta", C.c_double * MAX_PARAMS),
                 ("S", C.c_double), ("S_f64", C.c_double), ("J_rel", C.c_double),
                 ("iters", C.c_int32), ("winner", C.c_int32), ("nonfinite", C.c_int32),
-                ("status", C.c_int32)]
+                ("status", C.c_int32), ("defect", C.c_double), ("segments", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class AfmError(RuntimeError):
@@ -459,7 +460,7 @@ def decode_result(result_bytes) -> dict:
     r = Result.from_buffer_copy(raw[:C.sizeof(Result)])
     return dict(x=np.array(r.x[:]), theta=np.array(r.theta[:]), S=r.S, S_f64=r.S_f64,
                 J_rel=r.J_rel, iters=r.iters, winner=r.winner, nonfinite=r.nonfinite,
-                status=r.status)
+                status=r.status, defect=r.defect, segments=r.segments)
 
 
 def synth_records(prob: Problem, x_truth, off, sub: int, sigma_m: float, seed: int,

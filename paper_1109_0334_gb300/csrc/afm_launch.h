@@ -97,4 +97,33 @@ cudaError_t launch_invert_iter(const KConst<float>& K, const PsoConst& pc, const
 cudaError_t launch_invert_final(const KConst<double>& K, const PsoConst& pc, const SwarmPtrs& sw,
                                 const float* U, float* history, void* result, cudaStream_t st);
 
+// FP64 re-evaluation of one winner by multiple shooting in time
+// (kern_reeval.cu): segments of AFM_SEG steps, B = ceil(n_steps / AFM_SEG).
+struct ReevalWinner {
+    double x[AFM_MAXD];   // normalised parameters
+    double c[4];          // FP64 force coefficients (written by the guess kernel)
+    float S32;            // FP32 misfit that selected the winner
+    int winner;           // its particle index
+};
+struct ReevalPtrs {
+    ReevalWinner* win;
+    double* tab;          // [spc2 + 1] FP64 drive table
+    double* start[2];     // [B + 1][2m] segment start states (alternating sweeps)
+    double* E;            // [B][2m] segment end states
+    double* J;            // [B][2m][2m] segment tangent maps
+    double* Sb;           // [B] segment misfit shares
+    double* sumU2;        // [1]
+    int B;
+};
+bool reeval_supported(int m, int n_steps);
+size_t reeval_bytes(int m, int n_steps, int spc);
+void reeval_carve(void* base, int m, int n_steps, int spc, ReevalPtrs* R);
+cudaError_t launch_reeval_pick_swarm(const PsoConst& pc, const SwarmPtrs& sw, float* history,
+                                     ReevalWinner* w, cudaStream_t st);
+cudaError_t launch_reeval_pick_min(int D, int Kn, const float* x, const float* S, const int* idx,
+                                   ReevalWinner* w, cudaStream_t st);
+cudaError_t launch_reeval(const KConst<float>& Kf, const KConst<double>& Kd, const ReevalPtrs& R,
+                          const float* U, int iters, const int* flags, void* result,
+                          cudaStream_t st);
+
 }  // namespace afm

@@ -581,6 +581,17 @@ InvLayout invert_layout(int P, int D) {
     return L;
 }
 
+// Bytes of the multiple-shooting FP64 re-evaluation appended to the
+// inversion workspaces (0 where the sequential re-evaluation is used).
+int problem_modes(const afm_problem& pr) { return pr.model == AFM_POINT_MASS ? 1 : pr.n_modes; }
+
+size_t reeval_extra(const afm_problem& pr) {
+    if (pr.model == AFM_FE_HERMITE) return 0;
+    const int m = problem_modes(pr);
+    if (!afm::reeval_supported(m, pr.n_steps)) return 0;
+    return afm::reeval_bytes(m, pr.n_steps, pr.steps_per_cycle);
+}
+
 struct BatchLayout {
     size_t order, queue, total;
 };
@@ -889,7 +900,7 @@ afm_status afm_invert_workspace_size(const afm_problem* prob, const afm_pso_cfg*
     afm_status st = check_problem(prob);
     if (st) return st;
     if ((st = check_pso(cfg, prob->n_free))) return st;
-    *bytes = invert_layout(cfg->P, prob->n_free).total;
+    *bytes = invert_layout(cfg->P, prob->n_free).total + reeval_extra(*prob);
     return AFM_OK;
 }
 
@@ -906,8 +917,9 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
         return fail(AFM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     const int D = prob->n_free, P = cfg->P;
     const InvLayout L = invert_layout(P, D);
-    if (workspace_bytes < L.total)
-        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, L.total);
+    const size_t need = L.total + reeval_extra(*prob);
+    if (workspace_bytes < need)
+        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, need);
     char* ws = static_cast<char*>(workspace);
     afm::SwarmPtrs sw;
     sw.x = reinterpret_cast<float*>(ws + L.x);
@@ -938,6 +950,14 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
     for (int it = 0; it <= cfg->iters; ++it)
         AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_invert_iter(Kf, pc, sw, U, history, it, s); }),
                  "invert iteration kernel");
+    if (reeval_extra(*prob) > 0) {
+        afm::ReevalPtrs R;
+        afm::reeval_carve(ws + L.total, problem_modes(*prob), prob->n_steps, prob->steps_per_cycle, &R);
+        AFM_CUDA(afm::launch_reeval_pick_swarm(pc, sw, history, R.win, s), "winner pick kernel");
+        AFM_CUDA(afm::launch_reeval(Kf, Kd, R, U, cfg->iters, sw.flags, result, s),
+                 "FP64 re-evaluation kernels");
+        return AFM_OK;
+    }
     AFM_CUDA(afm::launch_invert_final(Kd, pc, sw, U, history, result, s), "invert final kernel");
     return AFM_OK;
 }
@@ -1064,7 +1084,7 @@ afm_status afm_invert_polished_workspace_size(const afm_problem* prob, const afm
     const size_t xk = align256(sizeof(float) * (size_t)prob->n_free * polish_k);
     const size_t sk = align256(sizeof(float) * (size_t)polish_k);
     const size_t ik = align256(sizeof(int) * (size_t)polish_k);
-    *bytes = inv + xk + sk + ik + polish_layout(*prob, polish_k, n_cand).total;
+    *bytes = inv + xk + sk + ik + polish_layout(*prob, polish_k, n_cand).total + reeval_extra(*prob);
     return AFM_OK;
 }
 
@@ -1111,6 +1131,15 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
     const int fin = (cfg->iters + 1) & 1;
     AFM_CUDA(afm::launch_topk(sw.pbS, sw.pb[fin], P, D, polish_k, xk, ik, s), "top-k kernel");
     if ((st = polish_run(ctx, *prob, Kf, U, xk, sk, polish_k, polish_steps, n_cand, pol, s))) return st;
+    if (reeval_extra(*prob) > 0) {
+        afm::ReevalPtrs R;
+        afm::reeval_carve(pol + polish_layout(*prob, polish_k, n_cand).total, problem_modes(*prob),
+                          prob->n_steps, prob->steps_per_cycle, &R);
+        AFM_CUDA(afm::launch_reeval_pick_min(D, polish_k, xk, sk, ik, R.win, s), "winner pick kernel");
+        AFM_CUDA(afm::launch_reeval(Kf, Kd, R, U, cfg->iters, sw.flags, result, s),
+                 "FP64 re-evaluation kernels");
+        return AFM_OK;
+    }
     AFM_CUDA(afm::launch_polish_final(Kd, polish_k, cfg->iters, xk, sk, ik, U, sw.flags, result, s),
              "polish final kernel");
     return AFM_OK;

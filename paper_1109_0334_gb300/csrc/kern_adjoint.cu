@@ -43,56 +43,6 @@ cudaError_t dispatch_mf(int m, int force, F&& f) {
 
 }  // namespace
 
-// Partial derivatives of the tip force with respect to the gap (Fd), the gap
-// rate (Fr) and the four coefficients (Fc[0..3]) at (d, d').
-template <int FORCE>
-__device__ __forceinline__ void force_partials(const Coef<float>& c, float d, float dd, float& Fd,
-                                               float& Fr, float* Fc) {
-    Fc[0] = Fc[1] = Fc[2] = Fc[3] = 0.f;
-    Fd = Fr = 0.f;
-    if (FORCE == F_LINEAR) {
-        Fd = -c.c0;
-        Fc[0] = -(d - c.c1);
-        Fc[1] = c.c0;
-    } else if (FORCE == F_DMT || FORCE == F_DMT_KV) {
-        const bool contact = d < c.c3;
-        const float dm = fmaxf(d, c.c3);
-        const float r = 1.f / dm;
-        const float r2 = r * r;
-        Fc[1] = -r2;
-        if (contact) {
-            const float del = c.c3 - d;
-            const float sq = sqrtf(del);
-            const float isq = 1.f / sq;
-            Fd = -1.5f * c.c0 * sq;
-            Fc[0] = del * sq;
-            Fc[3] = 1.5f * c.c0 * sq + 2.f * c.c1 * r2 * r;
-            if (FORCE == F_DMT_KV) {
-                Fd += 0.5f * c.c2 * dd * isq;
-                Fr = -c.c2 * sq;
-                Fc[2] = -sq * dd;
-                Fc[3] -= 0.5f * c.c2 * dd * isq;
-            }
-        } else {
-            Fd = 2.f * c.c1 * r2 * r;
-        }
-    } else if (FORCE == F_HOOKE) {
-        if (d < c.c1) {
-            Fd = -c.c0;
-            Fc[0] = c.c1 - d;
-            Fc[1] = c.c0;
-        }
-    } else {
-        if (d < c.c1) {
-            Fd = -c.c0;
-            Fr = -c.c2;
-            Fc[0] = c.c1 - d;
-            Fc[1] = c.c0;
-            Fc[2] = -dd;
-        }
-    }
-}
-
 // Transposed Jacobian of the modal right-hand side f(q, v) = (v, a) at one
 // stage, applied to w = (wq, wv); accumulates the force-coefficient
 // cotangents into cb.

@@ -182,6 +182,9 @@ __global__ void batch_final_kernel(const KConst<double> K, const PsoConst pc, co
     r->S_f64 = S64;
     r->J_rel = u2 > 0.0 ? sqrt(S64 / u2) : 0.0;
     r->status = (isfinite(S64) && r->nonfinite == 0) ? AFM_OK : AFM_ERR_NONFINITE;
+    r->defect = 0.0;
+    r->segments = 0;
+    r->reserved = 0;
 }
 
 

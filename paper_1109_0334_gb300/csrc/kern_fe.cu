@@ -279,6 +279,9 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
         res->winner = p;
         res->nonfinite = sw.flags ? sw.flags[0] : 0;
         res->status = (isfinite((double)S) && res->nonfinite == 0) ? AFM_OK : AFM_ERR_NONFINITE;
+        res->defect = 0.0;
+        res->segments = 0;
+        res->reserved = 0;
     }
 }
 

@@ -248,6 +248,9 @@ __global__ void invert_final_kernel(const KConst<double> K, const PsoConst pc, S
     res->winner = g;
     res->nonfinite = sw.flags ? sw.flags[0] : 0;
     res->status = (isfinite(S64) && (sw.flags == nullptr || sw.flags[0] == 0)) ? AFM_OK : AFM_ERR_NONFINITE;
+    res->defect = 0.0;
+    res->segments = 0;
+    res->reserved = 0;
 }
 
 cudaError_t launch_invert_final(const KConst<double>& K, const PsoConst& pc, const SwarmPtrs& sw,

@@ -156,6 +156,9 @@ __global__ void polish_final_kernel(const KConst<double> K, int Kn, int iters,
     res->winner = idx != nullptr ? idx[kb] : kb;
     res->nonfinite = flags ? flags[0] : 0;
     res->status = (isfinite(S64) && res->nonfinite == 0) ? AFM_OK : AFM_ERR_NONFINITE;
+    res->defect = 0.0;
+    res->segments = 0;
+    res->reserved = 0;
 }
 
 cudaError_t launch_polish_cand(int D, int K, int J, const float* x, const float* G, double alpha0,

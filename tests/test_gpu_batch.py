@@ -61,7 +61,9 @@ def test_batch_equals_single_pixel_inversions(orc, afm, kp):
         assert b["winner"] == single["winner"]
         assert b["S"] == single["S"]
         np.testing.assert_array_equal(b["x"], single["x"])
-        assert abs(b["S_f64"] - single["S_f64"]) <= 1e-12 * single["S_f64"]
+        # FP64 re-evaluations: sequential per pixel in the batch, multiple
+        # shooting in afm_invert (different FP64 rounding, same trajectory)
+        assert abs(b["S_f64"] - single["S_f64"]) <= 1e-11 * single["S_f64"]
 
 
 def test_batch_oracle_parity_and_autotune(orc, afm):

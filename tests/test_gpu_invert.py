@@ -108,6 +108,8 @@ def _check_inversion(orc, spec, U_m, r, x_o, S_o_m, hist):
     assert abs(r["S_f64"] - S_g_orc / NM ** 2) <= 1e-9 * S_o
     assert np.all(np.diff(hist) <= 0)
     assert r["status"] == 0 and r["nonfinite"] == 0
+    # the FP64 re-evaluation ran as multiple shooting over 32-step segments
+    assert r["segments"] == -(-len(U_m) // 32) and r["defect"] <= 1e-9
 
 
 def test_invert_c1_parity(orc, afm):

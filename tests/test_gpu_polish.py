@@ -68,3 +68,4 @@ def test_invert_polished_matches_oracle(orc, afm):
     assert err <= 0.005, (err, widths)
     assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2
     assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2
+    assert r["segments"] == -(-len(U_m) // 32) and r["defect"] <= 1e-9
