@@ -1005,3 +1005,141 @@ int orc_fe_forward(const orc_case* c, const double th[5], int n_steps, int sub, 
     free(Z); free(X); free(r); free(Mr); free(fe);
     return 0;
 }
+
+
+/* ======================================================================== */
+/* Normal equations of the misfit (reading R15).  The residual sensitivities */
+/* a_nd = d u_n / d x_d come from the complex step applied to the whole      */
+/* trajectory: u_n(x + i h e_d) = u_n + i h a_nd + O(h^2), h = 1e-30, with   */
+/* branches taken on real parts (as cmisfit).                                */
+/* ======================================================================== */
+static void ctraj(const orc_case* c, const orc_modal* md, const double complex th[5], int n,
+                  double complex* tip_out)
+{
+    int m = md->m, n2 = 2 * m;
+    double complex y[2 * ORC_MAXM], k[4][2 * ORC_MAXM], yt[2 * ORC_MAXM];
+    for (int i = 0; i < m; ++i) { y[i] = md->eta0[i]; y[m + i] = md->etad0[i]; }
+    double h = md->dt;
+    for (int step = 0; step < n; ++step) {
+        double g[3] = {orc_drive_half(md, c->spc, 2L * step),
+                       orc_drive_half(md, c->spc, 2L * step + 1),
+                       orc_drive_half(md, c->spc, 2L * step + 2)};
+        const double cs[4] = {0.0, 0.5, 0.5, 1.0};
+        const int gi[4] = {0, 1, 1, 2};
+        for (int s = 0; s < 4; ++s) {
+            for (int q = 0; q < n2; ++q) yt[q] = s == 0 ? y[q] : y[q] + cs[s] * h * k[s - 1][q];
+            double complex u = 0.0, ud = 0.0;
+            for (int i = 0; i < m; ++i) { u += yt[i]; ud += yt[m + i]; }
+            double complex F = cforce(c->force, th, c->Zc + u, ud);
+            for (int i = 0; i < m; ++i) {
+                k[s][i] = yt[m + i];
+                k[s][m + i] = F / md->mass + md->gam[i] * g[gi[s]]
+                              - md->w[i] * md->w[i] * yt[i] - (md->w[i] / c->Q[i]) * yt[m + i];
+            }
+        }
+        for (int q = 0; q < n2; ++q)
+            y[q] = y[q] + (h / 6.0) * (k[0][q] + 2.0 * k[1][q] + 2.0 * k[2][q] + k[3][q]);
+        double complex tip = 0.0;
+        for (int i = 0; i < m; ++i) tip += y[i];
+        tip_out[step] = tip;
+    }
+}
+
+static int normal_eq_serial(const orc_case* c, const orc_modal* md, const orc_pmap* pm,
+                            const double* x, const double* U, int n, double* S, double* H,
+                            double* b, int parallel)
+{
+    const double hs = 1e-30;
+    int D = pm->D;
+    double complex* ut = (double complex*)malloc(sizeof(double complex) * (size_t)n * D);
+    if (!ut) return -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads) if (parallel)
+#endif
+    for (int d = 0; d < D; ++d) {
+        double complex xc[5], th[5];
+        for (int e = 0; e < D; ++e) xc[e] = x[e] + (e == d ? I * hs : 0.0);
+        cmap(pm, xc, th);
+        ctraj(c, md, th, n, ut + (size_t)d * n);
+    }
+    (void)parallel;
+    double Sr = 0.0;
+    for (int i = 0; i < D * D; ++i) H[i] = 0.0;
+    for (int d = 0; d < D; ++d) b[d] = 0.0;
+    for (int t = 0; t < n; ++t) {
+        double r = U[t] - creal(ut[t]);
+        double a[5];
+        for (int d = 0; d < D; ++d) a[d] = cimag(ut[(size_t)d * n + t]) / hs;
+        Sr += r * r;
+        for (int d = 0; d < D; ++d) {
+            b[d] += a[d] * r;
+            for (int e = 0; e < D; ++e) H[d * D + e] += a[d] * a[e];
+        }
+    }
+    *S = Sr;
+    free(ut);
+    return 0;
+}
+
+int orc_normal_eq(const orc_case* c, const orc_pmap* pm, const double* x, const double* U,
+                  int n, double* S, double* H, double* b)
+{
+    orc_modal md;
+    if (orc_setup(c, &md)) return -1;
+    return normal_eq_serial(c, &md, pm, x, U, n, S, H, b, 1);
+}
+
+/* ======================================================================== */
+/* Levenberg-Marquardt polish of K candidates (reading R15); see the header. */
+/* ======================================================================== */
+int orc_lm_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, double* x,
+                  int K, int steps, int n_lambda, double lam0, double lam_ratio, double* S)
+{
+    orc_modal md;
+    if (orc_setup(c, &md)) return -1;
+    int D = pm->D, J = n_lambda, KJ = K * n_lambda;
+    double* Xc = (double*)malloc(sizeof(double) * (size_t)D * KJ);
+    double* Sc = (double*)malloc(sizeof(double) * (size_t)KJ);
+    if (!Xc || !Sc) { free(Xc); free(Sc); return -1; }
+    int rc = 0;
+    for (int st = 0; st < steps && rc == 0; ++st) {
+        for (int k = 0; k < K; ++k) {
+            double xk[5], H[25], b[5], Sk = 0.0;
+            for (int d = 0; d < D; ++d) xk[d] = x[(size_t)d * K + k];
+            if (normal_eq_serial(c, &md, pm, xk, U, n, &Sk, H, b, 1)) { rc = -1; break; }
+            S[k] = Sk;
+            double hmax = 0.0;
+            for (int d = 0; d < D; ++d) hmax = fmax(hmax, H[d * D + d]);
+            for (int j = 0; j < J; ++j) {
+                double lam = lam0 * pow(lam_ratio, j);
+                double A[25], delta[5];
+                int piv[5];
+                for (int d = 0; d < D; ++d) {
+                    for (int e = 0; e < D; ++e) A[d * D + e] = H[d * D + e];
+                    A[d * D + d] += lam * fmax(H[d * D + d], 1e-12 * hmax);
+                    delta[d] = b[d];
+                }
+                int ok = hmax > 0.0 && lu_factor(A, D, piv) == 0;
+                if (ok) lu_solve(A, D, piv, delta);
+                for (int d = 0; d < D; ++d) {
+                    double xn = xk[d] + (ok ? delta[d] : 0.0);
+                    if (!(xn > 0.0)) xn = 0.0;   /* also a NaN step */
+                    if (xn > 1.0) xn = 1.0;
+                    Xc[(size_t)d * KJ + (size_t)k * J + j] = xn;
+                }
+            }
+        }
+        if (rc) break;
+        orc_misfit_batch(c, pm, Xc, KJ, U, n, Sc);
+        for (int k = 0; k < K; ++k) {
+            int jb = argmin_first(Sc + (size_t)k * J, J);
+            if (Sc[(size_t)k * J + jb] < S[k])
+                for (int d = 0; d < D; ++d)
+                    x[(size_t)d * K + k] = Xc[(size_t)d * KJ + (size_t)k * J + jb];
+        }
+    }
+    if (rc == 0) orc_misfit_batch(c, pm, x, K, U, n, S);
+    free(Xc);
+    free(Sc);
+    return rc;
+}

@@ -9,7 +9,7 @@
  * it.  It shares no code, header, table or constant with the CUDA library.
  *
  * Citations name the paper's section / equation.  Readings of passages the
- * paper leaves open are labelled R1..R13 and listed in the repository's
+ * paper leaves open are labelled R1..R15 and listed in the repository's
  * design notes.
  *
  * Parity status per function:
@@ -32,6 +32,11 @@
  *                                  Newmark energy conservation, order 2)
  *   orc_polish             pinned (monotone descent, Armijo sufficient decrease,
  *                                  stationarity at an interior optimum)
+ *   orc_normal_eq          pinned (central differences of orc_forward; b = -grad/2
+ *                                  of orc_grad_cs)
+ *   orc_lm_polish          pinned (one step to the closed-form least-squares point
+ *                                  of a problem affine in its parameter; descent;
+ *                                  diagonally scaled gradient for large damping)
  */
 #ifndef AFM_ORACLE_H
 #define AFM_ORACLE_H
@@ -147,6 +152,19 @@ int orc_record(const orc_case* c, const orc_pmap* pm, const double* x, int n,
 /* ---- gradients ---------------------------------------------------------- */
 int orc_grad_cs(const orc_case* c, const orc_pmap* pm, const double* x,
                 const double* U, int n, double* S, double* grad);
+/* Residual sensitivities a_n = d u_n / d x (complex step on the whole
+ * trajectory) and the normal equations of the misfit: S = sum r_n^2,
+ * H = sum a_n a_n^T ([D][D]), b = sum a_n r_n ([D]), r_n = U_n - u_n. */
+int orc_normal_eq(const orc_case* c, const orc_pmap* pm, const double* x, const double* U,
+                  int n, double* S, double* H, double* b);
+/* Levenberg-Marquardt polish of K candidates x [D][K] (reading R15): per step
+ * and candidate the normal equations at x, trial points clamp(x + delta_j)
+ * with (H + lambda_j W) delta_j = b, lambda_j = lam0 * lam_ratio^j (j <
+ * n_lambda), W = diag(max(H_dd, 1e-12 max_e H_ee)); the trial point of least
+ * misfit (first on ties) replaces x if its misfit is lower.  S [K] receives
+ * the final misfits. */
+int orc_lm_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, double* x,
+                  int K, int steps, int n_lambda, double lam0, double lam_ratio, double* S);
 int orc_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, double* x, int K,
                int steps, int n_cand, double alpha0, double shrink, double sigma, double* S);
 

@@ -114,6 +114,10 @@ def lib():
                                       C.POINTER(C.c_double), _dp]
             L.orc_polish.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int, _dp, C.c_int,
                                      C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, _dp]
+            L.orc_normal_eq.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, _dp, C.c_int,
+                                        C.POINTER(C.c_double), _dp, _dp]
+            L.orc_lm_polish.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int, _dp,
+                                        C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp]
             L.orc_fe_dofs.argtypes = [C.POINTER(Case)]
             L.orc_fe_matrices.argtypes = [C.POINTER(Case), C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p]
@@ -313,6 +317,36 @@ def grad_cs(case: Case, pm: Pmap, x, U):
     lib().orc_grad_cs(C.byref(case), C.byref(pm), np.ascontiguousarray(x, dtype=np.float64),
                       U, len(U), C.byref(S), g)
     return S.value, g
+
+
+def normal_eq(case: Case, pm: Pmap, x, U):
+    """(S, H [D][D], b [D]) of the misfit at x: residual sensitivities by the
+    complex step on the whole trajectory (reading R15)."""
+    D = pm.D
+    H = np.zeros(D * D)
+    b = np.zeros(D)
+    S = C.c_double()
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    rc = lib().orc_normal_eq(C.byref(case), C.byref(pm), np.ascontiguousarray(x, dtype=np.float64),
+                             U, len(U), C.byref(S), H, b)
+    if rc:
+        raise ValueError("orc_normal_eq failed")
+    return S.value, H.reshape(D, D), b
+
+
+def lm_polish(case: Case, pm: Pmap, U, x_dk, steps: int, n_lambda: int = 8, lam0: float = 1e-7,
+              lam_ratio: float = 10.0):
+    """Levenberg-Marquardt polish with a ladder of n_lambda damping values
+    (reading R15); returns (x [D][K], S [K])."""
+    x = np.array(x_dk, dtype=np.float64, order="C")
+    D, K = x.shape
+    S = np.zeros(K)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    rc = lib().orc_lm_polish(C.byref(case), C.byref(pm), U, len(U), x, K, steps, n_lambda, lam0,
+                             lam_ratio, S)
+    if rc:
+        raise ValueError("orc_lm_polish failed")
+    return x, S
 
 
 def polish(case: Case, pm: Pmap, U, x_dk, steps: int, n_cand: int = 16, alpha0: float = 0.05,

@@ -565,6 +565,96 @@ def test_polish_descends_to_a_stationary_point(orc):
 
 
 # --------------------------------------------------------------------------
+# Levenberg-Marquardt polish (reading R15)
+# --------------------------------------------------------------------------
+def test_normal_equations_vs_trajectory_differences(orc):
+    """a_n = du_n/dx from the complex step on the trajectory, against 4th-
+    order central differences of the plain RK4 forward solve; b is -1/2 of
+    the complex-step gradient of S computed by the separate misfit code."""
+    w = W.get("c4", cycles=8)
+    c, pm = orc.make_case(w), orc.make_pmap(w)
+    n = W.n_steps(w)
+    U = orc.record(c, pm, orc.truth_x(pm.D, w["seed"]), n, 4, w["sigma"], w["seed"])
+    x = np.array([0.55, 0.45, 0.5, 0.52, 0.4])
+    S, H, b = orc.normal_eq(c, pm, x, U)
+    S_ref, g = orc.grad_cs(c, pm, x, U)
+    assert S == pytest.approx(S_ref, rel=1e-12)
+    np.testing.assert_allclose(b, -0.5 * g, rtol=1e-9, atol=1e-12 * np.max(np.abs(g)))
+    h = 1e-4
+    A = np.zeros((n, pm.D))
+    for d in range(pm.D):
+        us = []
+        for s in (-2, -1, 1, 2):
+            xx = x.copy()
+            xx[d] += s * h
+            us.append(orc.forward(c, orc.map_x(pm, xx), n))
+        A[:, d] = (us[0] - 8 * us[1] + 8 * us[2] - us[3]) / (12 * h)
+    u = orc.forward(c, orc.map_x(pm, x), n)
+    H_fd = A.T @ A
+    b_fd = A.T @ (U - u)
+    assert np.max(np.abs(H - H_fd)) <= 1e-5 * np.max(np.abs(H))
+    assert np.max(np.abs(b - b_fd)) <= 1e-5 * np.max(np.abs(b))
+    assert np.all(np.linalg.eigvalsh(H) >= -1e-12 * np.max(np.abs(H)))   # a Gram matrix
+
+
+def test_lm_one_step_solves_an_affine_problem(orc):
+    """A linear spring with only its rest gap free: the deflection is affine
+    in the parameter, the misfit exactly quadratic, so one undamped step
+    reaches the least-squares point, which two forward solves give in
+    closed form."""
+    w = W.get("c1", force="linear_spring", cycles=12,
+              free=[(1, 10e-9, 20e-9, False)], fixed=[5.0, 0.0, 0.0, 0.0, 0.0])
+    c, pm = orc.make_case(w), orc.make_pmap(w)
+    n = W.n_steps(w)
+    U = orc.record(c, pm, np.array([0.3]), n, 4, w["sigma"], w["seed"])   # noisy record
+    u0 = orc.forward(c, orc.map_x(pm, np.array([0.0])), n)
+    u1 = orc.forward(c, orc.map_x(pm, np.array([1.0])), n) - u0
+    x_star = float(np.sum((U - u0) * u1) / np.sum(u1 * u1))
+    assert 0.2 < x_star < 0.4
+    x1, S1 = orc.lm_polish(c, pm, U, np.array([[0.8]]), steps=1, n_lambda=1, lam0=1e-12)
+    assert abs(x1[0, 0] - x_star) <= 1e-8
+    S_star = np.sum((U - u0 - x_star * u1) ** 2)
+    assert S1[0] == pytest.approx(S_star, rel=1e-9)
+
+
+def test_lm_large_damping_is_a_scaled_gradient_step(orc):
+    """With damping lambda >> 1 the step is W^-1 b / lambda (W = diag H),
+    a descent direction, so it is taken."""
+    w = W.get("c2", cycles=6)
+    c, pm = orc.make_case(w), orc.make_pmap(w)
+    n = W.n_steps(w)
+    U = orc.record(c, pm, orc.truth_x(pm.D, w["seed"]), n, 4, w["sigma"], w["seed"])
+    x0 = np.array([0.5, 0.5, 0.5, 0.5])
+    S0, H, b = orc.normal_eq(c, pm, x0, U)
+    lam = 1e8
+    x1, S1 = orc.lm_polish(c, pm, U, x0.reshape(-1, 1), steps=1, n_lambda=1, lam0=lam)
+    expect = b / np.diag(H) / lam
+    np.testing.assert_allclose(x1[:, 0] - x0, expect, rtol=1e-6, atol=1e-15)
+    assert S1[0] < S0
+
+
+def test_lm_polish_descends_and_reaches_the_optimum(orc):
+    """Exact data of the two-parameter linear spring: the misfit never rises
+    with more steps and a few damped Gauss-Newton steps reach the data's
+    parameters."""
+    w = W.get("c2", force="linear_spring", cycles=10,
+              free=[(0, 2.0, 20.0, False), (1, 10e-9, 20e-9, False)], fixed=[0.0] * 5)
+    c, pm = orc.make_case(w), orc.make_pmap(w)
+    n = W.n_steps(w)
+    xt = np.array([0.4, 0.6])
+    U = orc.record(c, pm, xt, n, 1, 0.0, w["seed"])       # exact data: optimum at xt
+    x0 = np.array([[0.43, 0.30], [0.57, 0.75]])
+    S0 = orc.misfit_batch(c, pm, x0, U)
+    prev = S0
+    for steps in (1, 2, 4, 8):
+        xs, Ss = orc.lm_polish(c, pm, U, x0, steps=steps)
+        assert np.all(Ss <= prev)
+        prev = Ss
+    np.testing.assert_allclose(xs, np.array([[0.4, 0.4], [0.6, 0.6]]), atol=1e-6)
+    assert np.all(Ss < 1e-10 * S0)
+
+
+# --------------------------------------------------------------------------
 # Finite-element cantilever (reading R13)
 # --------------------------------------------------------------------------
 def test_fe_static_stiffness_and_frequencies(orc):
