@@ -240,7 +240,7 @@ def c3_inputs(A, W, dev, n_pix=None, cycles_div=1):
 
 def run_c3(A, W, dev, peak_ops, flush):
     import torch
-    spec, prob, U, off, total_steps, _ = c3_inputs(A, W, dev)
+    spec, prob, U, off, total_steps, xt = c3_inputs(A, W, dev)
     cfg = A.make_pso(spec)
     n_pix = spec["n_pix"]
     res, kp = A.invert_batch(prob, U, off, cfg)   # autotune + graph capture + warm-up
@@ -256,6 +256,8 @@ def run_c3(A, W, dev, peak_ops, flush):
     out = A.decode_results(res)
     ok = sum(1 for r in out if r["status"] == 0)
     ops = units * fp32_ops_per_step(spec["n_modes"], spec["force"])
+    polished = run_c3_polished(A, spec, prob, U, off, xt, out, flush)
+    polished["speedup_vs_plain_pso"] = ms / polished["ms"]
     return {"workload": "c3: 4096 pixels, 20..200 cycles x 256 steps, 256 particles x 60 updates",
             "pixels": n_pix, "record_steps_total": total_steps, "particle_steps": units,
             "ms": ms, "value": units / (ms / 1e3), "unit": UNIT,
@@ -264,7 +266,95 @@ def run_c3(A, W, dev, peak_ops, flush):
             "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e12,
                          "peak": peak_ops / 1e12, "unit": "T FP32 lane-ops/s",
                          "frac": ops / (ms / 1e3) / peak_ops,
-                         "note": "whole graph (swarm kernel + FP64 winners), one timed replay"}}
+                         "note": "whole graph (swarm kernel + FP64 winners), one timed replay"},
+            "lm_polished": polished}
+
+
+def _theta_of(spec, xn):
+    """SI parameter slots of normalised coordinates xn [D] (truth draws)."""
+    import math
+    th = [0.0] * 5
+    for s5, v in enumerate(spec["fixed"]):
+        th[s5] = v
+    for d, (slot, lo, hi, lg) in enumerate(spec["free"]):
+        th[slot] = 10 ** (math.log10(lo) + xn[d] * (math.log10(hi) - math.log10(lo))) if lg \
+            else lo + xn[d] * (hi - lo)
+    return th
+
+
+def _dmt_comb(th):
+    """The combinations a DMT record determines: H R, E* sqrt(R), a0."""
+    import math
+    return [th[1] * th[2], th[0] * math.sqrt(th[2]), th[3]]
+
+
+def _comb_err(a, b):
+    return max(abs(x / y - 1) for x, y in zip(_dmt_comb(a), _dmt_comb(b)))
+
+
+def run_c3_polished(A, spec, prob, U, off, xt, plain, flush, n_ref=512):
+    """The same 4096 pixels by a short swarm plus Levenberg-Marquardt polish
+    of each pixel's best particles, timed like the plain batch; accuracy of
+    both against the best misfit either reaches per pixel (and, on the first
+    n_ref pixels, a long reference run: 60 updates + 20 LM steps on 8)."""
+    import numpy as np
+    import torch
+    lp = spec["lm_polish"]
+    cfg = A.make_pso(dict(spec, iters=lp["iters"]))
+    n_pix = spec["n_pix"]
+    nbytes = A.invert_batch_polished_workspace_size(prob, cfg, n_pix, lp["polish_k"], lp["n_cand"], "lm")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=U.device)
+
+    def call(results=None):
+        return A.invert_batch_polished(prob, U, off, cfg, lp["polish_k"], lp["polish_steps"],
+                                       lp["n_cand"], method="lm", workspace=ws, results=results)
+    res, _ = call()
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res, kp = call(res)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    pol = A.decode_results(res)
+    off_h = off.cpu().numpy()
+    ref_off = off[:n_ref + 1].contiguous()
+    ref_U = U[:int(off_h[n_ref])].contiguous()
+    rr, _ = A.invert_batch_polished(prob, ref_U, ref_off, A.make_pso(dict(spec, iters=60)), 8, 20, 8,
+                                    method="lm")
+    ref = A.decode_results(rr)
+    var = (spec["sigma"] / 1e-9) ** 2
+    truth = [_theta_of(spec, xt[:, i]) for i in range(n_pix)]
+
+    def stats(res_m, idx, refs):
+        dchi, eb, et = [], [], []
+        for i in idx:
+            cands = [plain[i], pol[i]] + ([refs[i]] if refs is not None else [])
+            best = min(cands, key=lambda r: r["S_f64"])
+            dchi.append((res_m[i]["S_f64"] - best["S_f64"]) / var)
+            eb.append(_comb_err(list(res_m[i]["theta"]), list(best["theta"])))
+            et.append(_comb_err(list(res_m[i]["theta"]), truth[i]))
+        dchi, eb, et = map(np.array, (dchi, eb, et))
+        return {"frac_dchi2_le_1": float(np.mean(dchi <= 1.0)),
+                "frac_ident_within_0.5pct": float(np.mean(eb <= 0.005)),
+                "median_ident_err_vs_best": float(np.median(eb)),
+                "median_ident_err_vs_truth": float(np.median(et))}
+    allp, sub = range(n_pix), range(n_ref)
+    return {"config": f"{spec['P']} particles x {lp['iters']} updates, then {lp['polish_steps']} "
+                      f"Levenberg-Marquardt steps on each pixel's best {lp['polish_k']} "
+                      f"({lp['n_cand']} damping values per step)",
+            "ms": ms, "ms_per_pixel_inversion": ms / n_pix, "particles_per_thread": kp,
+            "pixels_ok": sum(1 for r in pol if r["status"] == 0),
+            "speedup_vs_plain_pso": None,
+            "accuracy": {
+                "criteria": "delta chi^2 = (S - S_best) / sigma^2 <= 1 (statistically at the "
+                            "optimum); identifiable combinations (H R, E* sqrt R, a0) within 0.5 % "
+                            "of the lowest-misfit point",
+                "all_pixels_vs_best_of_both": {"plain_pso": stats(plain, allp, None),
+                                               "lm_polished": stats(pol, allp, None)},
+                f"first_{n_ref}_vs_best_incl_reference": {"plain_pso": stats(plain, sub, ref),
+                                                          "lm_polished": stats(pol, sub, ref)}}}
 
 
 # ---------------------------------------------------------------------------
@@ -314,13 +404,27 @@ def run_c4(A, W, dev, flush):
                                                     spec["polish_steps"]))
     plain = A.make_pso(dict(spec, iters=100))
     ms_pso, r_pso = timed(lambda: A.invert(prob, U, plain))
+    lp = spec["lm_polish"]
+    cfg_lm = A.make_pso(dict(spec, iters=lp["iters"]))
+    ms_lm, r_lm = timed(lambda: A.invert_polished(prob, U, cfg_lm, lp["polish_k"], lp["polish_steps"],
+                                                  lp["n_cand"], method="lm"))
+    var = (spec["sigma"] / 1e-9) ** 2
+    S_best = min(r_pol["S_f64"], r_pso["S_f64"], r_lm["S_f64"])
     return {"workload": "c4: 3-mode DMT + Kelvin-Voigt, 5 unknowns, 100 cycles x 256 steps",
+            "lm_polished": {"config": f"1024 particles x {lp['iters']} updates + {lp['polish_steps']} "
+                                      f"Levenberg-Marquardt steps on the best {lp['polish_k']} "
+                                      f"({lp['n_cand']} damping values per step)",
+                            "ms_per_inversion": ms_lm, "S_f64_nm2": r_lm["S_f64"],
+                            "dchi2_vs_best": (r_lm["S_f64"] - S_best) / var,
+                            "ident_rel_err_vs_truth": ident_errors(list(r_lm["theta"]), th_true)},
             "polished": {"config": "1024 particles x 40 updates + 20 adjoint-gradient polish "
                                    "steps on the best 32 (16 Armijo candidates per step)",
                          "ms_per_inversion": ms_pol, "S_f64_nm2": r_pol["S_f64"],
+                         "dchi2_vs_best": (r_pol["S_f64"] - S_best) / var,
                          "ident_rel_err_vs_truth": ident_errors(list(r_pol["theta"]), th_true)},
             "plain_pso": {"config": "1024 particles x 100 updates",
                           "ms_per_inversion": ms_pso, "S_f64_nm2": r_pso["S_f64"],
+                          "dchi2_vs_best": (r_pso["S_f64"] - S_best) / var,
                           "ident_rel_err_vs_truth": ident_errors(list(r_pso["theta"]), th_true)},
             "ident": "H R, E* sqrt(R), a0, eta sqrt(R)"}
 

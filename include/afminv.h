@@ -227,27 +227,47 @@ afm_status afm_adjoint(afm_ctx* ctx, const afm_problem* prob, const float* x, in
                        const float* U, float* S, float* dS_dx, void* workspace,
                        size_t workspace_bytes, void* stream);
 
+/* ---- residual sensitivities (forward mode) ---------------------------------
+ * For P parameter sets x [D][P] (device, normalised): S [P] (bit-identical
+ * to afm_forward_batch), and the normal equations of the misfit Eq. 5,
+ * H [P][D][D] = sum_n a_n a_n^T and b [P][D] = sum_n a_n (U_n - u_n), with
+ * a_n = du_n/dx the tangent-linear sensitivities of the FP32 RK4 recurrence
+ * (Eq. 2, Sec. 3.2) accumulated in FP32 blocks of 32 steps and FP64 totals.
+ * -2 b is the misfit gradient (as afm_adjoint's dS_dx); 2 H is the
+ * Gauss-Newton Hessian.  H and b are device FP64 arrays. */
+afm_status afm_normal_equations(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
+                                const float* U, float* S, double* H, double* b, void* stream);
+
 /* ---- gradient polish ------------------------------------------------------
- * K candidates x [D][K] (device, in/out) take `steps` projected steepest-
- * descent steps in the normalised cube: gradient g by afm_adjoint, direction
- * -g / max_d |g_d|, trial points clamp(x + a_j dir) with a_j = 0.05 * 0.5^j
- * (j < n_cand), all evaluated in one batched forward launch; the largest step
- * with S(x_j) <= S(x) + 1e-4 g.(x_j - x) is taken, else x stays.  S [K]
- * (device) receives the final misfits.  workspace >= afm_polish_workspace_size.
+ * K candidates x [D][K] (device, in/out) take `steps` steps in the
+ * normalised cube; S [K] (device) receives the final misfits.
+ *   AFM_POLISH_STEEPEST: gradient g by afm_adjoint, direction -g / max_d |g_d|,
+ *     trial points clamp(x + a_j dir) with a_j = 0.05 * 0.5^j (j < n_cand);
+ *     the largest step with S(x_j) <= S(x) + 1e-4 g.(x_j - x) is taken, else
+ *     x stays.
+ *   AFM_POLISH_LM (Levenberg-Marquardt): normal equations by
+ *     afm_normal_equations, trial points clamp(x + delta_j) with
+ *     (H + lambda_j W) delta_j = b, lambda_j = 1e-7 * 10^j (j < n_cand),
+ *     W = diag(max(H_dd, 1e-12 max_e H_ee)); the trial point of least misfit
+ *     replaces x if it lowers the misfit.
+ * All trial points of a step are evaluated in one batched forward launch.
+ * workspace >= afm_polish_workspace_size.
  * afm_invert_polished: the inversion of afm_invert (cfg->iters updates), then
  * the polish_k particles of lowest personal-best misfit are polished for
  * polish_steps steps and the best of them is re-evaluated in FP64 into
  * `result` (result->winner = its swarm index).  history as afm_invert. */
-afm_status afm_polish_workspace_size(const afm_problem* prob, int K, int n_cand, size_t* bytes);
+typedef enum { AFM_POLISH_STEEPEST = 0, AFM_POLISH_LM = 1 } afm_polish_method;
+afm_status afm_polish_workspace_size(const afm_problem* prob, int K, int n_cand, int method,
+                                     size_t* bytes);
 afm_status afm_polish(afm_ctx* ctx, const afm_problem* prob, const float* U, float* x, float* S,
-                      int K, int steps, int n_cand, void* workspace, size_t workspace_bytes,
-                      void* stream);
+                      int K, int steps, int n_cand, int method, void* workspace,
+                      size_t workspace_bytes, void* stream);
 afm_status afm_invert_polished_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
-                                              int polish_k, int n_cand, size_t* bytes);
+                                              int polish_k, int n_cand, int method, size_t* bytes);
 afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const float* U,
                                const afm_pso_cfg* cfg, int polish_k, int polish_steps, int n_cand,
-                               void* workspace, size_t workspace_bytes, afm_result* result,
-                               float* history, void* stream);
+                               int method, void* workspace, size_t workspace_bytes,
+                               afm_result* result, float* history, void* stream);
 
 /* ---- many pixel inversions in one launch (image scans) -------------------
  * n_pix independent IPs, pixel i with record U_cat[off[i] .. off[i+1]) (its
@@ -271,6 +291,28 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
                             const int64_t* off, int n_pix, uint32_t pixel0,
                             const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
                             afm_result* results, int* particles_per_thread, void* stream);
+
+/* ---- many pixel inversions with gradient polish --------------------------
+ * afm_invert_batch (same queue, swarms and autotuner; no graph capture), then
+ * for every pixel the polish_k personal bests of lowest misfit (lowest index
+ * on ties) take polish_steps steps of the polish of afm_polish (`method`,
+ * n_cand trial points), all pixels' candidates together in each launch;
+ * the candidate of lowest misfit is the pixel's winner
+ * (results[i].winner = its swarm index) and is re-evaluated in FP64 as in
+ * afm_invert_batch.  Per candidate the arithmetic equals afm_invert_polished
+ * on that pixel alone.  AFM_POLISH_STEEPEST: prob->n_steps must be >= the
+ * longest record, as it sizes the adjoint checkpoints (a longer record keeps
+ * its swarm winner).
+ * workspace: device, >= afm_invert_batch_polished_workspace_size, 256-aligned. */
+afm_status afm_invert_batch_polished_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
+                                                    int n_pix, int polish_k, int n_cand,
+                                                    int method, size_t* bytes);
+afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
+                                     const int64_t* off, int n_pix, uint32_t pixel0,
+                                     const afm_pso_cfg* cfg, int polish_k, int polish_steps,
+                                     int n_cand, int method, void* workspace,
+                                     size_t workspace_bytes, afm_result* results,
+                                     int* particles_per_thread, void* stream);
 
 /* ---- inversion without any device allocation ----------------------------
  * The paper has no counterpart: this entry point exists for callers that

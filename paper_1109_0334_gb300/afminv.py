@@ -100,16 +100,24 @@ def lib():
                                      C.c_size_t, vp, vp, vp]
             L.afm_adjoint_workspace_size.argtypes = [C.POINTER(Problem), i, C.POINTER(C.c_size_t)]
             L.afm_adjoint.argtypes = [vp, C.POINTER(Problem), vp, i, vp, vp, vp, vp, C.c_size_t, vp]
-            L.afm_polish_workspace_size.argtypes = [C.POINTER(Problem), i, i, C.POINTER(C.c_size_t)]
-            L.afm_polish.argtypes = [vp, C.POINTER(Problem), vp, vp, vp, i, i, i, vp, C.c_size_t, vp]
+            L.afm_normal_equations.argtypes = [vp, C.POINTER(Problem), vp, i, vp, vp, vp, vp, vp]
+            L.afm_polish_workspace_size.argtypes = [C.POINTER(Problem), i, i, i,
+                                                    C.POINTER(C.c_size_t)]
+            L.afm_polish.argtypes = [vp, C.POINTER(Problem), vp, vp, vp, i, i, i, i, vp, C.c_size_t,
+                                     vp]
             L.afm_invert_polished_workspace_size.argtypes = [C.POINTER(Problem), C.POINTER(PsoCfg),
-                                                             i, i, C.POINTER(C.c_size_t)]
+                                                             i, i, i, C.POINTER(C.c_size_t)]
             L.afm_invert_polished.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), i, i,
-                                              i, vp, C.c_size_t, vp, vp, vp]
+                                              i, i, vp, C.c_size_t, vp, vp, vp]
             L.afm_invert_batch_workspace_size.argtypes = [i, C.POINTER(C.c_size_t)]
             L.afm_invert_batch.argtypes = [vp, C.POINTER(Problem), vp, vp, i, u32,
                                            C.POINTER(PsoCfg), vp, C.c_size_t, vp,
                                            C.POINTER(C.c_int), vp]
+            L.afm_invert_batch_polished_workspace_size.argtypes = [
+                C.POINTER(Problem), C.POINTER(PsoCfg), i, i, i, i, C.POINTER(C.c_size_t)]
+            L.afm_invert_batch_polished.argtypes = [vp, C.POINTER(Problem), vp, vp, i, u32,
+                                                    C.POINTER(PsoCfg), i, i, i, i, vp, C.c_size_t,
+                                                    vp, C.POINTER(C.c_int), vp]
             L.afm_invert_noalloc.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), vp,
                                              vp, vp]
             L.afm_synth_records.argtypes = [vp, C.POINTER(Problem), vp, i, vp, i, d, u64, u32,
@@ -360,44 +368,69 @@ def misfit_autograd(prob: Problem, x, U):
     return _MISFIT.apply(x, prob, U)
 
 
-def polish_workspace_size(prob: Problem, K: int, n_cand: int = 16) -> int:
+POLISH_STEEPEST, POLISH_LM = 0, 1
+_METHOD = {"steepest": POLISH_STEEPEST, "lm": POLISH_LM}
+
+
+def _method(m) -> int:
+    return _METHOD[m] if isinstance(m, str) else int(m)
+
+
+def normal_equations(prob: Problem, x, U, stream=None):
+    """Misfit S [P] and its normal equations H [P, D, D], b [P, D] (FP64) from
+    the tangent-linear sensitivities, for x float32 CUDA [D, P]."""
+    import torch
+    D, P = int(x.shape[0]), int(x.shape[1])
+    S = torch.empty(P, dtype=torch.float32, device=x.device)
+    H = torch.empty((P, D, D), dtype=torch.float64, device=x.device)
+    b = torch.empty((P, D), dtype=torch.float64, device=x.device)
+    _check(lib().afm_normal_equations(context(x.device.index), C.byref(prob), _ptr(x), P, _ptr(U),
+                                      _ptr(S), _ptr(H), _ptr(b), _stream(stream)))
+    return S, H, b
+
+
+def polish_workspace_size(prob: Problem, K: int, n_cand: int = 16, method="steepest") -> int:
     n = C.c_size_t()
-    _check(lib().afm_polish_workspace_size(C.byref(prob), int(K), int(n_cand), C.byref(n)))
+    _check(lib().afm_polish_workspace_size(C.byref(prob), int(K), int(n_cand), _method(method),
+                                           C.byref(n)))
     return int(n.value)
 
 
 def invert_polished_workspace_size(prob: Problem, cfg: PsoCfg, polish_k: int = 32,
-                                   n_cand: int = 16) -> int:
+                                   n_cand: int = 16, method="steepest") -> int:
     n = C.c_size_t()
     _check(lib().afm_invert_polished_workspace_size(C.byref(prob), C.byref(cfg), int(polish_k),
-                                                    int(n_cand), C.byref(n)))
+                                                    int(n_cand), _method(method), C.byref(n)))
     return int(n.value)
 
 
-def polish(prob: Problem, U, x, steps: int, n_cand: int = 16, stream=None):
+def polish(prob: Problem, U, x, steps: int, n_cand: int = 16, method="steepest", stream=None):
     """Projected-gradient polish of candidates x float32 CUDA [D, K] (in
     place); returns their misfits S [K]."""
     import torch
     D, K = int(x.shape[0]), int(x.shape[1])
     n = C.c_size_t()
-    _check(lib().afm_polish_workspace_size(C.byref(prob), K, int(n_cand), C.byref(n)))
+    _check(lib().afm_polish_workspace_size(C.byref(prob), K, int(n_cand), _method(method),
+                                           C.byref(n)))
     ws = torch.empty(int(n.value), dtype=torch.uint8, device=x.device)
     S = torch.empty(K, dtype=torch.float32, device=x.device)
     _check(lib().afm_polish(context(x.device.index), C.byref(prob), _ptr(U), _ptr(x), _ptr(S), K,
-                            int(steps), int(n_cand), _ptr(ws), C.c_size_t(ws.numel()),
+                            int(steps), int(n_cand), _method(method), _ptr(ws),
+                            C.c_size_t(ws.numel()),
                             _stream(stream)))
     return S
 
 
 def invert_polished(prob: Problem, U, cfg: PsoCfg, polish_k: int = 32, polish_steps: int = 20,
-                    n_cand: int = 16, workspace=None, result=None, history=None, stream=None):
+                    n_cand: int = 16, workspace=None, result=None, history=None, stream=None,
+                    method="steepest"):
     """PSO (cfg) then gradient polish of the best polish_k particles; returns
     (result uint8 tensor, history)."""
     import torch
     dev = U.device
     n = C.c_size_t()
     _check(lib().afm_invert_polished_workspace_size(C.byref(prob), C.byref(cfg), int(polish_k),
-                                                    int(n_cand), C.byref(n)))
+                                                    int(n_cand), _method(method), C.byref(n)))
     if workspace is None or workspace.numel() < n.value:
         workspace = torch.empty(int(n.value), dtype=torch.uint8, device=dev)
     if result is None:
@@ -406,7 +439,8 @@ def invert_polished(prob: Problem, U, cfg: PsoCfg, polish_k: int = 32, polish_st
         history = torch.empty(cfg.iters + 1, dtype=torch.float32, device=dev)
     _check(lib().afm_invert_polished(context(dev.index), C.byref(prob), _ptr(U), C.byref(cfg),
                                      int(polish_k), int(polish_steps), int(n_cand),
-                                     _ptr(workspace), C.c_size_t(workspace.numel()), _ptr(result),
+                                     _method(method), _ptr(workspace),
+                                     C.c_size_t(workspace.numel()), _ptr(result),
                                      _ptr(history), _stream(stream)))
     return result, history
 
@@ -435,6 +469,39 @@ def invert_batch(prob: Problem, U_cat, off, cfg: PsoCfg, pixel0: int = 0,
                                   int(pixel0), C.byref(cfg), _ptr(workspace),
                                   C.c_size_t(workspace.numel()), _ptr(results), C.byref(kp),
                                   _stream(stream)))
+    return results, kp.value
+
+
+def invert_batch_polished_workspace_size(prob: Problem, cfg: PsoCfg, n_pix: int, polish_k: int,
+                                         n_cand: int = 16, method="steepest") -> int:
+    n = C.c_size_t()
+    _check(lib().afm_invert_batch_polished_workspace_size(C.byref(prob), C.byref(cfg), int(n_pix),
+                                                          int(polish_k), int(n_cand),
+                                                          _method(method), C.byref(n)))
+    return int(n.value)
+
+
+def invert_batch_polished(prob: Problem, U_cat, off, cfg: PsoCfg, polish_k: int, polish_steps: int,
+                          n_cand: int = 16, pixel0: int = 0, particles_per_thread: int = 0,
+                          workspace=None, results=None, stream=None, method="steepest"):
+    """Many pixel inversions, each followed by the gradient polish of its
+    polish_k best particles (afm_invert_batch_polished).  prob.n_steps must
+    bound the record lengths.  Returns (results, particles per thread used)."""
+    import torch
+    dev = U_cat.device
+    n_pix = int(off.shape[0]) - 1
+    nbytes = invert_batch_polished_workspace_size(prob, cfg, n_pix, polish_k, n_cand, method)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    if results is None:
+        results = torch.zeros((n_pix, C.sizeof(Result)), dtype=torch.uint8, device=dev)
+    kp = C.c_int(int(particles_per_thread))
+    _check(lib().afm_invert_batch_polished(context(dev.index), C.byref(prob), _ptr(U_cat), _ptr(off),
+                                           n_pix, int(pixel0), C.byref(cfg), int(polish_k),
+                                           int(polish_steps), int(n_cand), _method(method),
+                                           _ptr(workspace),
+                                           C.c_size_t(workspace.numel()), _ptr(results),
+                                           C.byref(kp), _stream(stream)))
     return results, kp.value
 
 

@@ -196,6 +196,59 @@ __device__ __forceinline__ void force_partials(const Coef<float>& c, float d, fl
     }
 }
 
+// d c_k / d x_d (double) of the coefficient map in make_coef.
+template <typename X>
+__device__ __forceinline__ void coef_jacobian(const KConst<float>& K, const X* xd, double J[4][AFM_MAXD]) {
+    double th[AFM_MAXD], dth[AFM_MAXD];
+    int slot_of_dim[AFM_MAXD];
+    for (int s = 0; s < AFM_MAXD; ++s) th[s] = K.fixed[s];
+    for (int d = 0; d < K.D; ++d) {
+        double v = K.lo[d] + (double)xd[d] * K.span[d];
+        if (K.logs[d]) {
+            v = exp10(v);
+            dth[d] = v * 2.302585092994045684 * K.span[d];
+        } else {
+            dth[d] = K.span[d];
+        }
+        th[K.slot[d]] = v;
+        slot_of_dim[d] = K.slot[d];
+    }
+    double dc[4][AFM_MAXD];   // d c_k / d theta_s
+    for (int k = 0; k < 4; ++k)
+        for (int s = 0; s < AFM_MAXD; ++s) dc[k][s] = 0.0;
+    const double rt = 3.1622776601683794e-5;
+    switch (K.force) {
+        case F_LINEAR:
+        case F_HOOKE:
+            dc[0][0] = K.s1 / K.k;
+            dc[1][1] = 1e9;
+            break;
+        case F_SPRING_DAMPER:
+            dc[0][0] = K.s1 / K.k;
+            dc[1][1] = 1e9;
+            dc[2][2] = K.s1 / (K.k * K.tau);
+            break;
+        case F_DMT:
+        case F_DMT_KV: {
+            const double sR = sqrt(th[2]);
+            const double A = (4.0 / 3.0) * rt / K.k * K.s1;
+            const double B = K.s1 / (6e-27 * K.k);
+            const double C = rt * K.s1 / (K.k * K.tau);
+            dc[0][0] = A * sR;
+            dc[0][2] = A * th[0] / (2.0 * sR);
+            dc[1][1] = B * th[2];
+            dc[1][2] = B * th[1];
+            dc[2][4] = C * sR;
+            dc[2][2] = C * th[4] / (2.0 * sR);
+            dc[3][3] = 1e9;
+            break;
+        }
+    }
+    for (int k = 0; k < 4; ++k)
+        for (int d = 0; d < AFM_MAXD; ++d)
+            J[k][d] = d < K.D ? dc[k][slot_of_dim[d]] * dth[d] : 0.0;
+}
+
 // Modal accelerations (Eq. 2): a_i = tip_i F + gamma_i g - w2_i q_i - wq_i q_i'.
 // Mode 0's stiffness carries a low word (w2lo) so that the resonant mode's
 // frequency is represented to ~1e-15 in FP32 arithmetic.

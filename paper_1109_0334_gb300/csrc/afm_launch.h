@@ -48,6 +48,8 @@ struct BatchArgs {
     uint32_t pixel0;       // Philox counter word 2 of pixel 0
     int* queue;            // pixel counter (zeroed before the launch)
     afm_result* res;       // [n_pix]
+    float* pb_out;         // nullptr, or per queue slot the final personal bests
+                           // [D][P] followed by their misfits [P]
 };
 int batch_threads(int P, int kp);
 size_t batch_smem(int P, int D, int spc2);
@@ -60,9 +62,36 @@ cudaError_t launch_batch_final(const KConst<double>& K, const PsoConst& pc, cons
                                cudaStream_t st);
 
 // discrete adjoint (gradient of the misfit wrt the normalised parameters)
+// Ragged form (off != nullptr): particle p belongs to queue slot p / per_slot,
+// pixel order[slot] (or the slot itself), and is compared with that pixel's
+// record U + off[pix] of length off[pix+1] - off[pix] <= K.n_steps; records
+// longer than K.n_steps give S = inf and a zero gradient.
 size_t adjoint_ckpt_floats(int m, int n_steps, int P);
 cudaError_t launch_adjoint(const KConst<float>& K, const float* x, int P, const float* U, float* S,
-                           float* G, float* ckpt, cudaStream_t st);
+                           float* G, float* ckpt, cudaStream_t st, const int64_t* off = nullptr,
+                           const int* order = nullptr, int per_slot = 1);
+
+// Levenberg-Marquardt polish (kern_lm.cu): sensitivity pass (S [P], H
+// [P][D][D], b [P][D]; ragged form as launch_adjoint), damped trial points,
+// choice of the best trial point
+cudaError_t launch_sens(const KConst<float>& K, const float* x, int P, const float* U, float* S,
+                        double* H, double* b, cudaStream_t st, const int64_t* off = nullptr,
+                        const int* order = nullptr, int per_slot = 1);
+cudaError_t launch_lm_cand(int D, int K, int J, const float* x, const double* H, const double* b,
+                           double lam0, double ratio, float* Xc, cudaStream_t st);
+cudaError_t launch_lm_select(int D, int K, int J, float* x, float* S, const float* Xc,
+                             const float* Sc, cudaStream_t st);
+
+// batched polish (kern_bpolish.cu): candidates of queue slot s are columns
+// s * Kc .. s * Kc + Kc - 1 of [D][n_pix * Kc] arrays
+cudaError_t launch_topk_pix(const float* pb_all, int n_pix, int P, int D, int Kc, float* xk,
+                            float* Sk, int* ik, cudaStream_t st);
+cudaError_t launch_forward_ragged(const KConst<float>& K, const float* x, int Ptot, const float* U_cat,
+                                  const int64_t* off, const int* order, int per_slot, float* S,
+                                  cudaStream_t st);
+cudaError_t launch_pick_pix(int n_pix, int D, int Kc, const float* xk, const float* Sk,
+                            const int* ik, const int* order, int iters, afm_result* res,
+                            cudaStream_t st);
 
 // gradient polish
 cudaError_t launch_polish_cand(int D, int K, int J, const float* x, const float* G, double alpha0,

@@ -997,62 +997,119 @@ afm_status afm_adjoint(afm_ctx* ctx, const afm_problem* prob, const float* x, in
     return AFM_OK;
 }
 
-// Polish workspace: gradient [D][K], candidates [D][K*J], their misfits
-// [K*J], adjoint checkpoints of K particles.
+afm_status afm_normal_equations(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
+                                const float* U, float* S, double* H, double* b, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    if ((st = modal_only(prob, "afm_normal_equations"))) return st;
+    if ((st = check_ctx(ctx))) return st;
+    if (!x || !U || !S || !H || !b || P < 1 || prob->n_free < 1)
+        return fail(AFM_ERR_INVALID_ARG, "NULL array, P < 1 or no free parameter");
+    KConst<float> K32;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K32);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_sens(K32, x, P, U, S, H, b, s); }),
+             "sensitivity kernel");
+    return AFM_OK;
+}
+
+// Polish workspace.  Steepest descent: gradient [D][K], adjoint checkpoints
+// of K particles; Levenberg-Marquardt: normal equations H [K][D][D], b
+// [K][D] (FP64); both: trial points [D][K*J] and their misfits [K*J].
 struct PolishLayout {
-    size_t G, Xc, Sc, ckpt, total;
+    size_t G, ckpt, H, b, Xc, Sc, total;
 };
 
-PolishLayout polish_layout(const afm_problem& pr, int K, int J) {
+PolishLayout polish_layout(const afm_problem& pr, int K, int J, int method) {
     PolishLayout L;
-    const int D = pr.n_free;
+    const size_t D = (size_t)pr.n_free;
     const int m = pr.model == AFM_POINT_MASS ? 1 : pr.n_modes;
     size_t off = 0;
-    L.G = off; off += align256(sizeof(float) * (size_t)D * K);
-    L.Xc = off; off += align256(sizeof(float) * (size_t)D * K * J);
+    L.G = L.ckpt = L.H = L.b = 0;
+    if (method == AFM_POLISH_LM) {
+        L.H = off; off += align256(sizeof(double) * (size_t)K * D * D);
+        L.b = off; off += align256(sizeof(double) * (size_t)K * D);
+    } else {
+        L.G = off; off += align256(sizeof(float) * D * K);
+        L.ckpt = off; off += align256(sizeof(float) * afm::adjoint_ckpt_floats(m, pr.n_steps, K));
+    }
+    L.Xc = off; off += align256(sizeof(float) * D * K * J);
     L.Sc = off; off += align256(sizeof(float) * (size_t)K * J);
-    L.ckpt = off; off += align256(sizeof(float) * afm::adjoint_ckpt_floats(m, pr.n_steps, K));
     L.total = off;
     return L;
 }
 
 const double kPolishAlpha0 = 0.05, kPolishShrink = 0.5, kPolishSigma = 1e-4;
+const double kLmLambda0 = 1e-7, kLmRatio = 10.0;
 
-afm_status polish_run(afm_ctx* ctx, const afm_problem& pr, const KConst<float>& K, const float* U,
-                      float* x, float* S, int Kn, int steps, int J, char* ws, cudaStream_t s) {
-    const PolishLayout L = polish_layout(pr, Kn, J);
-    float* G = reinterpret_cast<float*>(ws + L.G);
+// One polish step of Kn candidates x [D][Kn] (S [Kn] receives the misfit at
+// the step's start, then that of the point kept).  Ragged form (off !=
+// nullptr): candidate k is compared with the record of pixel order[k / per].
+afm_status polish_step(afm_ctx* ctx, const KConst<float>& K, int method, const float* U,
+                       const int64_t* off, const int* order, int per, float* x, float* S, int Kn,
+                       int J, const PolishLayout& L, char* ws, cudaStream_t s) {
     float* Xc = reinterpret_cast<float*>(ws + L.Xc);
     float* Sc = reinterpret_cast<float*>(ws + L.Sc);
-    float* ck = reinterpret_cast<float*>(ws + L.ckpt);
-    const int D = pr.n_free;
-    for (int st = 0; st < steps; ++st) {
-        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_adjoint(K, x, Kn, U, S, G, ck, s); }),
+    const int D = K.D;
+    if (method == AFM_POLISH_LM) {
+        double* H = reinterpret_cast<double*>(ws + L.H);
+        double* b = reinterpret_cast<double*>(ws + L.b);
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_sens(K, x, Kn, U, S, H, b, s, off, order, per); }),
+                 "sensitivity kernel");
+        AFM_CUDA(afm::launch_lm_cand(D, Kn, J, x, H, b, kLmLambda0, kLmRatio, Xc, s), "LM trial kernel");
+    } else {
+        float* G = reinterpret_cast<float*>(ws + L.G);
+        float* ck = reinterpret_cast<float*>(ws + L.ckpt);
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_adjoint(K, x, Kn, U, S, G, ck, s, off, order, per); }),
                  "adjoint kernel");
         AFM_CUDA(afm::launch_polish_cand(D, Kn, J, x, G, kPolishAlpha0, kPolishShrink, Xc, s),
                  "polish candidate kernel");
+    }
+    if (off != nullptr)
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_ragged(K, Xc, Kn * J, U, off, order, per * J, Sc, s); }),
+                 "ragged forward kernel");
+    else
         AFM_CUDA(afm::launch_forward_f32(K, Xc, Kn * J, nullptr, U, Sc, nullptr, s), "forward kernel");
+    if (method == AFM_POLISH_LM) {
+        AFM_CUDA(afm::launch_lm_select(D, Kn, J, x, S, Xc, Sc, s), "LM select kernel");
+    } else {
+        const float* G = reinterpret_cast<const float*>(ws + L.G);
         AFM_CUDA(afm::launch_polish_select(D, Kn, J, (float)kPolishSigma, x, G, S, Xc, Sc, s),
                  "polish select kernel");
+    }
+    return AFM_OK;
+}
+
+afm_status polish_run(afm_ctx* ctx, const afm_problem& pr, const KConst<float>& K, const float* U,
+                      float* x, float* S, int Kn, int steps, int J, int method, char* ws,
+                      cudaStream_t s) {
+    const PolishLayout L = polish_layout(pr, Kn, J, method);
+    for (int st = 0; st < steps; ++st) {
+        afm_status e = polish_step(ctx, K, method, U, nullptr, nullptr, 1, x, S, Kn, J, L, ws, s);
+        if (e) return e;
     }
     if (steps == 0)
         AFM_CUDA(afm::launch_forward_f32(K, x, Kn, nullptr, U, S, nullptr, s), "forward kernel");
     return AFM_OK;
 }
 
-afm_status afm_polish_workspace_size(const afm_problem* prob, int K, int n_cand, size_t* bytes) {
+afm_status afm_polish_workspace_size(const afm_problem* prob, int K, int n_cand, int method,
+                                     size_t* bytes) {
     g_err[0] = 0;
     if (!bytes || K < 1 || n_cand < 1 || n_cand > 64)
         return fail(AFM_ERR_INVALID_ARG, "K >= 1, 1 <= n_cand <= 64 and bytes needed");
     afm_status st = check_problem(prob);
     if (st) return st;
-    *bytes = polish_layout(*prob, K, n_cand).total;
+    if (method != AFM_POLISH_STEEPEST && method != AFM_POLISH_LM)
+        return fail(AFM_ERR_INVALID_ARG, "unknown polish method %d", method);
+    *bytes = polish_layout(*prob, K, n_cand, method).total;
     return AFM_OK;
 }
 
 afm_status afm_polish(afm_ctx* ctx, const afm_problem* prob, const float* U, float* x, float* S,
-                      int K, int steps, int n_cand, void* workspace, size_t workspace_bytes,
-                      void* stream) {
+                      int K, int steps, int n_cand, int method, void* workspace,
+                      size_t workspace_bytes, void* stream) {
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
@@ -1061,18 +1118,18 @@ afm_status afm_polish(afm_ctx* ctx, const afm_problem* prob, const float* U, flo
     if (!U || !x || !S || !workspace || K < 1 || steps < 0 || prob->n_free < 1)
         return fail(AFM_ERR_INVALID_ARG, "NULL array, K < 1, steps < 0 or no free parameter");
     size_t need = 0;
-    if ((st = afm_polish_workspace_size(prob, K, n_cand, &need))) return st;
+    if ((st = afm_polish_workspace_size(prob, K, n_cand, method, &need))) return st;
     if (workspace_bytes < need || reinterpret_cast<uintptr_t>(workspace) % 256)
         return fail(AFM_ERR_INVALID_ARG, "workspace too small (%zu < %zu) or misaligned",
                     workspace_bytes, need);
     KConst<float> K32;
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K32);
-    return polish_run(ctx, *prob, K32, U, x, S, K, steps, n_cand, static_cast<char*>(workspace),
-                      reinterpret_cast<cudaStream_t>(stream));
+    return polish_run(ctx, *prob, K32, U, x, S, K, steps, n_cand, method,
+                      static_cast<char*>(workspace), reinterpret_cast<cudaStream_t>(stream));
 }
 
 afm_status afm_invert_polished_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
-                                              int polish_k, int n_cand, size_t* bytes) {
+                                              int polish_k, int n_cand, int method, size_t* bytes) {
     g_err[0] = 0;
     if (!bytes) return fail(AFM_ERR_INVALID_ARG, "bytes is NULL");
     afm_status st = check_problem(prob);
@@ -1080,18 +1137,21 @@ afm_status afm_invert_polished_workspace_size(const afm_problem* prob, const afm
     if ((st = check_pso(cfg, prob->n_free))) return st;
     if (polish_k < 1 || polish_k > cfg->P || n_cand < 1 || n_cand > 64)
         return fail(AFM_ERR_INVALID_ARG, "1 <= polish_k <= P and 1 <= n_cand <= 64 needed");
+    if (method != AFM_POLISH_STEEPEST && method != AFM_POLISH_LM)
+        return fail(AFM_ERR_INVALID_ARG, "unknown polish method %d", method);
     const size_t inv = invert_layout(cfg->P, prob->n_free).total;
     const size_t xk = align256(sizeof(float) * (size_t)prob->n_free * polish_k);
     const size_t sk = align256(sizeof(float) * (size_t)polish_k);
     const size_t ik = align256(sizeof(int) * (size_t)polish_k);
-    *bytes = inv + xk + sk + ik + polish_layout(*prob, polish_k, n_cand).total + reeval_extra(*prob);
+    *bytes = inv + xk + sk + ik + polish_layout(*prob, polish_k, n_cand, method).total +
+             reeval_extra(*prob);
     return AFM_OK;
 }
 
 afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const float* U,
                                const afm_pso_cfg* cfg, int polish_k, int polish_steps, int n_cand,
-                               void* workspace, size_t workspace_bytes, afm_result* result,
-                               float* history, void* stream) {
+                               int method, void* workspace, size_t workspace_bytes,
+                               afm_result* result, float* history, void* stream) {
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
@@ -1102,7 +1162,8 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
         return fail(AFM_ERR_INVALID_ARG, "NULL U, result or workspace, or polish_steps < 0");
     if (cfg->P > 8192) return fail(AFM_ERR_INVALID_ARG, "polished inversion supports P <= 8192");
     size_t need = 0;
-    if ((st = afm_invert_polished_workspace_size(prob, cfg, polish_k, n_cand, &need))) return st;
+    if ((st = afm_invert_polished_workspace_size(prob, cfg, polish_k, n_cand, method, &need)))
+        return st;
     if (workspace_bytes < need || reinterpret_cast<uintptr_t>(workspace) % 256)
         return fail(AFM_ERR_INVALID_ARG, "workspace too small (%zu < %zu) or misaligned",
                     workspace_bytes, need);
@@ -1130,10 +1191,11 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
                  "invert iteration kernel");
     const int fin = (cfg->iters + 1) & 1;
     AFM_CUDA(afm::launch_topk(sw.pbS, sw.pb[fin], P, D, polish_k, xk, ik, s), "top-k kernel");
-    if ((st = polish_run(ctx, *prob, Kf, U, xk, sk, polish_k, polish_steps, n_cand, pol, s))) return st;
+    if ((st = polish_run(ctx, *prob, Kf, U, xk, sk, polish_k, polish_steps, n_cand, method, pol, s)))
+        return st;
     if (reeval_extra(*prob) > 0) {
         afm::ReevalPtrs R;
-        afm::reeval_carve(pol + polish_layout(*prob, polish_k, n_cand).total, problem_modes(*prob),
+        afm::reeval_carve(pol + polish_layout(*prob, polish_k, n_cand, method).total, problem_modes(*prob),
                           prob->n_steps, prob->steps_per_cycle, &R);
         AFM_CUDA(afm::launch_reeval_pick_min(D, polish_k, xk, sk, ik, R.win, s), "winner pick kernel");
         AFM_CUDA(afm::launch_reeval(Kf, Kd, R, U, cfg->iters, sw.flags, result, s),
@@ -1152,34 +1214,46 @@ afm_status afm_invert_batch_workspace_size(int n_pix, size_t* bytes) {
     return AFM_OK;
 }
 
-afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
-                            const int64_t* off, int n_pix, uint32_t pixel0,
-                            const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
-                            afm_result* results, int* particles_per_thread, void* stream) {
-    g_err[0] = 0;
+}  // extern "C"
+
+namespace {
+
+// Validation and launch set-up shared by the batched inversions: constants,
+// the argument block (queue order sorted on `s`), and the particles per
+// thread (forced or autotuned) with the persistent grid size.
+struct BatchSetup {
+    KConst<float> Kf;
+    KConst<double> Kd;
+    afm::PsoConst pc;
+    afm::BatchArgs a;
+    int kp, grid;
+};
+
+afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
+                       const int64_t* off, int n_pix, uint32_t pixel0, const afm_pso_cfg* cfg,
+                       void* workspace, afm_result* results, int* particles_per_thread,
+                       cudaStream_t s, const char* who, BatchSetup* out) {
     afm_status st = check_problem(prob);
     if (st) return st;
-    if ((st = modal_only(prob, "afm_invert_batch"))) return st;
+    if ((st = modal_only(prob, who))) return st;
     if ((st = check_ctx(ctx))) return st;
     if ((st = check_pso(cfg, prob->n_free))) return st;
     if (!U_cat || !off || !results || !workspace || n_pix < 1)
         return fail(AFM_ERR_INVALID_ARG, "NULL U_cat, off, results or workspace, or n_pix < 1");
     if (reinterpret_cast<uintptr_t>(workspace) % 256)
         return fail(AFM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    const BatchLayout L = batch_layout(n_pix);
-    if (workspace_bytes < L.total)
-        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, L.total);
     if (cfg->P > 4096) return fail(AFM_ERR_INVALID_ARG, "batched swarms hold at most 4096 particles");
     const size_t smem = afm::batch_smem(cfg->P, prob->n_free, 2 * prob->steps_per_cycle);
     if (smem > 200 * 1024)
         return fail(AFM_ERR_INVALID_ARG, "swarm state of %zu bytes exceeds shared memory", smem);
+    const BatchLayout L = batch_layout(n_pix);
     char* ws = static_cast<char*>(workspace);
-    KConst<float> Kf;
-    KConst<double> Kd;
-    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kf);
-    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kd);
-    const afm::PsoConst pc = pso_const(*cfg, prob->n_free);
-    afm::BatchArgs a;
+    BatchSetup& B = *out;
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, B.Kf);
+    fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, B.Kd);
+    B.pc = pso_const(*cfg, prob->n_free);
+    afm::BatchArgs& a = B.a;
+    std::memset(&a, 0, sizeof(a));   // also the padding: the struct is part of a graph key
     a.U = U_cat;
     a.off = off;
     a.order = n_pix <= afm::batch_sort_max() ? reinterpret_cast<int*>(ws + L.order) : nullptr;
@@ -1187,24 +1261,52 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
     a.pixel0 = pixel0;
     a.queue = reinterpret_cast<int*>(ws + L.queue);
     a.res = results;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    a.pb_out = nullptr;
     // queue order (longest record first) is needed by the tuner's probe too
     if (a.order) AFM_CUDA(afm::batch_sort(off, n_pix, const_cast<int*>(a.order), s), "sort kernel");
     int kp = 0, occ = 0;
     const int want = particles_per_thread ? *particles_per_thread : 0;
+    const afm::PsoConst& pc = B.pc;
     if (want == 1 || want == 2 || want == 4) {
-        if (afm::batch_threads(pc.P, want) > 1024 || (want > 1 && Kf.m > 3))
+        if (afm::batch_threads(pc.P, want) > 1024 || (want > 1 && B.Kf.m > 3))
             return fail(AFM_ERR_INVALID_ARG, "particles_per_thread %d unsupported here", want);
         kp = want;
-        AFM_CUDA(afm::batch_occupancy(Kf.m, Kf.force, kp, pc.P, pc.D, Kf.spc2, &occ), "batch occupancy");
+        AFM_CUDA(afm::batch_occupancy(B.Kf.m, B.Kf.force, kp, pc.P, pc.D, B.Kf.spc2, &occ),
+                 "batch occupancy");
         if (occ < 1) return fail(AFM_ERR_UNSUPPORTED, "batch kernel does not fit (P = %d)", pc.P);
     } else if (want != 0) {
         return fail(AFM_ERR_INVALID_ARG, "particles_per_thread must be 0 (tune), 1, 2 or 4");
-    } else if ((st = batch_tune(ctx, Kf, pc, a, s, &kp, &occ))) {
+    } else if ((st = batch_tune(ctx, B.Kf, pc, a, s, &kp, &occ))) {
         return st;
     }
-    const int grid = std::min(n_pix, ctx->num_sms * occ);
+    B.kp = kp;
+    B.grid = std::min(n_pix, ctx->num_sms * occ);
     if (particles_per_thread) *particles_per_thread = kp;
+    return AFM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
+                            const int64_t* off, int n_pix, uint32_t pixel0,
+                            const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
+                            afm_result* results, int* particles_per_thread, void* stream) {
+    g_err[0] = 0;
+    if (n_pix >= 1 && workspace_bytes < batch_layout(n_pix).total)
+        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes,
+                    batch_layout(n_pix).total);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BatchSetup B;
+    afm_status st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, cfg, workspace, results,
+                                particles_per_thread, s, "afm_invert_batch", &B);
+    if (st) return st;
+    const KConst<float>& Kf = B.Kf;
+    const KConst<double>& Kd = B.Kd;
+    const afm::PsoConst& pc = B.pc;
+    const afm::BatchArgs& a = B.a;
+    const int kp = B.kp, grid = B.grid;
     // one graph: zero the queue, sort, persistent swarm kernel, FP64 winners
     std::vector<unsigned char> key;
     append_bytes(key, Kf);
@@ -1243,6 +1345,94 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
         ctx->batch_graphs.push_back({key, exec});
     }
     AFM_CUDA(cudaGraphLaunch(exec, s), "cudaGraphLaunch");
+    return AFM_OK;
+}
+
+// Workspace of the polished batch: the batch queue, every slot's final
+// personal bests, the Kc candidates per slot, then the polish workspace of
+// all n_pix * Kc candidates (polish_layout, checkpoints for the longest
+// record).
+struct BatchPolishLayout {
+    size_t pb, xk, Sk, ik, pol, total;
+    PolishLayout P;
+};
+
+static BatchPolishLayout batch_polish_layout(const afm_problem& pr, const afm_pso_cfg& cfg, int n_pix,
+                                             int Kc, int J, int method) {
+    BatchPolishLayout L;
+    const size_t D = (size_t)pr.n_free, P = (size_t)cfg.P, Nt = (size_t)n_pix * Kc;
+    size_t off = batch_layout(n_pix).total;
+    L.pb = off; off += align256(sizeof(float) * (size_t)n_pix * (D + 1) * P);
+    L.xk = off; off += align256(sizeof(float) * D * Nt);
+    L.Sk = off; off += align256(sizeof(float) * Nt);
+    L.ik = off; off += align256(sizeof(int) * Nt);
+    L.pol = off;
+    L.P = polish_layout(pr, (int)Nt, J, method);
+    L.total = off + L.P.total;
+    return L;
+}
+
+static afm_status check_batch_polish(const afm_problem* prob, const afm_pso_cfg* cfg, int n_pix,
+                                     int polish_k, int n_cand, int method) {
+    if (!prob || !cfg) return fail(AFM_ERR_INVALID_ARG, "NULL prob or cfg");
+    if (method != AFM_POLISH_STEEPEST && method != AFM_POLISH_LM)
+        return fail(AFM_ERR_INVALID_ARG, "unknown polish method %d", method);
+    if (n_pix < 1 || polish_k < 1 || polish_k > cfg->P || n_cand < 1 || n_cand > 64)
+        return fail(AFM_ERR_INVALID_ARG, "n_pix >= 1, 1 <= polish_k <= P and 1 <= n_cand <= 64 needed");
+    if ((size_t)n_pix * polish_k * n_cand > (size_t)1 << 30)
+        return fail(AFM_ERR_INVALID_ARG, "n_pix x polish_k x n_cand too large");
+    if (cfg->P > 4096) return fail(AFM_ERR_INVALID_ARG, "batched swarms hold at most 4096 particles");
+    return AFM_OK;
+}
+
+afm_status afm_invert_batch_polished_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
+                                                    int n_pix, int polish_k, int n_cand,
+                                                    int method, size_t* bytes) {
+    g_err[0] = 0;
+    if (!bytes) return fail(AFM_ERR_INVALID_ARG, "bytes is NULL");
+    afm_status st = check_batch_polish(prob, cfg, n_pix, polish_k, n_cand, method);
+    if (st) return st;
+    if ((st = check_problem(prob))) return st;
+    *bytes = batch_polish_layout(*prob, *cfg, n_pix, polish_k, n_cand, method).total;
+    return AFM_OK;
+}
+
+afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
+                                     const int64_t* off, int n_pix, uint32_t pixel0,
+                                     const afm_pso_cfg* cfg, int polish_k, int polish_steps,
+                                     int n_cand, int method, void* workspace, size_t workspace_bytes,
+                                     afm_result* results, int* particles_per_thread, void* stream) {
+    g_err[0] = 0;
+    afm_status st = check_batch_polish(prob, cfg, n_pix, polish_k, n_cand, method);
+    if (st) return st;
+    if (polish_steps < 0) return fail(AFM_ERR_INVALID_ARG, "polish_steps < 0");
+    if ((st = check_problem(prob))) return st;
+    const BatchPolishLayout PL = batch_polish_layout(*prob, *cfg, n_pix, polish_k, n_cand, method);
+    if (workspace_bytes < PL.total)
+        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, PL.total);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BatchSetup B;
+    if ((st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, cfg, workspace, results,
+                          particles_per_thread, s, "afm_invert_batch_polished", &B)))
+        return st;
+    char* ws = static_cast<char*>(workspace);
+    afm::BatchArgs a = B.a;
+    a.pb_out = reinterpret_cast<float*>(ws + PL.pb);
+    float* xk = reinterpret_cast<float*>(ws + PL.xk);
+    float* Sk = reinterpret_cast<float*>(ws + PL.Sk);
+    int* ik = reinterpret_cast<int*>(ws + PL.ik);
+    const int D = prob->n_free, Kc = polish_k, J = n_cand, Nt = n_pix * Kc;
+    AFM_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int), s), "cudaMemsetAsync");
+    AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_batch(B.Kf, B.pc, a, B.kp, B.grid, s); }),
+             "batch kernel");
+    AFM_CUDA(afm::launch_topk_pix(a.pb_out, n_pix, cfg->P, D, Kc, xk, Sk, ik, s), "top-k kernel");
+    for (int k = 0; k < polish_steps; ++k)
+        if ((st = polish_step(ctx, B.Kf, method, U_cat, off, a.order, Kc, xk, Sk, Nt, J, PL.P,
+                              ws + PL.pol, s)))
+            return st;
+    AFM_CUDA(afm::launch_pick_pix(n_pix, D, Kc, xk, Sk, ik, a.order, cfg->iters, results, s),
+             "winner pick kernel");
+    AFM_CUDA(afm::launch_batch_final(B.Kd, B.pc, a, s), "batch FP64 kernel");
     return AFM_OK;
 }
 

@@ -120,66 +120,16 @@ __device__ __forceinline__ void rk4_step_rec(const KConst<float>& K, const Coef<
     }
 }
 
-// d c_k / d x_d (double) of the coefficient map in make_coef.
-template <typename X>
-__device__ __forceinline__ void coef_jacobian(const KConst<float>& K, const X* xd, double J[4][AFM_MAXD]) {
-    double th[AFM_MAXD], dth[AFM_MAXD];
-    int slot_of_dim[AFM_MAXD];
-    for (int s = 0; s < AFM_MAXD; ++s) th[s] = K.fixed[s];
-    for (int d = 0; d < K.D; ++d) {
-        double v = K.lo[d] + (double)xd[d] * K.span[d];
-        if (K.logs[d]) {
-            v = exp10(v);
-            dth[d] = v * 2.302585092994045684 * K.span[d];
-        } else {
-            dth[d] = K.span[d];
-        }
-        th[K.slot[d]] = v;
-        slot_of_dim[d] = K.slot[d];
-    }
-    double dc[4][AFM_MAXD];   // d c_k / d theta_s
-    for (int k = 0; k < 4; ++k)
-        for (int s = 0; s < AFM_MAXD; ++s) dc[k][s] = 0.0;
-    const double rt = 3.1622776601683794e-5;
-    switch (K.force) {
-        case F_LINEAR:
-        case F_HOOKE:
-            dc[0][0] = K.s1 / K.k;
-            dc[1][1] = 1e9;
-            break;
-        case F_SPRING_DAMPER:
-            dc[0][0] = K.s1 / K.k;
-            dc[1][1] = 1e9;
-            dc[2][2] = K.s1 / (K.k * K.tau);
-            break;
-        case F_DMT:
-        case F_DMT_KV: {
-            const double sR = sqrt(th[2]);
-            const double A = (4.0 / 3.0) * rt / K.k * K.s1;
-            const double B = K.s1 / (6e-27 * K.k);
-            const double C = rt * K.s1 / (K.k * K.tau);
-            dc[0][0] = A * sR;
-            dc[0][2] = A * th[0] / (2.0 * sR);
-            dc[1][1] = B * th[2];
-            dc[1][2] = B * th[1];
-            dc[2][4] = C * sR;
-            dc[2][2] = C * th[4] / (2.0 * sR);
-            dc[3][3] = 1e9;
-            break;
-        }
-    }
-    for (int k = 0; k < 4; ++k)
-        for (int d = 0; d < AFM_MAXD; ++d)
-            J[k][d] = d < K.D ? dc[k][slot_of_dim[d]] * dth[d] : 0.0;
-}
-
 template <int M, int FORCE>
 __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(const KConst<float> K,
                                                               const float* __restrict__ x, int P,
                                                               const float* __restrict__ U,
                                                               float* __restrict__ S_out,
                                                               float* __restrict__ G,
-                                                              float* __restrict__ ckpt) {
+                                                              float* __restrict__ ckpt,
+                                                              const int64_t* __restrict__ off,
+                                                              const int* __restrict__ order,
+                                                              int per_slot) {
     extern __shared__ __align__(16) float sma[];
     float* tab = sma;
     float* seg = sma + ((K.spc2 + 1 + 3) & ~3);   // [SEG][SEGW][ADJ_THREADS]
@@ -188,7 +138,18 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(const KConst<float
     const int tid = threadIdx.x;
     const int p = blockIdx.x * blockDim.x + tid;
     if (p >= P) return;
-    const int N = K.n_steps;
+    int N = K.n_steps;
+    if (off != nullptr) {
+        const int slot = p / per_slot;
+        const int pix = order != nullptr ? order[slot] : slot;
+        U += off[pix];
+        N = (int)(off[pix + 1] - off[pix]);
+        if (N > K.n_steps) {   // beyond the checkpoint buffer
+            S_out[p] = INFINITY;
+            for (int d = 0; d < K.D; ++d) G[(size_t)d * P + p] = 0.f;
+            return;
+        }
+    }
     const int nseg = (N + SEG - 1) / SEG;
     float xd[AFM_MAXD];
     for (int d = 0; d < K.D; ++d) xd[d] = x[(size_t)d * P + p];
@@ -320,7 +281,8 @@ size_t adjoint_ckpt_floats(int m, int n_steps, int P) {
 }
 
 cudaError_t launch_adjoint(const KConst<float>& K, const float* x, int P, const float* U, float* S,
-                           float* G, float* ckpt, cudaStream_t st) {
+                           float* G, float* ckpt, cudaStream_t st, const int64_t* off,
+                           const int* order, int per_slot) {
     const size_t smem = sizeof(float) * ((size_t)((K.spc2 + 1 + 3) & ~3) +
                                          (size_t)SEG * SEGW * ADJ_THREADS);
     const int blocks = (P + ADJ_THREADS - 1) / ADJ_THREADS;
@@ -331,7 +293,7 @@ cudaError_t launch_adjoint(const KConst<float>& K, const float* x, int P, const 
                                                  (int)smem);
             if (e != cudaSuccess) return e;
         }
-        kern<<<blocks, ADJ_THREADS, smem, st>>>(K, x, P, U, S, G, ckpt);
+        kern<<<blocks, ADJ_THREADS, smem, st>>>(K, x, P, U, S, G, ckpt, off, order, per_slot);
         return cudaGetLastError();
     });
 }

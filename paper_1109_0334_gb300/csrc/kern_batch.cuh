@@ -138,6 +138,16 @@ __global__ void __launch_bounds__(1024) batch_kernel(const KConst<float> K, cons
             }
             __syncthreads();
         }
+        if (a.pb_out != nullptr) {   // final personal bests of this slot (own particles only)
+            float* dst = a.pb_out + (size_t)slot * (D + 1) * P;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const int p = tid + k * T;
+                if (p >= P) continue;
+                dst[(size_t)D * P + p] = pbS[k];
+                for (int d = 0; d < D; ++d) dst[(size_t)d * P + p] = spb[d * P + p];
+            }
+        }
         if (tid == 0) {
             const int g = min((int)(s_gkey & 0x7fffffffu), P - 1);
             afm_result* r = a.res + pix;

@@ -1,0 +1,370 @@
+// kern_lm.cu -- Levenberg-Marquardt polish: residual sensitivities by
+// tangent-linear (forward-mode) differentiation of the FP32 RK4 solve, the
+// normal equations of the misfit (Eq. 5), damped Gauss-Newton trial points
+// for a ladder of damping values, and the choice among them.
+//
+// For the misfit S = sum_n r_n^2, r_n = U_n - u_n(x), the sensitivities
+// a_n = du_n/dx (D per step) give H = sum a_n a_n^T (Gauss-Newton matrix,
+// half the Gauss-Newton Hessian) and b = sum a_n r_n = -dS/dx / 2.  The
+// primal solve inside the sensitivity kernel is the forward kernel's
+// arithmetic, so S is bit-identical to afm_forward_batch's.
+#include <type_traits>
+
+#include "afm_device.cuh"
+#include "afm_launch.h"
+
+namespace afm {
+
+namespace {
+
+template <typename F>
+cudaError_t dispatch_mfd(int m, int force, int D, F&& f) {
+    auto byD = [&](auto Mc, auto Fc) -> cudaError_t {
+        if (D <= 2) return f(Mc, Fc, std::integral_constant<int, 2>{});
+        if (D <= 4) return f(Mc, Fc, std::integral_constant<int, 4>{});
+        return f(Mc, Fc, std::integral_constant<int, AFM_MAXD>{});
+    };
+    auto byF = [&](auto Mc) -> cudaError_t {
+        switch (force) {
+            case F_LINEAR: return byD(Mc, std::integral_constant<int, F_LINEAR>{});
+            case F_DMT: return byD(Mc, std::integral_constant<int, F_DMT>{});
+            case F_DMT_KV: return byD(Mc, std::integral_constant<int, F_DMT_KV>{});
+            case F_HOOKE: return byD(Mc, std::integral_constant<int, F_HOOKE>{});
+            case F_SPRING_DAMPER: return byD(Mc, std::integral_constant<int, F_SPRING_DAMPER>{});
+        }
+        return cudaErrorInvalidValue;
+    };
+    if (m == 1) return byF(std::integral_constant<int, 1>{});
+    if (m == 3) return byF(std::integral_constant<int, 3>{});
+    return byF(std::integral_constant<int, AFM_MAXM>{});
+}
+
+constexpr int kThreads = 32;
+constexpr int kFold = 32;   // steps summed in FP32 before folding into FP64 totals
+
+// Tangent of the modal accelerations at one stage: for each direction n,
+// da_i = tip_i dF - wq_i dv_i - w2_i dq_i with dF = F_d sum dq + F_r sum dv +
+// sum_k F_ck dc_k/dx_n.
+template <int M, int FORCE, int ND>
+__device__ __forceinline__ void tl_accel(const KConst<float>& K, const Coef<float>& c,
+                                         const float (&Jc)[4][ND], const float* q, const float* v,
+                                         const float (&tq)[ND][M], const float (&tv)[ND][M],
+                                         float (&ta)[ND][M]) {
+    float u = q[0];
+#pragma unroll
+    for (int i = 1; i < M; ++i) u += q[i];
+    float dd = 0.f;
+    if (UsesRate<FORCE>::value) {
+        dd = v[0];
+#pragma unroll
+        for (int i = 1; i < M; ++i) dd += v[i];
+    }
+    float Fd, Fr, Fc[4];
+    force_partials<FORCE>(c, K.Zc + u, dd, Fd, Fr, Fc);
+#pragma unroll
+    for (int n = 0; n < ND; ++n) {
+        float su = tq[n][0], sv = tv[n][0];
+#pragma unroll
+        for (int i = 1; i < M; ++i) {
+            su += tq[n][i];
+            sv += tv[n][i];
+        }
+        float dF = Fd * su;
+        if (UsesRate<FORCE>::value) dF = fmaf(Fr, sv, dF);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dF = fmaf(Fc[k], Jc[k][n], dF);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const float base = fmaf(-K.wq[i], tv[n][i], -K.w2[i] * tq[n][i]);
+            ta[n][i] = (M <= 4) ? base + dF : fmaf(K.tip[i], dF, base);
+        }
+    }
+}
+
+// One RK4 step of rk4_step (identical primal arithmetic) with the tangents
+// of ND directions carried along.
+template <int M, int FORCE, int ND>
+__device__ __forceinline__ void rk4_step_tl(const KConst<float>& K, const Coef<float>& c,
+                                            const float (&Jc)[4][ND], float* q, float* v,
+                                            float* cq, float* cv, float (&tq)[ND][M],
+                                            float (&tv)[ND][M], float g0, float gh, float g1) {
+    float a[M], qs[M], vs[M], Kq[M], Kv[M];
+    float ta[ND][M], tqs[ND][M], tvs[ND][M], tKq[ND][M], tKv[ND][M];
+    accel<float, M, FORCE>(K, c, q, v, g0, a);
+    tl_accel<M, FORCE, ND>(K, c, Jc, q, v, tq, tv, ta);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        Kq[i] = v[i];
+        Kv[i] = a[i];
+        qs[i] = fmaf(3.f, v[i], q[i]);
+        vs[i] = fmaf(3.f, a[i], v[i]);
+#pragma unroll
+        for (int n = 0; n < ND; ++n) {
+            tKq[n][i] = tv[n][i];
+            tKv[n][i] = ta[n][i];
+            tqs[n][i] = fmaf(3.f, tv[n][i], tq[n][i]);
+            tvs[n][i] = fmaf(3.f, ta[n][i], tv[n][i]);
+        }
+    }
+    accel<float, M, FORCE>(K, c, qs, vs, gh, a);
+    tl_accel<M, FORCE, ND>(K, c, Jc, qs, vs, tqs, tvs, ta);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        Kq[i] = fmaf(2.f, vs[i], Kq[i]);
+        Kv[i] = fmaf(2.f, a[i], Kv[i]);
+        qs[i] = fmaf(3.f, vs[i], q[i]);
+        vs[i] = fmaf(3.f, a[i], v[i]);
+#pragma unroll
+        for (int n = 0; n < ND; ++n) {
+            tKq[n][i] = fmaf(2.f, tvs[n][i], tKq[n][i]);
+            tKv[n][i] = fmaf(2.f, ta[n][i], tKv[n][i]);
+            tqs[n][i] = fmaf(3.f, tvs[n][i], tq[n][i]);
+            tvs[n][i] = fmaf(3.f, ta[n][i], tv[n][i]);
+        }
+    }
+    accel<float, M, FORCE>(K, c, qs, vs, gh, a);
+    tl_accel<M, FORCE, ND>(K, c, Jc, qs, vs, tqs, tvs, ta);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        Kq[i] = fmaf(2.f, vs[i], Kq[i]);
+        Kv[i] = fmaf(2.f, a[i], Kv[i]);
+        qs[i] = fmaf(6.f, vs[i], q[i]);
+        vs[i] = fmaf(6.f, a[i], v[i]);
+#pragma unroll
+        for (int n = 0; n < ND; ++n) {
+            tKq[n][i] = fmaf(2.f, tvs[n][i], tKq[n][i]);
+            tKv[n][i] = fmaf(2.f, ta[n][i], tKv[n][i]);
+            tqs[n][i] = fmaf(6.f, tvs[n][i], tq[n][i]);
+            tvs[n][i] = fmaf(6.f, ta[n][i], tv[n][i]);
+        }
+    }
+    accel<float, M, FORCE>(K, c, qs, vs, g1, a);
+    tl_accel<M, FORCE, ND>(K, c, Jc, qs, vs, tqs, tvs, ta);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        Kq[i] = Kq[i] + vs[i];
+        Kv[i] = Kv[i] + a[i];
+        kahan_add(q[i], cq[i], Kq[i]);
+        kahan_add(v[i], cv[i], Kv[i]);
+#pragma unroll
+        for (int n = 0; n < ND; ++n) {
+            tq[n][i] = tq[n][i] + (tKq[n][i] + tvs[n][i]);
+            tv[n][i] = tv[n][i] + (tKv[n][i] + ta[n][i]);
+        }
+    }
+}
+
+}  // namespace
+
+// Sensitivity pass of one particle per thread: S (as the forward kernel),
+// H [P][D][D] and b [P][D] in FP64.  Ragged form as the adjoint: off !=
+// nullptr gives particle p the record of pixel order[p / per_slot].
+template <int M, int FORCE, int ND>
+__global__ void __launch_bounds__(kThreads) sens_kernel(const KConst<float> K,
+                                                        const float* __restrict__ x, int P,
+                                                        const float* __restrict__ U,
+                                                        const int64_t* __restrict__ off,
+                                                        const int* __restrict__ order,
+                                                        int per_slot, float* __restrict__ S_out,
+                                                        double* __restrict__ H_out,
+                                                        double* __restrict__ b_out) {
+    extern __shared__ __align__(16) float tab[];
+    __shared__ double accH[ND * (ND + 1) / 2][kThreads], accb[ND][kThreads];
+    build_drive_table(K, tab);
+    __syncthreads();
+    const int tid = threadIdx.x;
+    const int p = blockIdx.x * blockDim.x + tid;
+    if (p >= P) return;
+    const int D = K.D;
+    int n = K.n_steps;
+    if (off != nullptr) {
+        const int slot = p / per_slot;
+        const int pix = order != nullptr ? order[slot] : slot;
+        U += off[pix];
+        n = (int)(off[pix + 1] - off[pix]);
+    }
+    float xd[AFM_MAXD];
+    for (int d = 0; d < AFM_MAXD; ++d) xd[d] = d < D ? x[(size_t)d * P + p] : 0.f;
+    const Coef<float> c = make_coef<float, float>(K, xd);
+    float Jc[4][ND];
+    {
+        double Jd[4][AFM_MAXD];
+        coef_jacobian<float>(K, xd, Jd);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int e = 0; e < ND; ++e) Jc[k][e] = e < D ? (float)Jd[k][e] : 0.f;
+    }
+    float q[M], v[M], cq[M], cv[M], tq[ND][M], tv[ND][M];
+    init_state<float, M>(K, q, v, cq, cv);
+#pragma unroll
+    for (int e = 0; e < ND; ++e)
+#pragma unroll
+        for (int i = 0; i < M; ++i) tq[e][i] = tv[e][i] = 0.f;
+#pragma unroll
+    for (int t = 0; t < ND * (ND + 1) / 2; ++t) accH[t][tid] = 0.0;
+#pragma unroll
+    for (int e = 0; e < ND; ++e) accb[e][tid] = 0.0;
+    float hc[ND * (ND + 1) / 2], bc[ND];
+#pragma unroll
+    for (int t = 0; t < ND * (ND + 1) / 2; ++t) hc[t] = 0.f;
+#pragma unroll
+    for (int e = 0; e < ND; ++e) bc[e] = 0.f;
+    float S = 0.f, cS = 0.f;
+    int j = 0, fold = 0;
+    const int spc2 = K.spc2;
+    for (int s = 0; s < n; ++s) {
+        const float g0 = tab[j], gh = tab[j + 1], g1 = tab[j + 2];
+        j += 2;
+        if (j >= spc2) j = 0;
+        rk4_step_tl<M, FORCE, ND>(K, c, Jc, q, v, cq, cv, tq, tv, g0, gh, g1);
+        const float u = tip_sum<float, M>(q);
+        const float r = U[s] - u;
+        const float y = fmaf(r, r, -cS);
+        const float t = add_rn(S, y);
+        cS = sub_rn(sub_rn(t, S), y);
+        S = t;
+        float au[ND];
+#pragma unroll
+        for (int e = 0; e < ND; ++e) au[e] = tip_sum<float, M>(tq[e]);
+        int w = 0;
+#pragma unroll
+        for (int e = 0; e < ND; ++e) {
+            bc[e] = fmaf(au[e], r, bc[e]);
+#pragma unroll
+            for (int f = 0; f <= e; ++f) {
+                hc[w] = fmaf(au[e], au[f], hc[w]);
+                ++w;
+            }
+        }
+        if (++fold == kFold || s + 1 == n) {
+            fold = 0;
+#pragma unroll
+            for (int t2 = 0; t2 < ND * (ND + 1) / 2; ++t2) {
+                accH[t2][tid] += (double)hc[t2];
+                hc[t2] = 0.f;
+            }
+#pragma unroll
+            for (int e = 0; e < ND; ++e) {
+                accb[e][tid] += (double)bc[e];
+                bc[e] = 0.f;
+            }
+        }
+    }
+    if (!(S < INFINITY)) S = INFINITY;
+    S_out[p] = S;
+    double* H = H_out + (size_t)p * D * D;
+    int w = 0;
+    for (int e = 0; e < ND; ++e) {
+        for (int f = 0; f <= e; ++f) {
+            if (e < D) {
+                H[e * D + f] = accH[w][tid];
+                H[f * D + e] = accH[w][tid];
+            }
+            ++w;
+        }
+        if (e < D) b_out[(size_t)p * D + e] = accb[e][tid];
+    }
+}
+
+// Trial points of candidate k: clamp(x + delta_j) with (H + lambda_j W)
+// delta_j = b, lambda_j = lam0 ratio^j, W = diag(max(H_dd, 1e-12 max H_ee)),
+// solved by Cholesky in FP64.  Output column k * J + j of Xc [D][K*J].
+__global__ void lm_cand_kernel(int D, int K, int J, const float* __restrict__ x,
+                               const double* __restrict__ H, const double* __restrict__ b,
+                               double lam0, double ratio, float* __restrict__ Xc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const double* Hk = H + (size_t)k * D * D;
+    double hmax = 0.0;
+    for (int d = 0; d < D; ++d) hmax = fmax(hmax, Hk[d * D + d]);
+    const size_t KJ = (size_t)K * J;
+    double lam = lam0;
+    for (int j = 0; j < J; ++j, lam *= ratio) {
+        double L[AFM_MAXD][AFM_MAXD], y[AFM_MAXD];
+        bool ok = hmax > 0.0;
+        for (int r = 0; r < D && ok; ++r) {
+            for (int c = 0; c <= r; ++c) {
+                double s = Hk[r * D + c];
+                if (r == c) s += lam * fmax(Hk[r * D + r], 1e-12 * hmax);
+                for (int t = 0; t < c; ++t) s -= L[r][t] * L[c][t];
+                if (r == c) {
+                    if (!(s > 0.0)) {
+                        ok = false;
+                        break;
+                    }
+                    L[r][r] = sqrt(s);
+                } else {
+                    L[r][c] = s / L[c][c];
+                }
+            }
+        }
+        if (ok) {
+            for (int r = 0; r < D; ++r) {
+                double s = b[(size_t)k * D + r];
+                for (int t = 0; t < r; ++t) s -= L[r][t] * y[t];
+                y[r] = s / L[r][r];
+            }
+            for (int r = D - 1; r >= 0; --r) {
+                double s = y[r];
+                for (int t = r + 1; t < D; ++t) s -= L[t][r] * y[t];
+                y[r] = s / L[r][r];
+            }
+        }
+        for (int d = 0; d < D; ++d) {
+            double xn = (double)x[(size_t)d * K + k] + (ok ? y[d] : 0.0);
+            if (!(xn > 0.0)) xn = 0.0;
+            if (xn > 1.0) xn = 1.0;
+            Xc[(size_t)d * KJ + (size_t)k * J + j] = (float)xn;
+        }
+    }
+}
+
+// The trial point of least misfit (first on ties) replaces x if it lowers S.
+__global__ void lm_select_kernel(int D, int K, int J, float* __restrict__ x, float* __restrict__ S,
+                                 const float* __restrict__ Xc, const float* __restrict__ Sc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int jb = 0;
+    for (int j = 1; j < J; ++j)
+        if (Sc[(size_t)k * J + j] < Sc[(size_t)k * J + jb]) jb = j;
+    const float Sj = Sc[(size_t)k * J + jb];
+    if (Sj < S[k]) {
+        const size_t KJ = (size_t)K * J;
+        for (int d = 0; d < D; ++d) x[(size_t)d * K + k] = Xc[(size_t)d * KJ + (size_t)k * J + jb];
+        S[k] = Sj;
+    }
+}
+
+cudaError_t launch_sens(const KConst<float>& K, const float* x, int P, const float* U, float* S,
+                        double* H, double* b, cudaStream_t st, const int64_t* off, const int* order,
+                        int per_slot) {
+    const int blocks = (P + kThreads - 1) / kThreads;
+    const size_t smem = sizeof(float) * (size_t)(K.spc2 + 1);
+    return dispatch_mfd(K.m, K.force, K.D, [&](auto Mc, auto Fc, auto Dc) -> cudaError_t {
+        auto kern = sens_kernel<decltype(Mc)::value, decltype(Fc)::value, decltype(Dc)::value>;
+        if (smem > 24 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<blocks, kThreads, smem, st>>>(K, x, P, U, off, order, per_slot, S, H, b);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_lm_cand(int D, int K, int J, const float* x, const double* H, const double* b,
+                           double lam0, double ratio, float* Xc, cudaStream_t st) {
+    const int threads = 64;
+    lm_cand_kernel<<<(K + threads - 1) / threads, threads, 0, st>>>(D, K, J, x, H, b, lam0, ratio, Xc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lm_select(int D, int K, int J, float* x, float* S, const float* Xc,
+                             const float* Sc, cudaStream_t st) {
+    const int threads = 64;
+    lm_select_kernel<<<(K + threads - 1) / threads, threads, 0, st>>>(D, K, J, x, S, Xc, Sc);
+    return cudaGetLastError();
+}
+
+}  // namespace afm

@@ -42,12 +42,17 @@ WORKLOADS = {
     "c3": dict(name="4096 pixels, 3-mode EB DMT, 256 particles x 60 updates",
                model="modal_eb", n_modes=3, spc=256, cycles=(20, 200), force="dmt",
                free=[_E, _H, _R, _A0], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
-               P=256, iters=60, n_pix=4096, seed=SEED_BASE + 3, **_CANTILEVER, **_PSO),
+               P=256, iters=60, n_pix=4096, seed=SEED_BASE + 3,
+               # the same pixels by a short swarm and Levenberg-Marquardt polish
+               # of each pixel's best particles
+               lm_polish=dict(iters=5, polish_k=8, polish_steps=12, n_cand=8),
+               **_CANTILEVER, **_PSO),
     # DMT + Kelvin-Voigt contact damping, adjoint-polished.
     "c4": dict(name="3-mode EB DMT+KV, 5 unknowns, 1024 x 40 + 20 polish on 32",
                model="modal_eb", n_modes=3, spc=256, cycles=100, force="dmt_kv",
                free=[_E, _H, _R, _A0, _ETA], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
                P=1024, iters=40, polish_k=32, polish_steps=20, seed=SEED_BASE + 4,
+               lm_polish=dict(iters=10, polish_k=8, polish_steps=8, n_cand=8),
                **_CANTILEVER, **_PSO),
     # 32-element Hermite FE beam, Newmark beta = 1/4.
     "c5": dict(name="FE Hermite 32 elements DMT, 4 unknowns, 8192 particles x 60 updates",
