@@ -118,6 +118,7 @@ def measured_peaks() -> dict:
 
 KERNEL_SOURCES = {
     "invert_iter_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_invert.cu"],
+    "invert_pair_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_pair.cu"],
     "fwd_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_forward.cu"],
     "batch_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_batch.cuh",
                      "kern_batch.cu", "kern_batch_dmt.cu"],
@@ -584,8 +585,8 @@ def run_ours(args):
     achieved = ops_launch / avg_launch_s
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
             "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
-            "traffic": ncu_traffic("invert_iter_kernel", args.workload),
-            "kernel": "invert_iter_kernel<3,DMT>",
+            "traffic": ncu_traffic("invert_pair_kernel", args.workload),
+            "kernel": "invert_pair_kernel<3,DMT> (two lanes per particle)",
             "ops_per_particle_step": fp32_ops_per_step(m, spec["force"]),
             "launches_timed": kern_n, "avg_launch_ms": avg_launch_s * 1e3,
             "kernel_share_of_step": kern_ms / sum(step_ms),
@@ -747,6 +748,20 @@ def run_probe(args):
         torch.cuda.synchronize()
         print(json.dumps({"S_mean": float(S.mean()), "G_absmax": float(G.abs().max())}))
         return
+    if args.probe == "polish":
+        # one pixel wave of the LM-polished batch (records shortened tenfold)
+        props = torch.cuda.get_device_properties(0)
+        spec, prob, U, off, total, _ = c3_inputs(A, W, torch.device("cuda"),
+                                                 n_pix=props.multi_processor_count * 4,
+                                                 cycles_div=10)
+        lp = spec["lm_polish"]
+        cfg = A.make_pso(dict(spec, iters=lp["iters"]))
+        res, kp = A.invert_batch_polished(prob, U, off, cfg, lp["polish_k"], 2, lp["n_cand"],
+                                          method="lm")
+        torch.cuda.synchronize()
+        out = A.decode_results(res)
+        print(json.dumps({"pixels": len(out), "kp": kp, "ok": sum(r["status"] == 0 for r in out)}))
+        return
     spec = W.get(args.workload, iters=args.probe_iters)
     D = len(spec["free"])
     N = W.n_steps(spec)
@@ -759,6 +774,14 @@ def run_probe(args):
         torch.cuda.synchronize()
         print(json.dumps({k: (v.tolist() if hasattr(v, "tolist") else v)
                           for k, v in A.decode_result(res).items()}))
+    elif args.probe == "sens":
+        # normal equations of --probe-particles candidates (throughput regime)
+        g = torch.Generator(device="cuda").manual_seed(7)
+        x = torch.rand((D, args.probe_particles), dtype=torch.float32, device="cuda", generator=g)
+        for _ in range(2):
+            S, H, b = A.normal_equations(prob, x, U)
+        torch.cuda.synchronize()
+        print(json.dumps({"particles": args.probe_particles, "S_mean": float(S.mean())}))
     else:
         g = torch.Generator(device="cuda").manual_seed(7)
         x = torch.rand((D, args.probe_particles), dtype=torch.float32, device="cuda", generator=g)
@@ -780,7 +803,8 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the 4096-pixel batched inversion")
     ap.add_argument("--no-c4", action="store_true", help="skip the polished-inversion comparison")
     ap.add_argument("--no-c5", action="store_true", help="skip the finite-element inversion")
-    ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint", "fe"], default=None,
+    ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint", "fe", "sens", "polish"],
+                    default=None,
                     help="run one small untimed case for a profiler capture and exit")
     ap.add_argument("--probe-iters", type=int, default=2)
     ap.add_argument("--probe-particles", type=int, default=32768)

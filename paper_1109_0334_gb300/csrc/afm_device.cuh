@@ -272,7 +272,9 @@ __device__ __forceinline__ void accel(const KConst<T>& K, const Coef<T>& c, cons
         T ai = fma(-K.wq[i], v[i], K.gam[i] * g);
         if (i == 0) ai = fma(-K.w2lo[0], q[0], ai);
         ai = fma(-K.w2[i], q[i], ai);
-        a[i] = (M <= 4) ? ai + F : fma(K.tip[i], F, ai);
+        // add_rn: no contraction with a product inside F (laws whose force
+        // ends in a product), so every kernel rounds this sum the same way
+        a[i] = (M <= 4) ? add_rn(ai, F) : fma(K.tip[i], F, ai);
     }
 }
 

@@ -122,6 +122,11 @@ cudaError_t launch_pso_move(const PsoConst& pc, const SwarmPtrs& sw, int it, cud
 // fused inversion iteration (it = 0: initial evaluation)
 cudaError_t launch_invert_iter(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
                                const float* U, float* history, int it, cudaStream_t st);
+// the same iteration with two lanes per particle (rate-free laws, 1 or 3
+// modes, P <= 9728); launch_invert_iter selects it by itself
+bool pair_supported(int m, int force, int P);
+cudaError_t launch_invert_pair(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
+                               const float* U, float* history, int it, cudaStream_t st);
 // winner re-evaluation in FP64 and result record
 cudaError_t launch_invert_final(const KConst<double>& K, const PsoConst& pc, const SwarmPtrs& sw,
                                 const float* U, float* history, void* result, cudaStream_t st);

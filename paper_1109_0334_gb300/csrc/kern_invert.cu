@@ -193,6 +193,8 @@ __global__ void invert_iter_kernel(const KConst<float> K, const PsoConst pc, Swa
 
 cudaError_t launch_invert_iter(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
                                const float* U, float* history, int it, cudaStream_t st) {
+    // small swarms of rate-free force laws: two lanes per particle (kern_pair.cu)
+    if (pair_supported(K.m, K.force, pc.P)) return launch_invert_pair(K, pc, sw, U, history, it, st);
     const int threads = pc.P <= 152 * 32 * 4 ? 32 : 128;
     const int blocks = (pc.P + threads - 1) / threads;
     const size_t smem = sizeof(float) * (size_t)(K.spc2 + 1);

@@ -133,3 +133,30 @@ def test_invert_c2_full_size_parity(orc, afm):
     assert abs(float(np.sum(U_m ** 2)) / gold["sumU2_m2"] - 1) < 1e-9
     r, hist = _gpu_invert(afm, spec, U32)
     _check_inversion(orc, spec, U_m, r, np.array(gold["x"]), gold["S_m2"], hist)
+
+
+@pytest.mark.parametrize("name,over", [
+    ("c2", dict(cycles=12)),
+    ("c1", dict(cycles=12)),
+    ("c2", dict(cycles=12, force="linear_spring", fixed=[0.0] * 5,
+                free=[(0, 2.0, 20.0, False), (1, 10e-9, 20e-9, False)])),
+    ("c2", dict(cycles=12, force="hooke", fixed=[0.0] * 5,
+                free=[(0, 0.5, 8.0, True), (1, -2e-9, 4e-9, False)])),
+])
+def test_two_lane_iteration_is_bit_identical(orc, afm, name, over):
+    """Small swarms of rate-free laws run two lanes per particle (stage
+    forces split between the lanes); the result must be bit-identical to the
+    one-lane arithmetic of the batched-pixel kernel on the same pixel."""
+    spec = W.get(name, P=77, iters=6, **over)
+    U32, _, _ = oracle_record(orc, spec)
+    prob = afm.make_problem(spec)
+    cfg = afm.make_pso(spec)
+    Ut = torch.from_numpy(U32).cuda()
+    r1, h1 = afm.invert(prob, Ut, cfg)
+    off = torch.tensor([0, len(U32)], dtype=torch.int64, device="cuda")
+    rb, _ = afm.invert_batch(prob, Ut, off, cfg, particles_per_thread=1)
+    torch.cuda.synchronize()
+    a, b = afm.decode_result(r1), afm.decode_results(rb)[0]
+    assert a["winner"] == b["winner"] and a["S"] == b["S"]
+    np.testing.assert_array_equal(a["x"], b["x"])
+    assert np.all(np.diff(h1.cpu().numpy()) <= 0)
