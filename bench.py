@@ -151,18 +151,24 @@ def ncu_traffic(kernel: str, workload: str):
 # ---------------------------------------------------------------------------
 # Distributed plumbing
 # ---------------------------------------------------------------------------
-def dist_setup():
+def dist_setup(backend: str | None = None):
+    """Rank, world size and local rank from the torchrun environment; joins the
+    process group for N > 1 (NCCL on GPUs, gloo where none is visible)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if backend is None:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        if torch.cuda.is_available():
-            torch.cuda.set_device(0)
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
     return rank, world, local
 
 
@@ -173,13 +179,30 @@ def barrier(world):
 
 
 def all_max(val: float, world: int) -> float:
+    """Maximum of a per-rank value over all ranks (the job's wall time is the
+    slowest rank's)."""
     if world == 1:
         return val
     import torch
     import torch.distributed as dist
-    t = torch.tensor([val], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([val], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_slice(n: int, rank: int, world: int):
+    """Contiguous share [lo, hi) of n independent units (pixels) for a rank;
+    the shares partition range(n) and differ in size by at most one."""
+    q, r = divmod(n, world)
+    lo = rank * q + min(rank, r)
+    return lo, lo + q + (1 if rank < r else 0)
+
+
+def job_rate(units_per_rank: float, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job throughput under weak scaling: every rank processes
+    units_per_rank per step; the job takes the slowest rank's time."""
+    return world * units_per_rank * steps / (max_ms / 1e3)
 
 
 # ---------------------------------------------------------------------------
@@ -549,7 +572,7 @@ def run_ours(args):
     r = A.decode_result(res)
 
     units = P * (iters + 1) * N
-    value = world * units * args.steps / (T_ms / 1e3)
+    value = job_rate(units, args.steps, T_ms, world)
 
     # end to end through the public API with host buffers
     res_host = torch.empty_like(res, device="cpu").pin_memory()
@@ -570,7 +593,7 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     E_ms = all_max(sum(e2e_ms), world)
-    e2e = {"value": world * units * args.steps / (E_ms / 1e3), "unit": UNIT,
+    e2e = {"value": job_rate(units, args.steps, E_ms, world), "unit": UNIT,
            "h2d_bytes_per_step": int(U.numel() * 4),
            "d2h_bytes_per_step": int(res.numel() + hist.numel() * 4),
            "ms_per_inversion": E_ms / args.steps}
