@@ -504,6 +504,40 @@ def run_c5(A, W, dev, peak_ops, flush, iters=None):
 
 
 # ---------------------------------------------------------------------------
+# The paper's own tip-sample experiments (App. A cantilever, 8 modes)
+# ---------------------------------------------------------------------------
+def run_paper_laws(A, W, dev, flush):
+    """Hooke contact (k, h) and spring-damper (k, zeta_s) inversions with the
+    paper's truth values; records made on the GPU at dt/4 plus noise."""
+    import torch
+    out = {}
+    for name in ("f2_hooke", "f2_spring_damper"):
+        spec = W.get(name)
+        N = W.n_steps(spec)
+        prob = A.make_problem(spec)
+        xt = torch.tensor(spec["x_truth"], dtype=torch.float64, device=dev).reshape(-1, 1)
+        off = torch.tensor([0, N], dtype=torch.int64, device=dev)
+        U = A.synth_records(prob, xt, off, spec["record_sub"], spec["sigma"], spec["seed"], 0)
+        cfg = A.make_pso(spec)
+        A.invert(prob, U, cfg)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res, _ = A.invert(prob, U, cfg)
+        e1.record()
+        e1.synchronize()
+        r = A.decode_result(res)
+        th_t = _theta_of(spec, spec["x_truth"])
+        slots = [f[0] for f in spec["free"]]
+        out[name] = {"workload": spec["name"], "ms_per_inversion": e0.elapsed_time(e1),
+                     "record_steps": N, "theta_free": [r["theta"][s] for s in slots],
+                     "theta_truth": [th_t[s] for s in slots], "S_f64_nm2": r["S_f64"],
+                     "J_rel": r["J_rel"], "status": r["status"]}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -648,6 +682,10 @@ def run_ours(args):
     if not args.no_c5:
         c5 = run_c5(A, W, dev, peak_ops, flush)
 
+    f2 = None
+    if not args.no_f2:
+        f2 = run_paper_laws(A, W, dev, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, threads, desc, _ = oracle_sample(spec)
@@ -678,6 +716,7 @@ def run_ours(args):
             "batched_inversion": c3,
             "polished_inversion": c4,
             "fe_inversion": c5,
+            "paper_force_laws": f2,
         }
         print(json.dumps(out))
     if world > 1:
@@ -826,6 +865,7 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the 4096-pixel batched inversion")
     ap.add_argument("--no-c4", action="store_true", help="skip the polished-inversion comparison")
     ap.add_argument("--no-c5", action="store_true", help="skip the finite-element inversion")
+    ap.add_argument("--no-f2", action="store_true", help="skip the paper's Hooke / spring-damper inversions")
     ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint", "fe", "sens", "polish"],
                     default=None,
                     help="run one small untimed case for a profiler capture and exit")

@@ -134,7 +134,8 @@ typedef struct {
     int32_t nonfinite;              /* count of non-finite misfits seen           */
     int32_t status;                 /* afm_status of the device-side run          */
     /* How S_f64 was computed.  segments > 0: by multiple shooting over that
-     * many time segments (afm_invert, afm_invert_polished with 1 or 3 modes);
+     * many time segments (afm_invert, afm_invert_polished; modal models,
+     * records of 64 steps or more);
      * defect is then the sum over the segment joins of the max-norm mismatch
      * between one segment's FP64 end state and the next one's start [scaled
      * state units: nm and nm per tau], at most 1e-9.  segments = 0: one

@@ -50,6 +50,7 @@ cudaError_t dispatch_m13(int m, int force, F&& f) {
     };
     if (m == 1) return byF(std::integral_constant<int, 1>{});
     if (m == 3) return byF(std::integral_constant<int, 3>{});
+    if (m >= 1 && m <= AFM_MAXM) return byF(std::integral_constant<int, AFM_MAXM>{});
     return cudaErrorInvalidValue;
 }
 
@@ -74,7 +75,7 @@ __device__ __forceinline__ void accel64(const KConst<double>& K, const Coef<doub
     for (int i = 0; i < M; ++i) {
         double ai = fma(-K.wq[i], v[i], K.gam[i] * g);
         ai = fma(-K.w2[i], q[i], ai);
-        a[i] = ai + F;
+        a[i] = (M <= 4) ? ai + F : fma(K.tip[i], F, ai);   // tip 0: padding modes
     }
 }
 
@@ -132,8 +133,9 @@ __device__ __forceinline__ void step64(const KConst<double>& K, const Coef<doubl
 
 // Linearised stage: da = dA/d(q, v) . (dq, dv) with the recorded slopes.
 template <int M, int FORCE>
-__device__ __forceinline__ void jvp_stage(const float* w2, const float* wq, const float* rec,
-                                          int st, const float* dq, const float* dv, float* da) {
+__device__ __forceinline__ void jvp_stage(const float* w2, const float* wq, const float* tip,
+                                          const float* rec, int st, const float* dq,
+                                          const float* dv, float* da) {
     float su = dq[0];
 #pragma unroll
     for (int i = 1; i < M; ++i) su += dq[i];
@@ -145,16 +147,19 @@ __device__ __forceinline__ void jvp_stage(const float* w2, const float* wq, cons
         dF = fmaf(rec[(2 * st + 1) * 32], sv, dF);
     }
 #pragma unroll
-    for (int i = 0; i < M; ++i) da[i] = fmaf(-wq[i], dv[i], fmaf(-w2[i], dq[i], dF));
+    for (int i = 0; i < M; ++i) {
+        const float base = fmaf(-wq[i], dv[i], -w2[i] * dq[i]);
+        da[i] = (M <= 4) ? base + dF : fmaf(tip[i], dF, base);
+    }
 }
 
 // The RK4 step of step64 linearised about its recorded stages, applied to one
 // tangent direction (dq, dv) in place.
 template <int M, int FORCE>
-__device__ __forceinline__ void jvp_step(const float* w2, const float* wq, const float* rec,
-                                         float* dq, float* dv) {
+__device__ __forceinline__ void jvp_step(const float* w2, const float* wq, const float* tip,
+                                         const float* rec, float* dq, float* dv) {
     float a[M], qs[M], vs[M], Kq[M], Kv[M];
-    jvp_stage<M, FORCE>(w2, wq, rec, 0, dq, dv, a);
+    jvp_stage<M, FORCE>(w2, wq, tip, rec, 0, dq, dv, a);
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         Kq[i] = dv[i];
@@ -162,7 +167,7 @@ __device__ __forceinline__ void jvp_step(const float* w2, const float* wq, const
         qs[i] = fmaf(3.f, dv[i], dq[i]);
         vs[i] = fmaf(3.f, a[i], dv[i]);
     }
-    jvp_stage<M, FORCE>(w2, wq, rec, 1, qs, vs, a);
+    jvp_stage<M, FORCE>(w2, wq, tip, rec, 1, qs, vs, a);
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         Kq[i] = fmaf(2.f, vs[i], Kq[i]);
@@ -170,7 +175,7 @@ __device__ __forceinline__ void jvp_step(const float* w2, const float* wq, const
         qs[i] = fmaf(3.f, vs[i], dq[i]);
         vs[i] = fmaf(3.f, a[i], dv[i]);
     }
-    jvp_stage<M, FORCE>(w2, wq, rec, 2, qs, vs, a);
+    jvp_stage<M, FORCE>(w2, wq, tip, rec, 2, qs, vs, a);
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         Kq[i] = fmaf(2.f, vs[i], Kq[i]);
@@ -178,7 +183,7 @@ __device__ __forceinline__ void jvp_step(const float* w2, const float* wq, const
         qs[i] = fmaf(6.f, vs[i], dq[i]);
         vs[i] = fmaf(6.f, a[i], dv[i]);
     }
-    jvp_stage<M, FORCE>(w2, wq, rec, 3, qs, vs, a);
+    jvp_stage<M, FORCE>(w2, wq, tip, rec, 3, qs, vs, a);
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         dq[i] = dq[i] + (Kq[i] + vs[i]);
@@ -332,11 +337,12 @@ __global__ void __launch_bounds__(32) reeval_pass_kernel(const KConst<double> K,
     }
     R.Sb[b] = S;
     if (TANGENT) {
-        float w2[M], wq[M];
+        float w2[M], wq[M], tip[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             w2[i] = (float)K.w2[i];
             wq[i] = (float)K.wq[i];
+            tip[i] = (float)K.tip[i];
         }
         const int ns = n1 - n0;
 #pragma unroll 1
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(32) reeval_pass_kernel(const KConst<double> K,
                 dq[i] = col == i ? 1.f : 0.f;
                 dv[i] = col == M + i ? 1.f : 0.f;
             }
-            for (int t = 0; t < ns; ++t) jvp_step<M, FORCE>(w2, wq, rec + lane + t * kRec * 32, dq, dv);
+            for (int t = 0; t < ns; ++t) jvp_step<M, FORCE>(w2, wq, tip, rec + lane + t * kRec * 32, dq, dv);
             double* Jc = R.J + (size_t)b * S2 * S2 + col;
 #pragma unroll
             for (int i = 0; i < M; ++i) {
@@ -475,20 +481,23 @@ __global__ void __launch_bounds__(256) reeval_final_kernel(const KConst<double> 
 // Host side
 // ---------------------------------------------------------------------------
 bool reeval_supported(int m, int n_steps) {
-    return (m == 1 || m == 3) && n_steps >= 2 * AFM_SEG;
+    return m >= 1 && m <= AFM_MAXM && n_steps >= 2 * AFM_SEG;
 }
+
+// State components of the kernels' template mode count for m modes.
+static int reeval_modes(int m) { return (m == 1 || m == 3) ? m : AFM_MAXM; }
 
 static int reeval_segments(int n_steps) { return (n_steps + AFM_SEG - 1) / AFM_SEG; }
 
 size_t reeval_bytes(int m, int n_steps, int spc) {
-    const size_t B = (size_t)reeval_segments(n_steps), S2 = 2 * (size_t)m;
+    const size_t B = (size_t)reeval_segments(n_steps), S2 = 2 * (size_t)reeval_modes(m);
     return a256(sizeof(ReevalWinner)) + a256(sizeof(double) * (2 * (size_t)spc + 1)) +
            2 * a256(sizeof(double) * (B + 1) * S2) + a256(sizeof(double) * B * S2) +
            a256(sizeof(double) * B * S2 * S2) + a256(sizeof(double) * B) + 256;
 }
 
 void reeval_carve(void* base, int m, int n_steps, int spc, ReevalPtrs* R) {
-    const size_t B = (size_t)reeval_segments(n_steps), S2 = 2 * (size_t)m;
+    const size_t B = (size_t)reeval_segments(n_steps), S2 = 2 * (size_t)reeval_modes(m);
     char* p = static_cast<char*>(base);
     R->win = reinterpret_cast<ReevalWinner*>(p);
     p += a256(sizeof(ReevalWinner));

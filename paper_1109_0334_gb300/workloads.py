@@ -1,5 +1,6 @@
-"""Seeded synthetic workloads: the five cantilever / force / swarm
-configurations the library is exercised on, as plain SI values.
+"""Seeded synthetic workloads: the cantilever / force / swarm configurations
+the library is exercised on (C1-C5 and the paper's own tip-sample
+experiments), as plain SI values.
 
 This module holds inputs only (physical constants, bounds, swarm sizes,
 seeds, and a seeded sampler for swarm coordinates).  It contains none of the
@@ -18,7 +19,6 @@ import numpy as np
 SEED_BASE = 1109033400
 
 _CANTILEVER = dict(f1_hz=300e3, k=40.0, Q=400.0, A0=20e-9, Zc=16e-9)
-_NOISE = 0.005 * 20e-9          # 0.5 % of A0
 _PSO = dict(w=0.7, c1=1.5, c2=1.5)
 
 _E = (0, 1e8, 1e10, True)       # E* in [0.1, 10] GPa, log
@@ -61,8 +61,30 @@ WORKLOADS = {
                free=[_E, _H, _R, _A0], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
                P=8192, iters=60, seed=SEED_BASE + 5, **_CANTILEVER, **_PSO),
 }
+# The paper's own tip-sample experiments (Sec. 4.2, 4.3) on its App. A
+# cantilever (L = 525 um, 35 x 5 um silicon, mu = 4.0775e-7 kg/m): first
+# natural frequency 25 468.9 Hz (printed in App. A), mode-1 modal stiffness
+# omega_1^2 mu L / 4 = 1.3705 N/m, 8 modes.  Set-point: the sample 50 nm from
+# the neutral axis (the paper's h), free amplitude 60 nm.  Truths are the
+# paper's (normalised in x_truth), not drawn.
+_APPA = dict(f1_hz=25468.9, k=1.3705, Q=400.0, A0=60e-9, Zc=50e-9)
+_KS = (0, 0.0, 25.0, False)            # sample stiffness [N/m], linear
+_HD = (1, -10e-9, 10e-9, False)        # contact datum: separation 50 nm - c1
+_ZS = (2, 0.0, 2e-6, False)            # sample damping [N s/m], linear
+WORKLOADS["f2_hooke"] = dict(
+    name="App. A cantilever, 8 modes, Hooke contact (k, h), 512 particles x 30 updates",
+    model="modal_eb", n_modes=8, spc=512, cycles=8, force="hooke",
+    free=[_KS, _HD], fixed=[0.0, 0.0, 0.0, 0.0, 0.0], x_truth=[4.0 / 25.0, 0.5],
+    rel_scale=[None, 50e-9],           # datum errors relative to the 50 nm separation
+    P=512, iters=30, seed=SEED_BASE + 6, **_APPA, **_PSO)
+WORKLOADS["f2_spring_damper"] = dict(
+    name="App. A cantilever, 8 modes, spring-damper contact (k, zeta_s), 512 x 30",
+    model="modal_eb", n_modes=8, spc=512, cycles=8, force="spring_damper",
+    free=[_KS, _ZS], fixed=[0.0, 0.0, 0.0, 0.0, 0.0], x_truth=[4.0 / 25.0, 0.05],
+    P=512, iters=30, seed=SEED_BASE + 7, **_APPA, **_PSO)
+
 for _w in WORKLOADS.values():
-    _w["sigma"] = _NOISE
+    _w["sigma"] = 0.005 * _w["A0"]    # 0.5 % of the free amplitude
     _w["record_sub"] = 4
 
 

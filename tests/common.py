@@ -68,12 +68,23 @@ def hessian_x(orc, c, pm, U_m, x0, h=1e-3):
     return H
 
 
+def _rel_scale(spec, d):
+    """Fixed scale for relative errors of free dimension d (workload key
+    rel_scale), or None: relative to the parameter's own value."""
+    rs = spec.get("rel_scale")
+    return None if rs is None else rs[d]
+
+
 def log_jacobian(spec, x):
-    """d ln(theta_d) / d x_d for each free dimension at x."""
+    """d ln(theta_d) / d x_d for each free dimension at x (for a dimension
+    with a fixed relative scale s: d (theta_d / s) / d x_d)."""
     J = np.empty(len(spec["free"]))
     for d, (slot, lo, hi, lg) in enumerate(spec["free"]):
+        sc = _rel_scale(spec, d)
         if lg:
             J[d] = math.log(10.0) * (math.log10(hi) - math.log10(lo))
+        elif sc is not None:
+            J[d] = (hi - lo) / sc
         else:
             th = lo + x[d] * (hi - lo)
             J[d] = (hi - lo) / th if th > 0 else np.inf
@@ -97,7 +108,8 @@ def identifiable_check(orc, spec, U_m, x_ref, S_ref, x_test, rel_param=0.005):
     ident = widths <= rel_param
     th_ref = orc.map_x(pm, x_ref)
     th_t = orc.map_x(pm, x_test)
-    drho = np.array([math.log(th_t[s] / th_ref[s]) for (s, *_r) in spec["free"]])
+    drho = np.array([(th_t[s] - th_ref[s]) / _rel_scale(spec, d) if _rel_scale(spec, d) is not None
+                     else math.log(th_t[s] / th_ref[s]) for d, (s, *_r) in enumerate(spec["free"])])
     proj = np.abs(V.T @ drho)
     err = float(proj[ident].max()) if ident.any() else 0.0
     S_t = orc.misfit_batch(c, pm, np.asarray(x_test, dtype=np.float64).reshape(-1, 1), U_m)[0]

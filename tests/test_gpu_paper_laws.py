@@ -1,0 +1,49 @@
+"""The paper's own tip-sample experiments (Sec. 4.2 Hooke contact, Sec. 4.3
+spring-damper) on its App. A cantilever with 8 modes: the GPU inversion
+against the oracle's inversion of the same record (identifiable parameter
+combinations within 0.5 %, misfit within 1e-4, FP64 re-evaluation within
+1e-9), and the paper's truth recovered where the record determines it."""
+import numpy as np
+import pytest
+
+from paper_1109_0334_gb300 import workloads as W
+from common import NM, identifiable_check
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def afm():
+    from paper_1109_0334_gb300 import build
+    build.build()
+    from paper_1109_0334_gb300 import afminv
+    assert torch.cuda.is_available()
+    return afminv
+
+
+@pytest.mark.parametrize("name", ["f2_hooke", "f2_spring_damper"])
+def test_paper_force_law_inversion(orc, afm, name):
+    spec = W.get(name)
+    c, pm = orc.make_case(spec), orc.make_pmap(spec)
+    n = W.n_steps(spec)
+    xt = np.array(spec["x_truth"])
+    U_m = orc.record(c, pm, xt, n, spec["record_sub"], spec["sigma"], spec["seed"], 0)
+    U32 = (U_m / NM).astype(np.float32)
+    U_m = U32.astype(np.float64) * NM
+    x_o, S_o, _ = orc.invert(c, pm, U_m, spec["P"], spec["iters"], spec["w"], spec["c1"],
+                             spec["c2"], spec["seed"])
+    prob = afm.make_problem(spec)
+    res, hist = afm.invert(prob, torch.from_numpy(U32).cuda(), afm.make_pso(spec))
+    torch.cuda.synchronize()
+    r = afm.decode_result(res)
+    D = pm.D
+    err, n_id, S_g, widths = identifiable_check(orc, spec, U_m, x_o, S_o, r["x"][:D])
+    assert r["status"] == 0 and n_id >= 1
+    assert err <= 0.005, (err, widths)
+    assert S_g <= S_o * (1 + 1e-4)
+    assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2
+    assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2
+    # the paper's truth lies within the record's statistical resolution
+    err_t, _, _, _ = identifiable_check(orc, spec, U_m, x_o, S_o, xt)
+    assert err_t <= 0.01

@@ -35,6 +35,9 @@ CASES = [
                 free=[(0, 0.5, 8.0, True), (1, -2e-9, 4e-9, False)])),
     ("c2", dict(P=32, iters=2, cycles=30, force="spring_damper", fixed=[0.0] * 5,
                 free=[(0, 0.5, 8.0, True), (1, -2e-9, 4e-9, False), (2, 0.0, 2e-7, False)])),
+    ("f2_hooke", dict(P=64, iters=3, cycles=4)),
+    ("f2_spring_damper", dict(P=64, iters=3, cycles=4)),
+    ("c2", dict(P=32, iters=2, cycles=20, n_modes=5, spc=512)),
 ]
 
 
@@ -46,7 +49,8 @@ def _invert(afm, spec, U32, n=None):
 
 
 @pytest.mark.parametrize("name,over", CASES, ids=["c1-dmt", "c2-dmt", "c4-kv", "linear", "hooke",
-                                                  "spring-damper"])
+                                                  "spring-damper", "8-modes-hooke",
+                                                  "8-modes-spring-damper", "5-modes-padded"])
 def test_multiple_shooting_matches_oracle_and_sequential(orc, afm, name, over):
     spec = W.get(name, **over)
     U32, U_m, _ = oracle_record(orc, spec)
