@@ -1143,3 +1143,60 @@ int orc_lm_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n,
     free(Sc);
     return rc;
 }
+
+
+/* ======================================================================== */
+/* Swarm inside a box, with seed particles (reading R17: the cross-pixel     */
+/* warm start of image scans).  The swarm of Eq. 8 moves in box-local        */
+/* coordinates y in [0, 1]^D; a particle's parameters are x = lo + y (hi -   */
+/* lo) in the normalised cube.  Particles p < n_seed start at the seed points */
+/* (seeds [n_seed][D], normalised, clamped into the box) with zero velocity;  */
+/* the others start as in orc_pso_init.  best_x is returned in the cube.      */
+/* ======================================================================== */
+int orc_invert_boxed(const orc_case* c, const orc_pmap* pm, const double* U, int n,
+                     const orc_pso* cfg, const double* lo, const double* hi,
+                     const double* seeds, int n_seed, double* best_x, double* best_S)
+{
+    int P = cfg->P, D = pm->D;
+    size_t sz = (size_t)P * D;
+    double* y = (double*)malloc(sizeof(double) * sz);
+    double* v = (double*)malloc(sizeof(double) * sz);
+    double* pb = (double*)malloc(sizeof(double) * sz);
+    double* X = (double*)malloc(sizeof(double) * sz);
+    double* S = (double*)malloc(sizeof(double) * P);
+    double* pbS = (double*)malloc(sizeof(double) * P);
+    if (!y || !v || !pb || !X || !S || !pbS) {
+        free(y); free(v); free(pb); free(X); free(S); free(pbS);
+        return -1;
+    }
+    double gb[5];
+    orc_pso_init(P, D, cfg->seed, cfg->pixel, y, v);
+    for (int p = 0; p < n_seed && p < P; ++p)
+        for (int d = 0; d < D; ++d) {
+            double t = (seeds[(size_t)p * D + d] - lo[d]) / (hi[d] - lo[d]);
+            if (t < 0.0) t = 0.0;
+            if (t > 1.0) t = 1.0;
+            y[(size_t)d * P + p] = t;
+            v[(size_t)d * P + p] = 0.0;
+        }
+    for (int it = 0; it <= cfg->iters; ++it) {
+        if (it > 0)
+            orc_pso_update(P, D, (uint32_t)it, cfg->seed, cfg->pixel, cfg->w, cfg->c1, cfg->c2,
+                           y, v, pb, gb);
+        for (int d = 0; d < D; ++d)
+            for (int p = 0; p < P; ++p)
+                X[(size_t)d * P + p] = lo[d] + y[(size_t)d * P + p] * (hi[d] - lo[d]);
+        orc_misfit_batch(c, pm, X, P, U, n, S);
+        for (int p = 0; p < P; ++p)
+            if (it == 0 || S[p] < pbS[p]) {
+                pbS[p] = S[p];
+                for (int d = 0; d < D; ++d) pb[(size_t)d * P + p] = y[(size_t)d * P + p];
+            }
+        int g = argmin_first(pbS, P);
+        for (int d = 0; d < D; ++d) gb[d] = pb[(size_t)d * P + g];
+        *best_S = pbS[g];
+    }
+    for (int d = 0; d < D; ++d) best_x[d] = lo[d] + gb[d] * (hi[d] - lo[d]);
+    free(y); free(v); free(pb); free(X); free(S); free(pbS);
+    return 0;
+}

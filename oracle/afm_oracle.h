@@ -9,7 +9,7 @@
  * it.  It shares no code, header, table or constant with the CUDA library.
  *
  * Citations name the paper's section / equation.  Readings of passages the
- * paper leaves open are labelled R1..R15 and listed in the repository's
+ * paper leaves open are labelled R1..R17 and listed in the repository's
  * design notes.
  *
  * Parity status per function:
@@ -34,6 +34,9 @@
  *                                  stationarity at an interior optimum)
  *   orc_normal_eq          pinned (central differences of orc_forward; b = -grad/2
  *                                  of orc_grad_cs)
+ *   orc_invert_boxed       pinned (whole-cube box = orc_invert; result inside the box;
+ *                                  an exact seed is kept; a box around the optimum
+ *                                  reaches it with a fraction of the swarm)
  *   orc_lm_polish          pinned (one step to the closed-form least-squares point
  *                                  of a problem affine in its parameter; descent;
  *                                  diagonally scaled gradient for large damping)
@@ -140,6 +143,12 @@ void orc_pso_init(int P, int D, uint64_t seed, uint32_t pixel, double* x, double
 void orc_pso_update(int P, int D, uint32_t it, uint64_t seed, uint32_t pixel,
                     double w, double c1, double c2, double* x, double* v,
                     const double* pbest_x, const double* gbest_x);
+/* The swarm of orc_invert searching the box [lo, hi] (normalised
+ * coordinates, [D] each) with particles p < n_seed started at seeds
+ * [n_seed][D] (reading R17); best_x in the normalised cube. */
+int orc_invert_boxed(const orc_case* c, const orc_pmap* pm, const double* U, int n,
+                     const orc_pso* cfg, const double* lo, const double* hi,
+                     const double* seeds, int n_seed, double* best_x, double* best_S);
 int orc_invert(const orc_case* c, const orc_pmap* pm, const double* U, int n,
                const orc_pso* cfg, double* best_x, double* best_S, double* hist);
 

@@ -118,6 +118,9 @@ def lib():
                                         C.POINTER(C.c_double), _dp, _dp]
             L.orc_lm_polish.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int, _dp,
                                         C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp]
+            L.orc_invert_boxed.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int,
+                                           C.POINTER(Pso), _dp, _dp, _dp, C.c_int, _dp,
+                                           C.POINTER(C.c_double)]
             L.orc_fe_dofs.argtypes = [C.POINTER(Case)]
             L.orc_fe_matrices.argtypes = [C.POINTER(Case), C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p]
@@ -288,6 +291,25 @@ def invert(case: Case, pm: Pmap, U, P: int, iters: int, w: float, c1: float, c2:
     hist = np.zeros(iters + 1)
     lib().orc_invert(C.byref(case), C.byref(pm), U, len(U), C.byref(cfg), bx, C.byref(bS), hist)
     return bx, bS.value, hist
+
+
+def invert_boxed(case: Case, pm: Pmap, U, P: int, iters: int, w: float, c1: float, c2: float,
+                 seed: int, lo, hi, seeds=None, pixel: int = 0):
+    """The swarm searching the box [lo, hi] with seed particles [n_seed][D]
+    (reading R17); returns (best x in the cube, best S)."""
+    cfg = Pso(P=P, iters=iters, w=w, c1=c1, c2=c2, seed=seed, pixel=pixel)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    sd = np.zeros((0, pm.D)) if seeds is None else np.asarray(seeds, dtype=np.float64)
+    sd = np.ascontiguousarray(sd.reshape(-1, pm.D))
+    bx = np.zeros(pm.D)
+    bS = C.c_double()
+    rc = lib().orc_invert_boxed(C.byref(case), C.byref(pm), U, len(U), C.byref(cfg),
+                                np.ascontiguousarray(lo, dtype=np.float64),
+                                np.ascontiguousarray(hi, dtype=np.float64),
+                                sd if len(sd) else np.zeros(pm.D), len(sd), bx, C.byref(bS))
+    if rc:
+        raise ValueError("orc_invert_boxed failed")
+    return bx, bS.value
 
 
 def truth_x(D: int, seed: int, pixel: int = 0) -> np.ndarray:

@@ -565,6 +565,42 @@ def test_polish_descends_to_a_stationary_point(orc):
 
 
 # --------------------------------------------------------------------------
+# Swarm in a box with seed particles (reading R17)
+# --------------------------------------------------------------------------
+def test_boxed_swarm_special_cases(orc, c1_problem):
+    """Whole-cube box without seeds is the plain swarm (same Philox streams,
+    same arithmetic); the result always lies in the box; a seed at the exact
+    optimum of noise-free data is kept."""
+    w, c, pm, n, _, U = c1_problem
+    P, it = 32, 8
+    x0, S0, _ = orc.invert(c, pm, U, P, it, w["w"], w["c1"], w["c2"], w["seed"])
+    xb, Sb = orc.invert_boxed(c, pm, U, P, it, w["w"], w["c1"], w["c2"], w["seed"],
+                              [0.0, 0.0], [1.0, 1.0])
+    assert Sb == S0 and np.array_equal(xb, x0)
+    lo, hi = np.array([0.05, 0.6]), np.array([0.25, 0.9])
+    xb, Sb = orc.invert_boxed(c, pm, U, P, it, w["w"], w["c1"], w["c2"], w["seed"], lo, hi)
+    assert np.all(xb >= lo - 1e-15) and np.all(xb <= hi + 1e-15)
+    # noise-free record made by the solver's own step: the truth has misfit 0
+    xt = np.array([0.37, 0.61])
+    U0 = orc.record(c, pm, xt, n, 1, 0.0, w["seed"])
+    xs, Ss = orc.invert_boxed(c, pm, U0, P, it, w["w"], w["c1"], w["c2"], w["seed"],
+                              [0.3, 0.5], [0.5, 0.7], seeds=xt.reshape(1, 2))
+    S_scale = float(np.sum(U0 ** 2))
+    assert Ss <= 1e-24 * S_scale
+    np.testing.assert_allclose(xs, xt, atol=1e-12)
+
+
+def test_boxed_swarm_reaches_the_optimum_with_a_small_swarm(orc, c1_problem):
+    """A box of +-0.05 around the full swarm's optimum: 16 particles x 10
+    updates reach its misfit (the paper's tighter bounds, fewer generations)."""
+    w, c, pm, n, _, U = c1_problem
+    x0, S0, _ = orc.invert(c, pm, U, w["P"], w["iters"], w["w"], w["c1"], w["c2"], w["seed"])
+    lo, hi = np.clip(x0 - 0.05, 0, 1), np.clip(x0 + 0.05, 0, 1)
+    xb, Sb = orc.invert_boxed(c, pm, U, 16, 10, w["w"], w["c1"], w["c2"], w["seed"], lo, hi)
+    assert Sb <= S0 * (1 + 1e-4)
+
+
+# --------------------------------------------------------------------------
 # Levenberg-Marquardt polish (reading R15)
 # --------------------------------------------------------------------------
 def test_normal_equations_vs_trajectory_differences(orc):
