@@ -504,6 +504,77 @@ def run_c5(A, W, dev, peak_ops, flush, iters=None):
 
 
 # ---------------------------------------------------------------------------
+# Image scan with cross-pixel warm start
+# ---------------------------------------------------------------------------
+def run_image(A, W, dev, flush):
+    """64 x 64 image of smoothly varying truths: every pixel cold (short
+    swarm + LM polish, the polished-batch configuration) against the two-pass
+    warm start (coarse grid cold, the rest inside their neighbours' box);
+    accuracy against the better of the two per pixel."""
+    import numpy as np
+    import torch
+    spec = W.get("f1_image")
+    Wd, Hd = spec["width"], spec["height"]
+    n_pix = Wd * Hd
+    D = len(spec["free"])
+    N = W.n_steps(spec)
+    xt = W.image_truth(D, Wd, Hd, spec["seed"])
+    prob = A.make_problem(spec)
+    off = torch.arange(0, (n_pix + 1) * N, N, dtype=torch.int64, device=dev)
+    U = A.synth_records(prob, torch.from_numpy(xt).to(dev), off, spec["record_sub"], spec["sigma"],
+                        spec["seed"], 0)
+    coarse = A.make_pso(spec)
+    fine = A.make_pso(dict(spec, P=spec["fine"]["P"], iters=spec["fine"]["iters"]))
+    icfg = A.make_image_cfg(Wd, Hd, spec["stride"], spec["margin"], coarse, fine,
+                            coarse_polish=(spec["polish_k"], spec["polish_steps"]),
+                            fine_polish=(spec["fine"]["polish_k"], spec["fine"]["polish_steps"]),
+                            n_cand=spec["n_cand"], method="lm")
+
+    def timed(fn):
+        r = fn()
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1), A.decode_results(r[0] if isinstance(r, tuple) else r)
+
+    ms_cold, cold = timed(lambda: A.invert_batch_polished(prob, U, off, coarse, spec["polish_k"],
+                                                          spec["polish_steps"], spec["n_cand"],
+                                                          method="lm"))
+    ms_warm, warm = timed(lambda: A.invert_image(prob, U, off, icfg))
+    var = (spec["sigma"] / 1e-9) ** 2
+    truth = [_theta_of(spec, xt[:, i]) for i in range(n_pix)]
+
+    def stats(res):
+        dchi, eb, et = [], [], []
+        for i in range(n_pix):
+            best = min((cold[i], warm[i]), key=lambda r: r["S_f64"])
+            dchi.append((res[i]["S_f64"] - best["S_f64"]) / var)
+            eb.append(_comb_err(list(res[i]["theta"]), list(best["theta"])))
+            et.append(_comb_err(list(res[i]["theta"]), truth[i]))
+        dchi, eb, et = map(np.array, (dchi, eb, et))
+        return {"frac_dchi2_le_1": float(np.mean(dchi <= 1.0)),
+                "frac_ident_within_0.5pct": float(np.mean(eb <= 0.005)),
+                "median_ident_err_vs_truth": float(np.median(et))}
+    return {"workload": f"{Wd} x {Hd} image, 3-mode DMT, {spec['cycles']} cycles x {spec['spc']} "
+                        f"steps per pixel, truths smooth over the image",
+            "cold": {"config": f"every pixel: {spec['P']} particles x {spec['iters']} updates + "
+                               f"{spec['polish_steps']} LM steps on the best {spec['polish_k']}",
+                     "ms": ms_cold, "ms_per_pixel": ms_cold / n_pix, **stats(cold)},
+            "warm_start": {"config": f"coarse grid (every {spec['stride']}th row and column) as cold; "
+                                     f"the rest {spec['fine']['P']} particles x {spec['fine']['iters']} "
+                                     f"updates inside the box of the 4 coarse neighbours' winners "
+                                     f"(+-{spec['margin']}), seeded with them, + "
+                                     f"{spec['fine']['polish_steps']} LM steps on the best "
+                                     f"{spec['fine']['polish_k']}",
+                           "ms": ms_warm, "ms_per_pixel": ms_warm / n_pix, **stats(warm)},
+            "speedup": ms_cold / ms_warm}
+
+
+# ---------------------------------------------------------------------------
 # The paper's own tip-sample experiments (App. A cantilever, 8 modes)
 # ---------------------------------------------------------------------------
 def run_paper_laws(A, W, dev, flush):
@@ -685,6 +756,9 @@ def run_ours(args):
     f2 = None
     if not args.no_f2:
         f2 = run_paper_laws(A, W, dev, flush)
+    f1 = None
+    if not args.no_image:
+        f1 = run_image(A, W, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -717,6 +791,7 @@ def run_ours(args):
             "polished_inversion": c4,
             "fe_inversion": c5,
             "paper_force_laws": f2,
+            "image_warm_start": f1,
         }
         print(json.dumps(out))
     if world > 1:
@@ -866,6 +941,7 @@ def main():
     ap.add_argument("--no-c4", action="store_true", help="skip the polished-inversion comparison")
     ap.add_argument("--no-c5", action="store_true", help="skip the finite-element inversion")
     ap.add_argument("--no-f2", action="store_true", help="skip the paper's Hooke / spring-damper inversions")
+    ap.add_argument("--no-image", action="store_true", help="skip the image warm-start comparison")
     ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint", "fe", "sens", "polish"],
                     default=None,
                     help="run one small untimed case for a profiler capture and exit")

@@ -293,6 +293,22 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
                             const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
                             afm_result* results, int* particles_per_thread, void* stream);
 
+/* Optional selection and prior of a polished batch (image scans):
+ * pixels [n_run] (device) lists the pixels to invert, in this order (no
+ * longest-first sorting); box_lo / box_hi [n_run][D] (device, normalised
+ * cube, or both NULL) restrict each listed pixel's swarm to a box, which it
+ * searches in box-local coordinates; seeds [n_run][n_seed][D] (device,
+ * normalised, or NULL with n_seed = 0) start the first n_seed particles,
+ * clamped into the box, at rest.  Unlisted pixels' results are untouched. */
+typedef struct {
+    const int* pixels;
+    int n_run;
+    const float* box_lo;
+    const float* box_hi;
+    const float* seeds;
+    int n_seed;
+} afm_batch_select;
+
 /* ---- many pixel inversions with gradient polish --------------------------
  * afm_invert_batch (same queue, swarms and autotuner; no graph capture), then
  * for every pixel the polish_k personal bests of lowest misfit (lowest index
@@ -303,17 +319,44 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
  * afm_invert_batch.  Per candidate the arithmetic equals afm_invert_polished
  * on that pixel alone.  AFM_POLISH_STEEPEST: prob->n_steps must be >= the
  * longest record, as it sizes the adjoint checkpoints (a longer record keeps
- * its swarm winner).
- * workspace: device, >= afm_invert_batch_polished_workspace_size, 256-aligned. */
+ * its swarm winner).  select (or NULL): a subset of the n_pix pixels and a
+ * prior for each (afm_batch_select).
+ * workspace: device, >= afm_invert_batch_polished_workspace_size(n_run) with
+ * n_run the number of pixels inverted (select->n_run, else n_pix), 256-aligned. */
 afm_status afm_invert_batch_polished_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
-                                                    int n_pix, int polish_k, int n_cand,
+                                                    int n_run, int polish_k, int n_cand,
                                                     int method, size_t* bytes);
 afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
                                      const int64_t* off, int n_pix, uint32_t pixel0,
                                      const afm_pso_cfg* cfg, int polish_k, int polish_steps,
-                                     int n_cand, int method, void* workspace,
-                                     size_t workspace_bytes, afm_result* results,
-                                     int* particles_per_thread, void* stream);
+                                     int n_cand, int method, const afm_batch_select* select,
+                                     void* workspace, size_t workspace_bytes,
+                                     afm_result* results, int* particles_per_thread,
+                                     void* stream);
+
+/* ---- image scans with cross-pixel warm start ------------------------------
+ * A row-major width x height image (pixel id = row * width + column; record
+ * of pixel i at U_cat[off[i] .. off[i+1])) in two polished batches: the
+ * coarse pixels (rows and columns multiple of `stride`) with swarm `coarse`,
+ * then every other pixel with swarm `fine` inside a box spanning the winners
+ * of its (up to 4) surrounding coarse pixels, widened by `margin`
+ * (normalised units), those winners seeding 4 particles.  Philox counter
+ * word 2 of pixel i is pixel0 + i (the cfg's pixel fields are ignored).
+ * results [width * height] (device). */
+typedef struct {
+    int width, height, stride;
+    double margin;
+    afm_pso_cfg coarse, fine;
+    int coarse_polish_k, coarse_polish_steps;
+    int fine_polish_k, fine_polish_steps;
+    int n_cand, method;
+} afm_image_cfg;
+afm_status afm_invert_image_workspace_size(const afm_problem* prob, const afm_image_cfg* icfg,
+                                           size_t* bytes);
+afm_status afm_invert_image(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
+                            const int64_t* off, uint32_t pixel0, const afm_image_cfg* icfg,
+                            void* workspace, size_t workspace_bytes, afm_result* results,
+                            void* stream);
 
 /* ---- inversion without any device allocation ----------------------------
  * The paper has no counterpart: this entry point exists for callers that

@@ -48,6 +48,19 @@ class PsoCfg(C.Structure):
                 ("c2", C.c_double), ("seed", C.c_uint64), ("pixel", C.c_uint32)]
 
 
+class BatchSelect(C.Structure):
+    _fields_ = [("pixels", C.c_void_p), ("n_run", C.c_int), ("box_lo", C.c_void_p),
+                ("box_hi", C.c_void_p), ("seeds", C.c_void_p), ("n_seed", C.c_int)]
+
+
+class ImageCfg(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("stride", C.c_int),
+                ("margin", C.c_double), ("coarse", PsoCfg), ("fine", PsoCfg),
+                ("coarse_polish_k", C.c_int), ("coarse_polish_steps", C.c_int),
+                ("fine_polish_k", C.c_int), ("fine_polish_steps", C.c_int),
+                ("n_cand", C.c_int), ("method", C.c_int)]
+
+
 class Swarm(C.Structure):
     _fields_ = [("P", C.c_int), ("D", C.c_int), ("x", C.c_void_p), ("v", C.c_void_p),
                 ("pbest_x", C.c_void_p), ("pbest_S", C.c_void_p), ("gbest", C.c_void_p)]
@@ -116,8 +129,13 @@ def lib():
             L.afm_invert_batch_polished_workspace_size.argtypes = [
                 C.POINTER(Problem), C.POINTER(PsoCfg), i, i, i, i, C.POINTER(C.c_size_t)]
             L.afm_invert_batch_polished.argtypes = [vp, C.POINTER(Problem), vp, vp, i, u32,
-                                                    C.POINTER(PsoCfg), i, i, i, i, vp, C.c_size_t,
+                                                    C.POINTER(PsoCfg), i, i, i, i,
+                                                    C.POINTER(BatchSelect), vp, C.c_size_t,
                                                     vp, C.POINTER(C.c_int), vp]
+            L.afm_invert_image_workspace_size.argtypes = [C.POINTER(Problem), C.POINTER(ImageCfg),
+                                                          C.POINTER(C.c_size_t)]
+            L.afm_invert_image.argtypes = [vp, C.POINTER(Problem), vp, vp, u32, C.POINTER(ImageCfg),
+                                           vp, C.c_size_t, vp, vp]
             L.afm_invert_noalloc.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), vp,
                                              vp, vp]
             L.afm_synth_records.argtypes = [vp, C.POINTER(Problem), vp, i, vp, i, d, u64, u32,
@@ -483,14 +501,28 @@ def invert_batch_polished_workspace_size(prob: Problem, cfg: PsoCfg, n_pix: int,
 
 def invert_batch_polished(prob: Problem, U_cat, off, cfg: PsoCfg, polish_k: int, polish_steps: int,
                           n_cand: int = 16, pixel0: int = 0, particles_per_thread: int = 0,
-                          workspace=None, results=None, stream=None, method="steepest"):
+                          workspace=None, results=None, stream=None, method="steepest",
+                          pixels=None, box_lo=None, box_hi=None, seeds=None):
     """Many pixel inversions, each followed by the gradient polish of its
     polish_k best particles (afm_invert_batch_polished).  prob.n_steps must
-    bound the record lengths.  Returns (results, particles per thread used)."""
+    bound the record lengths.  Optional selection and prior (CUDA tensors):
+    pixels int32 [n_run], box_lo / box_hi float32 [n_run, D], seeds float32
+    [n_run, n_seed, D].  Returns (results, particles per thread used)."""
     import torch
     dev = U_cat.device
     n_pix = int(off.shape[0]) - 1
-    nbytes = invert_batch_polished_workspace_size(prob, cfg, n_pix, polish_k, n_cand, method)
+    sel = None
+    if pixels is not None:
+        # row-major device arrays, as the C API reads them
+        pixels = pixels.to(torch.int32).contiguous()
+        box_lo = None if box_lo is None else box_lo.to(torch.float32).contiguous()
+        box_hi = None if box_hi is None else box_hi.to(torch.float32).contiguous()
+        seeds = None if seeds is None else seeds.to(torch.float32).contiguous()
+        sel = BatchSelect(pixels=C.c_void_p(pixels.data_ptr()), n_run=int(pixels.numel()),
+                          box_lo=_ptr(box_lo), box_hi=_ptr(box_hi), seeds=_ptr(seeds),
+                          n_seed=0 if seeds is None else int(seeds.shape[1]))
+    n_run = n_pix if sel is None else sel.n_run
+    nbytes = invert_batch_polished_workspace_size(prob, cfg, n_run, polish_k, n_cand, method)
     if workspace is None or workspace.numel() < nbytes:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     if results is None:
@@ -499,10 +531,44 @@ def invert_batch_polished(prob: Problem, U_cat, off, cfg: PsoCfg, polish_k: int,
     _check(lib().afm_invert_batch_polished(context(dev.index), C.byref(prob), _ptr(U_cat), _ptr(off),
                                            n_pix, int(pixel0), C.byref(cfg), int(polish_k),
                                            int(polish_steps), int(n_cand), _method(method),
-                                           _ptr(workspace),
+                                           None if sel is None else C.byref(sel), _ptr(workspace),
                                            C.c_size_t(workspace.numel()), _ptr(results),
                                            C.byref(kp), _stream(stream)))
     return results, kp.value
+
+
+def make_image_cfg(width: int, height: int, stride: int, margin: float, coarse: PsoCfg,
+                   fine: PsoCfg, coarse_polish=(8, 12), fine_polish=(4, 6), n_cand: int = 8,
+                   method="lm") -> ImageCfg:
+    return ImageCfg(width=int(width), height=int(height), stride=int(stride), margin=float(margin),
+                    coarse=coarse, fine=fine, coarse_polish_k=int(coarse_polish[0]),
+                    coarse_polish_steps=int(coarse_polish[1]), fine_polish_k=int(fine_polish[0]),
+                    fine_polish_steps=int(fine_polish[1]), n_cand=int(n_cand),
+                    method=_method(method))
+
+
+def invert_image_workspace_size(prob: Problem, icfg: ImageCfg) -> int:
+    n = C.c_size_t()
+    _check(lib().afm_invert_image_workspace_size(C.byref(prob), C.byref(icfg), C.byref(n)))
+    return int(n.value)
+
+
+def invert_image(prob: Problem, U_cat, off, icfg: ImageCfg, pixel0: int = 0, workspace=None,
+                 results=None, stream=None):
+    """Image scan with cross-pixel warm start (afm_invert_image); returns the
+    results [width * height, sizeof(afm_result)] (uint8, device)."""
+    import torch
+    dev = U_cat.device
+    nbytes = invert_image_workspace_size(prob, icfg)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    if results is None:
+        results = torch.zeros((icfg.width * icfg.height, C.sizeof(Result)), dtype=torch.uint8,
+                              device=dev)
+    _check(lib().afm_invert_image(context(dev.index), C.byref(prob), _ptr(U_cat), _ptr(off),
+                                  int(pixel0), C.byref(icfg), _ptr(workspace),
+                                  C.c_size_t(workspace.numel()), _ptr(results), _stream(stream)))
+    return results
 
 
 def decode_results(results) -> list:

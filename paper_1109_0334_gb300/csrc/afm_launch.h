@@ -49,7 +49,14 @@ struct BatchArgs {
     int* queue;            // pixel counter (zeroed before the launch)
     afm_result* res;       // [n_pix]
     float* pb_out;         // nullptr, or per queue slot the final personal bests
-                           // [D][P] followed by their misfits [P]
+                           // [D][P] (normalised cube) followed by their misfits [P]
+    // optional prior per queue slot (image scans): the swarm searches the box
+    // [box_lo, box_hi] ([slot][D], normalised) in box-local coordinates, and
+    // particles p < n_seed start at seeds [slot][n_seed][D]
+    const float* box_lo;
+    const float* box_hi;
+    const float* seeds;
+    int n_seed;
 };
 int batch_threads(int P, int kp);
 size_t batch_smem(int P, int D, int spc2);
@@ -81,6 +88,17 @@ cudaError_t launch_lm_cand(int D, int K, int J, const float* x, const double* H,
                            double lam0, double ratio, float* Xc, cudaStream_t st);
 cudaError_t launch_lm_select(int D, int K, int J, float* x, float* S, const float* Xc,
                              const float* Sc, cudaStream_t st);
+
+// image scans (kern_image.cu): coarse and fine pixel lists of a row-major
+// width x height image with coarse spacing `stride`; per fine pixel a box
+// around its (up to 4) coarse neighbours' winners, widened by `margin`, and
+// those winners as 4 seed points
+void image_counts(int width, int height, int stride, int* n_coarse, int* n_fine);
+cudaError_t launch_image_plan(int width, int height, int stride, int* coarse, int* fine,
+                              cudaStream_t st);
+cudaError_t launch_image_prior(int width, int height, int stride, int D, float margin,
+                               const afm_result* res, const int* fine, int n_fine, float* box_lo,
+                               float* box_hi, float* seeds, cudaStream_t st);
 
 // batched polish (kern_bpolish.cu): candidates of queue slot s are columns
 // s * Kc .. s * Kc + Kc - 1 of [D][n_pix * Kc] arrays

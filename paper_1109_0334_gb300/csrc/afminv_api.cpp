@@ -1232,7 +1232,8 @@ struct BatchSetup {
 afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
                        const int64_t* off, int n_pix, uint32_t pixel0, const afm_pso_cfg* cfg,
                        void* workspace, afm_result* results, int* particles_per_thread,
-                       cudaStream_t s, const char* who, BatchSetup* out) {
+                       cudaStream_t s, const char* who, BatchSetup* out,
+                       const afm_batch_select* select = nullptr) {
     afm_status st = check_problem(prob);
     if (st) return st;
     if ((st = modal_only(prob, who))) return st;
@@ -1246,7 +1247,8 @@ afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat
     const size_t smem = afm::batch_smem(cfg->P, prob->n_free, 2 * prob->steps_per_cycle);
     if (smem > 200 * 1024)
         return fail(AFM_ERR_INVALID_ARG, "swarm state of %zu bytes exceeds shared memory", smem);
-    const BatchLayout L = batch_layout(n_pix);
+    // queue (and sort order) sized for the pixels inverted
+    const BatchLayout L = batch_layout(select != nullptr ? select->n_run : n_pix);
     char* ws = static_cast<char*>(workspace);
     BatchSetup& B = *out;
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, B.Kf);
@@ -1262,8 +1264,23 @@ afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat
     a.queue = reinterpret_cast<int*>(ws + L.queue);
     a.res = results;
     a.pb_out = nullptr;
+    if (select != nullptr) {
+        if (!select->pixels || select->n_run < 1 || select->n_seed < 0 ||
+            select->n_seed > cfg->P || (select->n_seed > 0 && !select->seeds) ||
+            ((select->box_lo == nullptr) != (select->box_hi == nullptr)))
+            return fail(AFM_ERR_INVALID_ARG,
+                        "select: pixels and n_run >= 1, 0 <= n_seed <= P with seeds, box_lo and "
+                        "box_hi both or neither needed");
+        a.order = select->pixels;
+        a.n_pix = select->n_run;
+        a.box_lo = select->box_lo;
+        a.box_hi = select->box_hi;
+        a.seeds = select->n_seed > 0 ? select->seeds : nullptr;
+        a.n_seed = select->n_seed;
+    }
     // queue order (longest record first) is needed by the tuner's probe too
-    if (a.order) AFM_CUDA(afm::batch_sort(off, n_pix, const_cast<int*>(a.order), s), "sort kernel");
+    if (a.order && select == nullptr)
+        AFM_CUDA(afm::batch_sort(off, n_pix, const_cast<int*>(a.order), s), "sort kernel");
     int kp = 0, occ = 0;
     const int want = particles_per_thread ? *particles_per_thread : 0;
     const afm::PsoConst& pc = B.pc;
@@ -1280,7 +1297,7 @@ afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat
         return st;
     }
     B.kp = kp;
-    B.grid = std::min(n_pix, ctx->num_sms * occ);
+    B.grid = std::min(a.n_pix, ctx->num_sms * occ);
     if (particles_per_thread) *particles_per_thread = kp;
     return AFM_OK;
 }
@@ -1397,26 +1414,45 @@ afm_status afm_invert_batch_polished_workspace_size(const afm_problem* prob, con
     return AFM_OK;
 }
 
+static afm_status batch_polished_run(afm_ctx* ctx, const afm_problem* prob, const BatchSetup& B,
+                                     const BatchPolishLayout& PL, const float* U_cat,
+                                     const int64_t* off, const afm_pso_cfg* cfg, int polish_k,
+                                     int polish_steps, int n_cand, int method, char* ws,
+                                     afm_result* results, cudaStream_t s);
+
 afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
                                      const int64_t* off, int n_pix, uint32_t pixel0,
                                      const afm_pso_cfg* cfg, int polish_k, int polish_steps,
-                                     int n_cand, int method, void* workspace, size_t workspace_bytes,
-                                     afm_result* results, int* particles_per_thread, void* stream) {
+                                     int n_cand, int method, const afm_batch_select* select,
+                                     void* workspace, size_t workspace_bytes,
+                                     afm_result* results, int* particles_per_thread,
+                                     void* stream) {
     g_err[0] = 0;
-    afm_status st = check_batch_polish(prob, cfg, n_pix, polish_k, n_cand, method);
+    const int n_run = select ? select->n_run : n_pix;
+    afm_status st = check_batch_polish(prob, cfg, n_run, polish_k, n_cand, method);
     if (st) return st;
     if (polish_steps < 0) return fail(AFM_ERR_INVALID_ARG, "polish_steps < 0");
     if ((st = check_problem(prob))) return st;
-    const BatchPolishLayout PL = batch_polish_layout(*prob, *cfg, n_pix, polish_k, n_cand, method);
+    const BatchPolishLayout PL = batch_polish_layout(*prob, *cfg, n_run, polish_k, n_cand, method);
     if (workspace_bytes < PL.total)
         return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, PL.total);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     BatchSetup B;
     if ((st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, cfg, workspace, results,
-                          particles_per_thread, s, "afm_invert_batch_polished", &B)))
+                          particles_per_thread, s, "afm_invert_batch_polished", &B, select)))
         return st;
-    char* ws = static_cast<char*>(workspace);
+    return batch_polished_run(ctx, prob, B, PL, U_cat, off, cfg, polish_k, polish_steps, n_cand,
+                              method, static_cast<char*>(workspace), results, s);
+}
+
+static afm_status batch_polished_run(afm_ctx* ctx, const afm_problem* prob, const BatchSetup& B,
+                                     const BatchPolishLayout& PL, const float* U_cat,
+                                     const int64_t* off, const afm_pso_cfg* cfg, int polish_k,
+                                     int polish_steps, int n_cand, int method, char* ws,
+                                     afm_result* results, cudaStream_t s) {
+    afm_status st = AFM_OK;
     afm::BatchArgs a = B.a;
+    const int n_pix = a.n_pix;   // queue slots
     a.pb_out = reinterpret_cast<float*>(ws + PL.pb);
     float* xk = reinterpret_cast<float*>(ws + PL.xk);
     float* Sk = reinterpret_cast<float*>(ws + PL.Sk);
@@ -1434,6 +1470,112 @@ afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* prob, cons
              "winner pick kernel");
     AFM_CUDA(afm::launch_batch_final(B.Kd, B.pc, a, s), "batch FP64 kernel");
     return AFM_OK;
+}
+
+// Image scan workspace: the coarse and fine pixel lists, the fine pixels'
+// boxes and seeds, then one polished-batch workspace for the larger pass.
+struct ImageLayout {
+    size_t coarse, fine, blo, bhi, seeds, batch, total;
+    int n_coarse, n_fine;
+};
+
+static afm_status image_layout(const afm_problem& pr, const afm_image_cfg& ic, ImageLayout* L) {
+    if (ic.width < 1 || ic.height < 1 || ic.stride < 2 || !(ic.margin >= 0.0) || ic.margin > 1.0)
+        return fail(AFM_ERR_INVALID_ARG, "width, height >= 1, stride >= 2, 0 <= margin <= 1 needed");
+    if ((size_t)ic.width * ic.height > (size_t)1 << 26)
+        return fail(AFM_ERR_INVALID_ARG, "image too large");
+    afm::image_counts(ic.width, ic.height, ic.stride, &L->n_coarse, &L->n_fine);
+    const size_t D = (size_t)pr.n_free;
+    const int nf = std::max(L->n_fine, 1);
+    size_t off = 0;
+    L->coarse = off; off += align256(sizeof(int) * (size_t)L->n_coarse);
+    L->fine = off; off += align256(sizeof(int) * (size_t)nf);
+    L->blo = off; off += align256(sizeof(float) * (size_t)nf * D);
+    L->bhi = off; off += align256(sizeof(float) * (size_t)nf * D);
+    L->seeds = off; off += align256(sizeof(float) * (size_t)nf * 4 * D);
+    L->batch = off;
+    afm_status st = check_batch_polish(&pr, &ic.coarse, L->n_coarse, ic.coarse_polish_k, ic.n_cand,
+                                       ic.method);
+    if (st) return st;
+    if (L->n_fine > 0 &&
+        (st = check_batch_polish(&pr, &ic.fine, L->n_fine, ic.fine_polish_k, ic.n_cand, ic.method)))
+        return st;
+    if (ic.fine.P < 4 && L->n_fine > 0)
+        return fail(AFM_ERR_INVALID_ARG, "the fine swarm needs P >= 4 (4 seed particles)");
+    const size_t bc = batch_polish_layout(pr, ic.coarse, L->n_coarse, ic.coarse_polish_k, ic.n_cand,
+                                          ic.method).total;
+    const size_t bf = L->n_fine > 0 ? batch_polish_layout(pr, ic.fine, L->n_fine, ic.fine_polish_k,
+                                                          ic.n_cand, ic.method).total
+                                    : 0;
+    L->total = off + std::max(bc, bf);
+    return AFM_OK;
+}
+
+afm_status afm_invert_image_workspace_size(const afm_problem* prob, const afm_image_cfg* icfg,
+                                           size_t* bytes) {
+    g_err[0] = 0;
+    if (!prob || !icfg || !bytes) return fail(AFM_ERR_INVALID_ARG, "NULL prob, icfg or bytes");
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    ImageLayout L;
+    if ((st = image_layout(*prob, *icfg, &L))) return st;
+    *bytes = L.total;
+    return AFM_OK;
+}
+
+afm_status afm_invert_image(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
+                            const int64_t* off, uint32_t pixel0, const afm_image_cfg* icfg,
+                            void* workspace, size_t workspace_bytes, afm_result* results,
+                            void* stream) {
+    g_err[0] = 0;
+    if (!prob || !icfg) return fail(AFM_ERR_INVALID_ARG, "NULL prob or icfg");
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    ImageLayout L;
+    if ((st = image_layout(*prob, *icfg, &L))) return st;
+    if (!workspace || workspace_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % 256)
+        return fail(AFM_ERR_INVALID_ARG, "workspace NULL, misaligned or < %zu bytes", L.total);
+    const afm_image_cfg& ic = *icfg;
+    const int n_pix = ic.width * ic.height, D = prob->n_free;
+    char* ws = static_cast<char*>(workspace);
+    int* coarse = reinterpret_cast<int*>(ws + L.coarse);
+    int* fine = reinterpret_cast<int*>(ws + L.fine);
+    float* blo = reinterpret_cast<float*>(ws + L.blo);
+    float* bhi = reinterpret_cast<float*>(ws + L.bhi);
+    float* seeds = reinterpret_cast<float*>(ws + L.seeds);
+    char* bws = ws + L.batch;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    AFM_CUDA(afm::launch_image_plan(ic.width, ic.height, ic.stride, coarse, fine, s), "image plan kernel");
+    // pass 1: the coarse pixels, full search
+    afm_batch_select sel{};
+    sel.pixels = coarse;
+    sel.n_run = L.n_coarse;
+    BatchSetup B;
+    if ((st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, &ic.coarse, bws, results, nullptr, s,
+                          "afm_invert_image", &B, &sel)))
+        return st;
+    BatchPolishLayout PL = batch_polish_layout(*prob, ic.coarse, L.n_coarse, ic.coarse_polish_k,
+                                               ic.n_cand, ic.method);
+    if ((st = batch_polished_run(ctx, prob, B, PL, U_cat, off, &ic.coarse, ic.coarse_polish_k,
+                                 ic.coarse_polish_steps, ic.n_cand, ic.method, bws, results, s)))
+        return st;
+    if (L.n_fine == 0) return AFM_OK;
+    // pass 2: every other pixel inside the box of its coarse neighbours' winners
+    AFM_CUDA(afm::launch_image_prior(ic.width, ic.height, ic.stride, D, (float)ic.margin, results, fine,
+                                     L.n_fine, blo, bhi, seeds, s),
+             "image prior kernel");
+    sel.pixels = fine;
+    sel.n_run = L.n_fine;
+    sel.box_lo = blo;
+    sel.box_hi = bhi;
+    sel.seeds = seeds;
+    sel.n_seed = 4;
+    if ((st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, &ic.fine, bws, results, nullptr, s,
+                          "afm_invert_image", &B, &sel)))
+        return st;
+    PL = batch_polish_layout(*prob, ic.fine, L.n_fine, ic.fine_polish_k, ic.n_cand, ic.method);
+    return batch_polished_run(ctx, prob, B, PL, U_cat, off, &ic.fine, ic.fine_polish_k,
+                              ic.fine_polish_steps, ic.n_cand, ic.method, bws, results, s);
 }
 
 afm_status afm_synth_records(afm_ctx* ctx, const afm_problem* prob, const double* x_truth,

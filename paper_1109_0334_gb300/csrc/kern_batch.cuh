@@ -40,14 +40,23 @@ __global__ void __launch_bounds__(1024) batch_kernel(const KConst<float> K, cons
     __shared__ unsigned long long wkey[32];
     __shared__ unsigned long long s_gkey;
     __shared__ int s_slot, s_bad;
+    __shared__ float s_blo[AFM_MAXD], s_bspan[AFM_MAXD];   // optional per-slot box
+    const bool boxed = a.box_lo != nullptr;
     build_drive_table(K, tab);
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = T >> 5;
     for (;;) {
         __syncthreads();   // table built / previous pixel finished with shared memory
         if (tid == 0) {
-            s_slot = atomicAdd(a.queue, 1);
+            const int sl = atomicAdd(a.queue, 1);
+            s_slot = sl;
             s_bad = 0;
+            if (boxed && sl < a.n_pix)
+                for (int d = 0; d < D; ++d) {
+                    const float lo = a.box_lo[(size_t)sl * D + d];
+                    s_blo[d] = lo;
+                    s_bspan[d] = a.box_hi[(size_t)sl * D + d] - lo;
+                }
         }
         __syncthreads();
         const int slot = s_slot;
@@ -74,6 +83,16 @@ __global__ void __launch_bounds__(1024) batch_kernel(const KConst<float> K, cons
                     const float u0 = unif24(word_of(w0, q)), u1 = unif24(word_of(w1, q));
                     sx[d * P + p] = u0;
                     sv[d * P + p] = (u1 - u0) * 0.5f;
+                }
+            }
+            if (a.seeds != nullptr && p < a.n_seed) {   // seed particle, at rest, box-local
+                for (int d = 0; d < D; ++d) {
+                    const float s = a.seeds[((size_t)slot * a.n_seed + p) * D + d];
+                    const float lo = boxed ? s_blo[d] : 0.f, sp = boxed ? s_bspan[d] : 1.f;
+                    float t = sp > 0.f ? (s - lo) / sp : 0.f;
+                    t = t > 0.f ? (t < 1.f ? t : 1.f) : 0.f;
+                    sx[d * P + p] = t;
+                    sv[d * P + p] = 0.f;
                 }
             }
         }
@@ -104,7 +123,8 @@ __global__ void __launch_bounds__(1024) batch_kernel(const KConst<float> K, cons
             for (int k = 0; k < KP; ++k) {
                 const int p = min(tid + k * T, P - 1);
                 float x[AFM_MAXD];
-                for (int d = 0; d < D; ++d) x[d] = sx[d * P + p];
+                for (int d = 0; d < D; ++d)
+                    x[d] = boxed ? fmaf(sx[d * P + p], s_bspan[d], s_blo[d]) : sx[d * P + p];
                 c[k] = make_coef<float, float>(K, x);
             }
             float S[KP];
@@ -145,13 +165,18 @@ __global__ void __launch_bounds__(1024) batch_kernel(const KConst<float> K, cons
                 const int p = tid + k * T;
                 if (p >= P) continue;
                 dst[(size_t)D * P + p] = pbS[k];
-                for (int d = 0; d < D; ++d) dst[(size_t)d * P + p] = spb[d * P + p];
+                for (int d = 0; d < D; ++d)
+                    dst[(size_t)d * P + p] =
+                        boxed ? fmaf(spb[d * P + p], s_bspan[d], s_blo[d]) : spb[d * P + p];
             }
         }
         if (tid == 0) {
             const int g = min((int)(s_gkey & 0x7fffffffu), P - 1);
             afm_result* r = a.res + pix;
-            for (int d = 0; d < AFM_MAXD; ++d) r->x[d] = d < D ? (double)spb[d * P + g] : 0.0;
+            for (int d = 0; d < AFM_MAXD; ++d)
+                r->x[d] = d >= D ? 0.0
+                                 : (double)(boxed ? fmaf(spb[d * P + g], s_bspan[d], s_blo[d])
+                                                  : spb[d * P + g]);
             r->S = (double)__uint_as_float((uint32_t)(s_gkey >> 32));
             r->iters = pc.iters;
             r->winner = g;

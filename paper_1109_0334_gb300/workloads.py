@@ -83,6 +83,17 @@ WORKLOADS["f2_spring_damper"] = dict(
     free=[_KS, _ZS], fixed=[0.0, 0.0, 0.0, 0.0, 0.0], x_truth=[4.0 / 25.0, 0.05],
     P=512, iters=30, seed=SEED_BASE + 7, **_APPA, **_PSO)
 
+# Image scan with cross-pixel warm start: a 64 x 64 image of the 3-mode DMT
+# cantilever, 40 cycles per pixel, truths varying smoothly over the image.
+WORKLOADS["f1_image"] = dict(
+    name="64 x 64 image, 3-mode EB DMT, coarse grid every 4th pixel",
+    model="modal_eb", n_modes=3, spc=256, cycles=40, force="dmt",
+    free=[_E, _H, _R, _A0], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
+    width=64, height=64, stride=4, margin=0.05,
+    P=256, iters=5, polish_k=8, polish_steps=12, n_cand=8,            # coarse pixels
+    fine=dict(P=64, iters=0, polish_k=4, polish_steps=6),             # the others
+    seed=SEED_BASE + 8, **_CANTILEVER, **_PSO)
+
 for _w in WORKLOADS.values():
     _w["sigma"] = 0.005 * _w["A0"]    # 0.5 % of the free amplitude
     _w["record_sub"] = 4
@@ -107,3 +118,20 @@ def sample_x(D: int, P: int, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.
     rng = np.random.default_rng(seed)
     x = rng.uniform(lo, hi, size=(D, P)).astype(np.float32)
     return x
+
+
+def image_truth(D: int, width: int, height: int, seed: int) -> np.ndarray:
+    """Seeded truths varying smoothly over a width x height image, [D][W*H]
+    in [0.15, 0.85] (row-major pixels): per dimension two plane waves of
+    small integer wave numbers."""
+    rng = np.random.default_rng(seed)
+    j, i = np.meshgrid(np.arange(height), np.arange(width), indexing="ij")
+    out = np.empty((D, width * height))
+    for d in range(D):
+        f = np.zeros((height, width))
+        for amp in (0.6, 0.4):
+            kx, ky = rng.integers(0, 3, size=2)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += amp * np.sin(2 * np.pi * (kx * i / width + ky * j / height) + ph)
+        out[d] = (0.5 + 0.35 * f).reshape(-1)
+    return out
