@@ -194,7 +194,25 @@ int orc_setup(const orc_case* c, orc_modal* md)
         md->etad0[i] = w * creal(ci);
     }
     md->dt = 1.0 / (c->f1 * c->spc);
+    if (c->drive == 1) {          /* base motion set per parameter vector; start at rest */
+        if (c->dt <= 0.0 || c->model == ORC_FE_HERMITE) return -1;
+        md->dt = c->dt;
+        md->a = md->psi = 0.0;
+        for (int i = 0; i < m; ++i) md->eta0[i] = md->etad0[i] = 0.0;
+    }
     return 0;
+}
+
+/* Drive mode 1 (reading R18): g = -d^2 y_b/dt^2 for y_b = a sin(phi),
+ * phi = 2 pi (f t + g t^2):  g(t) = a (phi'^2 sin phi - phi'' cos phi) with
+ * phi' = 2 pi (f + 2 g t), phi'' = 4 pi g; (a, f, g) = th[5..7]. */
+double orc_drive_chirp(const double th[ORC_NSLOT], double t)
+{
+    double a = th[5], f = th[6], g = th[7];
+    double phi = 2.0 * M_PI * (f * t + g * t * t);
+    double dphi = 2.0 * M_PI * (f + 2.0 * g * t);
+    double ddphi = 4.0 * M_PI * g;
+    return a * (dphi * dphi * sin(phi) - ddphi * cos(phi));
 }
 
 /* g = -d^2 y_b/dt^2 at the half-step index j, i.e. t = j dt / 2, with the
@@ -210,7 +228,7 @@ double orc_drive_half(const orc_modal* md, int spc, long j)
 /* Tip-sample forces.  d is the gap, ddot its rate; F > 0 pushes the tip     */
 /* away from the sample.                                                     */
 /* ======================================================================== */
-double orc_force(int kind, const double th[5], double d, double ddot)
+double orc_force(int kind, const double th[ORC_NSLOT], double d, double ddot)
 {
     switch (kind) {
     case ORC_F_LINEAR:
@@ -236,7 +254,7 @@ double orc_force(int kind, const double th[5], double d, double ddot)
 /* Right-hand side of the modal system (Eq. 2 with 2 zeta omega_i = omega_i/Q,
  * reading R4):  eta_i'' = F/m + gamma_i g - omega_i^2 eta_i - (omega_i/Q_i) eta_i'
  * with the gap d = Zc + sum_i eta_i (tip-normalised shapes, reading R5). */
-static void rhs(const orc_case* c, const orc_modal* md, const double th[5], double g,
+static void rhs(const orc_case* c, const orc_modal* md, const double th[ORC_NSLOT], double g,
                 const double* y, double* f)
 {
     int m = md->m;
@@ -255,11 +273,12 @@ static void rhs(const orc_case* c, const orc_modal* md, const double th[5], doub
  * the synthetic records, reading R10).  u[n] = tip deflection at the end of
  * record step n + 1.  state (optional) receives [n_steps + 1][2m] modal states
  * at the record instants, starting with t = 0. */
-int orc_forward(const orc_case* c, const double th[5], int n_steps, int sub,
+int orc_forward(const orc_case* c, const double th[ORC_NSLOT], int n_steps, int sub,
                 double* u, double* state)
 {
     orc_case cf = *c;
     cf.spc = c->spc * sub;
+    cf.dt = c->dt / sub;
     orc_modal md;
     if (orc_setup(&cf, &md)) return -1;
     int m = md.m, n2 = 2 * m;
@@ -271,9 +290,17 @@ int orc_forward(const orc_case* c, const double th[5], int n_steps, int sub,
     long step = 0;
     for (int n = 0; n < n_steps; ++n) {
         for (int s = 0; s < sub; ++s, ++step) {
-            double g0 = orc_drive_half(&md, cf.spc, 2 * step);
-            double gh = orc_drive_half(&md, cf.spc, 2 * step + 1);
-            double g1 = orc_drive_half(&md, cf.spc, 2 * step + 2);
+            double g0, gh, g1;
+            if (c->drive == 1) {
+                double t = (double)step * h;
+                g0 = orc_drive_chirp(th, t);
+                gh = orc_drive_chirp(th, t + 0.5 * h);
+                g1 = orc_drive_chirp(th, t + h);
+            } else {
+                g0 = orc_drive_half(&md, cf.spc, 2 * step);
+                gh = orc_drive_half(&md, cf.spc, 2 * step + 1);
+                g1 = orc_drive_half(&md, cf.spc, 2 * step + 2);
+            }
             rhs(&cf, &md, th, g0, y, k1);
             for (int q = 0; q < n2; ++q) yt[q] = y[q] + 0.5 * h * k1[q];
             rhs(&cf, &md, th, gh, yt, k2);
@@ -303,9 +330,9 @@ double orc_misfit(const double* U, const double* u, int n)
 
 /* Normalised coordinates x in [0,1]^D -> physical slots (reading R12):
  * log10-linear for log dims, linear otherwise. */
-void orc_map(const orc_pmap* pm, const double* x, double th[5])
+void orc_map(const orc_pmap* pm, const double* x, double th[ORC_NSLOT])
 {
-    for (int s = 0; s < 5; ++s) th[s] = pm->fixed[s];
+    for (int s = 0; s < ORC_NSLOT; ++s) th[s] = pm->fixed[s];
     for (int d = 0; d < pm->D; ++d) {
         double lo = pm->lo[d], hi = pm->hi[d];
         if (pm->logs[d])
@@ -315,10 +342,10 @@ void orc_map(const orc_pmap* pm, const double* x, double th[5])
     }
 }
 
-int orc_fe_forward(const orc_case* c, const double th[5], int n_steps, int sub, double* u,
+int orc_fe_forward(const orc_case* c, const double th[ORC_NSLOT], int n_steps, int sub, double* u,
                    double* setup_out);
 
-static int forward_any(const orc_case* c, const double th[5], int n, double* u)
+static int forward_any(const orc_case* c, const double th[ORC_NSLOT], int n, double* u)
 {
     if (c->model == ORC_FE_HERMITE) return orc_fe_forward(c, th, n, 1, u, NULL);
     return orc_forward(c, th, n, 1, u, NULL);
@@ -327,7 +354,7 @@ static int forward_any(const orc_case* c, const double th[5], int n, double* u)
 int orc_misfit_x(const orc_case* c, const orc_pmap* pm, const double* x,
                  const double* U, int n, double* S)
 {
-    double th[5];
+    double th[ORC_NSLOT];
     orc_map(pm, x, th);
     double* u = (double*)malloc(sizeof(double) * n);
     int rc = forward_any(c, th, n, u);
@@ -472,7 +499,7 @@ int orc_cycles(uint64_t seed, uint32_t pixel, int lo, int hi)
 int orc_record(const orc_case* c, const orc_pmap* pm, const double* x, int n,
                int sub, double sigma, uint64_t seed, uint32_t pixel, double* U)
 {
-    double th[5];
+    double th[ORC_NSLOT];
     orc_map(pm, x, th);
     int rc = c->model == ORC_FE_HERMITE ? orc_fe_forward(c, th, n, sub, U, NULL)
                                         : orc_forward(c, th, n, sub, U, NULL);
@@ -490,6 +517,15 @@ int orc_record(const orc_case* c, const orc_pmap* pm, const double* x, int n,
             U[j] += sigma * z;
         }
     }
+    return 0;
+}
+
+/* The complex-step paths cover the force-law slots of the steady drive. */
+static int complex_step_unsupported(const orc_case* c, const orc_pmap* pm)
+{
+    if (c->drive != 0) return 1;
+    for (int d = 0; d < pm->D; ++d)
+        if (pm->slot[d] < 0 || pm->slot[d] >= 5) return 1;
     return 0;
 }
 
@@ -588,6 +624,7 @@ static void grad_cs_serial(const orc_case* c, const orc_modal* md, const orc_pma
 int orc_grad_cs(const orc_case* c, const orc_pmap* pm, const double* x,
                 const double* U, int n, double* S, double* grad)
 {
+    if (complex_step_unsupported(c, pm)) return -1;
     orc_modal md;
     if (orc_setup(c, &md)) return -1;
     const double h = 1e-30;
@@ -619,6 +656,7 @@ int orc_grad_cs(const orc_case* c, const orc_pmap* pm, const double* x,
 int orc_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, double* x, int K,
                int steps, int n_cand, double alpha0, double shrink, double sigma, double* S)
 {
+    if (complex_step_unsupported(c, pm)) return -1;
     orc_modal md;
     if (orc_setup(c, &md)) return -1;
     int D = pm->D;
@@ -895,7 +933,7 @@ int orc_fe_matrices(const orc_case* c, double* M, double* K, double* C, double* 
 }
 
 /* d F / d d for the tip-force laws without rate dependence. */
-static double force_slope(int kind, const double th[5], double d)
+static double force_slope(int kind, const double th[ORC_NSLOT], double d)
 {
     switch (kind) {
     case ORC_F_LINEAR:
@@ -916,9 +954,10 @@ static double force_slope(int kind, const double th[5], double d)
  * h = 1 / (f_1 spc) with f_1 the FE model's own first frequency, each split
  * into `sub` Newmark steps).  setup_out (optional, 8 values): w1, w2, alpha,
  * beta, a, psi, h, thickness. */
-int orc_fe_forward(const orc_case* c, const double th[5], int n_steps, int sub, double* u,
+int orc_fe_forward(const orc_case* c, const double th[ORC_NSLOT], int n_steps, int sub, double* u,
                    double* setup_out)
 {
+    if (c->drive != 0) return -1;
     if (c->force == ORC_F_DMT_KV || c->force == ORC_F_SPRING_DAMPER) return -1;
     orc_fe_mats* fe = (orc_fe_mats*)malloc(sizeof(orc_fe_mats));
     if (fe_build(c, fe)) { free(fe); return -1; }
@@ -1084,6 +1123,7 @@ static int normal_eq_serial(const orc_case* c, const orc_modal* md, const orc_pm
 int orc_normal_eq(const orc_case* c, const orc_pmap* pm, const double* x, const double* U,
                   int n, double* S, double* H, double* b)
 {
+    if (complex_step_unsupported(c, pm)) return -1;
     orc_modal md;
     if (orc_setup(c, &md)) return -1;
     return normal_eq_serial(c, &md, pm, x, U, n, S, H, b, 1);
@@ -1095,6 +1135,7 @@ int orc_normal_eq(const orc_case* c, const orc_pmap* pm, const double* x, const 
 int orc_lm_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, double* x,
                   int K, int steps, int n_lambda, double lam0, double lam_ratio, double* S)
 {
+    if (complex_step_unsupported(c, pm)) return -1;
     orc_modal md;
     if (orc_setup(c, &md)) return -1;
     int D = pm->D, J = n_lambda, KJ = K * n_lambda;

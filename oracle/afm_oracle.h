@@ -51,6 +51,10 @@ extern "C" {
 #endif
 
 #define ORC_MAXM 8
+/* Parameter slots th[ORC_NSLOT]: 0..4 the force law's (below); 5..7 the
+ * base motion of drive mode 1 (reading R18): amplitude a [m], frequency f
+ * [Hz], chirp rate g [Hz/s], y_b(t) = a sin(2 pi (f t + g t^2)). */
+#define ORC_NSLOT 8
 
 /* Cantilever model families. */
 enum { ORC_POINT_MASS = 0, ORC_MODAL_EB = 1, ORC_FE_HERMITE = 2 };
@@ -82,6 +86,11 @@ typedef struct {
     double fe_f1;         /* first natural frequency target [Hz]                 */
     double fe_Q;          /* Rayleigh damping: Q of modes 1 and 2                */
     double nm_beta;       /* Newmark beta (gamma = 1/2)                          */
+    /* base motion: 0 = driven at f1 with free amplitude A0, starting on the
+     * free steady state (R6); 1 = y_b = a sin(2 pi (f t + g t^2)) with (a, f,
+     * g) in slots 5..7, starting at rest (R18; modal models only) */
+    int drive;
+    double dt;            /* drive 1: step [s] (spc is not used)                 */
 } orc_case;
 
 /* Derived modal quantities (SI). */
@@ -103,7 +112,7 @@ typedef struct {
     int slot[5];          /* theta slot of free dim d                           */
     double lo[5], hi[5];  /* bounds of free dim d (SI)                          */
     int logs[5];          /* 1: log10 map, 0: linear                            */
-    double fixed[5];      /* values of all slots (free ones are overwritten)    */
+    double fixed[ORC_NSLOT];  /* values of all slots (free ones are overwritten) */
 } orc_pmap;
 
 typedef struct {
@@ -126,13 +135,14 @@ int orc_modal_factors(int n_modes, int n_points, double* bL, double* gam,
                       double* int_phi2, double* phi_tip);
 int orc_setup(const orc_case* c, orc_modal* md);
 double orc_drive_half(const orc_modal* md, int spc, long j);
+double orc_drive_chirp(const double th[ORC_NSLOT], double t);
 
 /* ---- force, forward, misfit (Eqs. 2-5) ----------------------------------- */
-double orc_force(int kind, const double th[5], double d, double ddot);
-int orc_forward(const orc_case* c, const double th[5], int n_steps, int sub,
+double orc_force(int kind, const double th[ORC_NSLOT], double d, double ddot);
+int orc_forward(const orc_case* c, const double th[ORC_NSLOT], int n_steps, int sub,
                 double* u, double* state);
 double orc_misfit(const double* U, const double* u, int n);
-void orc_map(const orc_pmap* pm, const double* x, double th[5]);
+void orc_map(const orc_pmap* pm, const double* x, double th[ORC_NSLOT]);
 int orc_misfit_x(const orc_case* c, const orc_pmap* pm, const double* x,
                  const double* U, int n, double* S);
 int orc_misfit_batch(const orc_case* c, const orc_pmap* pm, const double* x,
@@ -181,7 +191,7 @@ int orc_polish(const orc_case* c, const orc_pmap* pm, const double* U, int n, do
 int orc_fe_dofs(const orc_case* c);
 int orc_fe_matrices(const orc_case* c, double* M, double* K, double* C, double* w12,
                     double* geom);
-int orc_fe_forward(const orc_case* c, const double th[5], int n_steps, int sub, double* u,
+int orc_fe_forward(const orc_case* c, const double th[ORC_NSLOT], int n_steps, int sub, double* u,
                    double* setup_out);
 
 void orc_set_threads(int n);

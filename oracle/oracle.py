@@ -24,6 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 MAXM = 8
+NSLOT = 8       # parameter slots: 0..4 force law, 5..7 base motion (a, f, g)
 POINT_MASS, MODAL_EB, FE_HERMITE = 0, 1, 2
 F_LINEAR, F_DMT, F_DMT_KV, F_HOOKE, F_SPRING_DAMPER = 0, 1, 2, 3, 4
 
@@ -50,7 +51,8 @@ class Case(C.Structure):
                 ("Zc", C.c_double), ("spc", C.c_int), ("force", C.c_int),
                 ("n_elem", C.c_int), ("L", C.c_double), ("E", C.c_double),
                 ("rho", C.c_double), ("fe_k", C.c_double), ("fe_f1", C.c_double),
-                ("fe_Q", C.c_double), ("nm_beta", C.c_double)]
+                ("fe_Q", C.c_double), ("nm_beta", C.c_double), ("drive", C.c_int),
+                ("dt", C.c_double)]
 
 
 class Modal(C.Structure):
@@ -62,7 +64,7 @@ class Modal(C.Structure):
 
 class Pmap(C.Structure):
     _fields_ = [("D", C.c_int), ("slot", C.c_int * 5), ("lo", C.c_double * 5),
-                ("hi", C.c_double * 5), ("logs", C.c_int * 5), ("fixed", C.c_double * 5)]
+                ("hi", C.c_double * 5), ("logs", C.c_int * 5), ("fixed", C.c_double * NSLOT)]
 
 
 class Pso(C.Structure):
@@ -99,6 +101,8 @@ def lib():
             L.orc_misfit.argtypes = [_dp, _dp, C.c_int]
             L.orc_misfit.restype = C.c_double
             L.orc_map.argtypes = [C.POINTER(Pmap), _dp, _dp]
+            L.orc_drive_chirp.restype = C.c_double
+            L.orc_drive_chirp.argtypes = [_dp, C.c_double]
             L.orc_misfit_batch.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int,
                                            _dp, C.c_int, _dp]
             L.orc_pso_init.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32, _dp, _dp]
@@ -169,6 +173,8 @@ def make_case(spec: dict) -> Case:
     c.fe_f1 = float(spec.get("f1_hz", 0.0))
     c.fe_Q = float(qs[0])
     c.nm_beta = float(spec.get("newmark_beta", 0.25))
+    c.drive = 1 if spec.get("drive") == "chirp" else 0
+    c.dt = float(spec.get("dt", 0.0))
     return c
 
 
@@ -184,6 +190,8 @@ def make_pmap(spec: dict) -> Pmap:
         pm.logs[d] = int(bool(lg))
     for s in range(5):
         pm.fixed[s] = float(spec["fixed"][s])
+    for s, v in enumerate(spec.get("drive_params", (0.0, 0.0, 0.0))):   # slots 5..7: a, f, g
+        pm.fixed[5 + s] = float(v)
     return pm
 
 
@@ -249,7 +257,7 @@ def misfit(U, u) -> float:
 
 
 def map_x(pm: Pmap, x) -> np.ndarray:
-    th = np.zeros(5)
+    th = np.zeros(NSLOT)
     lib().orc_map(C.byref(pm), np.ascontiguousarray(x, dtype=np.float64), th)
     return th
 

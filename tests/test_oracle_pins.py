@@ -565,6 +565,92 @@ def test_polish_descends_to_a_stationary_point(orc):
 
 
 # --------------------------------------------------------------------------
+# Base-motion inversion: drive mode 1, y_b = a sin(2 pi (f t + g t^2)) from rest
+# (reading R18)
+# --------------------------------------------------------------------------
+def _drive_spec(**over):
+    spec = dict(W.get("c1"), model="point_mass", force="linear_spring", drive="chirp",
+                dt=1e-7, fixed=[0.0] * 5, free=[(5, 0.0, 100e-9, False)],
+                drive_params=(2e-9, 25600.0, 0.0), f1_hz=25468.9, k=1.3705)
+    spec.update(over)
+    return spec
+
+
+def test_chirp_drive_is_minus_the_base_acceleration(orc):
+    th = np.zeros(8)
+    th[5:8] = (2e-9, 10000.0, 2e7)
+    yb = lambda t: th[5] * np.sin(2 * np.pi * (th[6] * t + th[7] * t * t))
+    h = 1e-9
+    for t in (0.0, 3.3e-5, 1e-4):
+        fd = -(yb(t + h) - 2 * yb(t) + yb(t - h)) / h ** 2
+        g = orc.lib().orc_drive_chirp(th, t)
+        assert g == pytest.approx(fd, rel=1e-5, abs=1e-9 * abs(fd) + 1e-3)
+
+
+def test_sine_drive_from_rest_closed_form(orc):
+    """Point mass, no tip force, y_b = a sin(W t) from rest: particular plus
+    homogeneous solution of the damped oscillator."""
+    spec = _drive_spec()
+    c, pm = orc.make_case(spec), orc.make_pmap(spec)
+    n = 3000
+    th = orc.map_x(pm, np.array([0.02]))          # a = 2 nm
+    u = orc.forward(c, th, n)
+    w0, Q, a, Wd = 2 * np.pi * spec["f1_hz"], 400.0, th[5], 2 * np.pi * th[6]
+    t = np.arange(1, n + 1) * spec["dt"]
+    den = (w0 ** 2 - Wd ** 2) ** 2 + (w0 * Wd / Q) ** 2
+    A_s = a * Wd ** 2 * (w0 ** 2 - Wd ** 2) / den
+    A_c = -a * Wd ** 2 * (w0 * Wd / Q) / den
+    zeta = 1 / (2 * Q)
+    wdd = w0 * np.sqrt(1 - zeta ** 2)
+    A = -A_c                                     # eta(0) = 0
+    B = (-A_s * Wd + zeta * w0 * A) / wdd        # eta'(0) = 0
+    exact = A_s * np.sin(Wd * t) + A_c * np.cos(Wd * t) + \
+        np.exp(-zeta * w0 * t) * (A * np.cos(wdd * t) + B * np.sin(wdd * t))
+    assert np.max(np.abs(u - exact)) <= 1e-6 * np.max(np.abs(exact))
+
+
+def test_chirp_three_modes_against_an_independent_integrator(orc):
+    """3-mode cantilever driven by a chirp from rest: the RK4 record against
+    scipy's DOP853 at tight tolerance on the same modal equations."""
+    from scipy.integrate import solve_ivp
+    spec = _drive_spec(model="modal_eb", n_modes=3, drive_params=(2e-9, 10000.0, 2e7),
+                       free=[(5, 0.0, 100e-9, False), (6, 7500.0, 12500.0, False),
+                             (7, 1.9e7, 2.1e7, False)])
+    c, pm = orc.make_case(spec), orc.make_pmap(spec)
+    md = orc.setup(c)
+    n = 1000
+    th = orc.map_x(pm, np.array([0.02, 0.5, 0.5]))
+    u = orc.forward(c, th, n)
+    m = 3
+    w, gam = np.array(md.w[:m]), np.array(md.gam[:m])
+
+    def f(t, y):
+        g = orc.lib().orc_drive_chirp(th, t)
+        return np.concatenate([y[m:], gam * g - w ** 2 * y[:m] - (w / 400.0) * y[m:]])
+    t = np.arange(1, n + 1) * spec["dt"]
+    sol = solve_ivp(f, (0, t[-1]), np.zeros(2 * m), method="DOP853", t_eval=t, rtol=1e-12,
+                    atol=1e-22)
+    ref = sol.y[:m].sum(axis=0)
+    assert np.max(np.abs(u - ref)) <= 1e-6 * np.max(np.abs(ref))
+
+
+def test_amplitude_inversion_is_linear_least_squares(orc):
+    """Without tip force the record is linear in the base amplitude, the
+    misfit quadratic: the swarm's optimum is the closed-form least-squares
+    amplitude."""
+    spec = _drive_spec(P=64, iters=30, sigma=0.1e-9)
+    c, pm = orc.make_case(spec), orc.make_pmap(spec)
+    n = 1000
+    U = orc.record(c, pm, np.array([0.02]), n, 4, spec["sigma"], spec["seed"])
+    u1 = orc.forward(c, orc.map_x(pm, np.array([1.0])), n)      # a = 100 nm
+    x_star = float(np.sum(U * u1) / np.sum(u1 * u1))
+    x, S, _ = orc.invert(c, pm, U, spec["P"], spec["iters"], spec["w"], spec["c1"], spec["c2"],
+                         spec["seed"])
+    assert abs(x[0] - x_star) <= 1e-4 * x_star
+    assert abs(x_star - 0.02) <= 1e-3
+
+
+# --------------------------------------------------------------------------
 # Swarm in a box with seed particles (reading R17)
 # --------------------------------------------------------------------------
 def test_boxed_swarm_special_cases(orc, c1_problem):
