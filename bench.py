@@ -295,11 +295,14 @@ def run_c3(A, W, dev, peak_ops, flush):
 
 
 def _theta_of(spec, xn):
-    """SI parameter slots of normalised coordinates xn [D] (truth draws)."""
+    """SI parameter slots (5 force-law slots, then base a, f, g) of
+    normalised coordinates xn [D] (truth draws)."""
     import math
-    th = [0.0] * 5
+    th = [0.0] * 8
     for s5, v in enumerate(spec["fixed"]):
         th[s5] = v
+    for k, v in enumerate(spec.get("drive_params", (0.0, 0.0, 0.0))):
+        th[5 + k] = v
     for d, (slot, lo, hi, lg) in enumerate(spec["free"]):
         th[slot] = 10 ** (math.log10(lo) + xn[d] * (math.log10(hi) - math.log10(lo))) if lg \
             else lo + xn[d] * (hi - lo)
@@ -575,20 +578,30 @@ def run_image(A, W, dev, flush):
 
 
 # ---------------------------------------------------------------------------
-# The paper's own tip-sample experiments (App. A cantilever, 8 modes)
+# The paper's own experiments (App. A cantilever, 8 modes)
 # ---------------------------------------------------------------------------
 def run_paper_laws(A, W, dev, flush):
-    """Hooke contact (k, h) and spring-damper (k, zeta_s) inversions with the
-    paper's truth values; records made on the GPU at dt/4 plus noise."""
+    """Hooke contact (k, h) and spring-damper (k, zeta_s) inversions (Sec. 4.2,
+    4.3) and the base-motion inversions (Sec. 4.1: amplitude, amplitude and
+    frequency, chirp) with the paper's truth values; records made on the GPU
+    at dt/4 plus noise."""
     import torch
     out = {}
-    for name in ("f2_hooke", "f2_spring_damper"):
+    for name in ("f2_hooke", "f2_spring_damper", "f3_amp", "f3_amp_freq", "f3_chirp"):
         spec = W.get(name)
         N = W.n_steps(spec)
         prob = A.make_problem(spec)
         xt = torch.tensor(spec["x_truth"], dtype=torch.float64, device=dev).reshape(-1, 1)
-        off = torch.tensor([0, N], dtype=torch.int64, device=dev)
-        U = A.synth_records(prob, xt, off, spec["record_sub"], spec["sigma"], spec["seed"], 0)
+        if spec.get("drive") == "chirp":
+            # record: the library's forward at dt/4 (every 4th sample) plus noise
+            fine = A.make_problem(dict(spec, dt=spec["dt"] / 4, n_steps=4 * N))
+            d, _ = A.forward_batch_f64(fine, xt, None)
+            gen = torch.Generator(device=dev).manual_seed(spec["seed"])
+            U = (d[3::4, 0].float() + (spec["sigma"] / 1e-9) *
+                 torch.randn(N, device=dev, generator=gen)).contiguous()
+        else:
+            off = torch.tensor([0, N], dtype=torch.int64, device=dev)
+            U = A.synth_records(prob, xt, off, spec["record_sub"], spec["sigma"], spec["seed"], 0)
         cfg = A.make_pso(spec)
         A.invert(prob, U, cfg)
         torch.cuda.synchronize()
@@ -601,8 +614,9 @@ def run_paper_laws(A, W, dev, flush):
         r = A.decode_result(res)
         th_t = _theta_of(spec, spec["x_truth"])
         slots = [f[0] for f in spec["free"]]
+        val = list(r["theta"]) + list(r["drive"])
         out[name] = {"workload": spec["name"], "ms_per_inversion": e0.elapsed_time(e1),
-                     "record_steps": N, "theta_free": [r["theta"][s] for s in slots],
+                     "record_steps": N, "theta_free": [val[s] for s in slots],
                      "theta_truth": [th_t[s] for s in slots], "S_f64_nm2": r["S_f64"],
                      "J_rel": r["J_rel"], "status": r["status"]}
     return out
@@ -790,7 +804,7 @@ def run_ours(args):
             "batched_inversion": c3,
             "polished_inversion": c4,
             "fe_inversion": c5,
-            "paper_force_laws": f2,
+            "paper_experiments": f2,
             "image_warm_start": f1,
         }
         print(json.dumps(out))
@@ -940,7 +954,7 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the 4096-pixel batched inversion")
     ap.add_argument("--no-c4", action="store_true", help="skip the polished-inversion comparison")
     ap.add_argument("--no-c5", action="store_true", help="skip the finite-element inversion")
-    ap.add_argument("--no-f2", action="store_true", help="skip the paper's Hooke / spring-damper inversions")
+    ap.add_argument("--no-f2", action="store_true", help="skip the paper's own experiments (tip-sample laws, base motion)")
     ap.add_argument("--no-image", action="store_true", help="skip the image warm-start comparison")
     ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint", "fe", "sens", "polish"],
                     default=None,

@@ -43,6 +43,7 @@ extern "C" {
 
 #define AFM_MAX_MODES 8
 #define AFM_MAX_PARAMS 5
+#define AFM_DRIVE_SLOT 5        /* slots 5, 6, 7: base amplitude, frequency, chirp rate */
 #define AFM_MAX_SPC 2048
 
 typedef enum {
@@ -101,6 +102,16 @@ typedef struct {
     double lo[AFM_MAX_PARAMS];  /* bounds of free dimension d (SI)                 */
     double hi[AFM_MAX_PARAMS];
     int log_scale[AFM_MAX_PARAMS];  /* 1: log10-uniform map, 0: linear             */
+    /* Base motion.  drive_mode 0: driven at f1_hz with free tip amplitude A0_m,
+     * starting on that free steady state (steps_per_cycle sets the step).
+     * drive_mode 1 (base-motion inversion, Sec. 4.1): y_b(t) = a sin(2 pi
+     * (f t + g t^2)) starting at rest, step dt_s; a, f, g are slots 5, 6, 7
+     * of slot[] (free) or drive_a_m, drive_f_hz, drive_g_hz_s (fixed); in
+     * this mode only afm_forward_batch(_f64) and afm_invert run, on modal
+     * models, and steps_per_cycle and A0_m are not used. */
+    int drive_mode;
+    double dt_s;
+    double drive_a_m, drive_f_hz, drive_g_hz_s;
 } afm_problem;
 
 /* Particle-swarm settings (Sec. 3.4, Eq. 8). */
@@ -144,6 +155,7 @@ typedef struct {
     double defect;
     int32_t segments;
     int32_t reserved;               /* 0                                          */
+    double drive[3];                /* drive_mode 1: the winner's a [m], f [Hz], g [Hz/s]; else 0 */
 } afm_result;
 
 typedef struct afm_ctx afm_ctx;

@@ -40,7 +40,9 @@ class Problem(C.Structure):
                 ("n_steps", C.c_int), ("force", C.c_int), ("fixed", C.c_double * MAX_PARAMS),
                 ("n_free", C.c_int), ("slot", C.c_int * MAX_PARAMS),
                 ("lo", C.c_double * MAX_PARAMS), ("hi", C.c_double * MAX_PARAMS),
-                ("log_scale", C.c_int * MAX_PARAMS)]
+                ("log_scale", C.c_int * MAX_PARAMS), ("drive_mode", C.c_int),
+                ("dt_s", C.c_double), ("drive_a_m", C.c_double), ("drive_f_hz", C.c_double),
+                ("drive_g_hz_s", C.c_double)]
 
 
 class PsoCfg(C.Structure):
@@ -71,7 +73,7 @@ class Result(C.Structure):
                 ("S", C.c_double), ("S_f64", C.c_double), ("J_rel", C.c_double),
                 ("iters", C.c_int32), ("winner", C.c_int32), ("nonfinite", C.c_int32),
                 ("status", C.c_int32), ("defect", C.c_double), ("segments", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("drive", C.c_double * 3)]
 
 
 class AfmError(RuntimeError):
@@ -205,9 +207,9 @@ def make_problem(spec: dict, n_steps: int | None = None) -> Problem:
     p.newmark_beta = float(spec.get("newmark_beta", 0.25))
     p.A0_m = float(spec["A0"])
     p.Zc_m = float(spec["Zc"])
-    p.steps_per_cycle = int(spec["spc"])
+    p.steps_per_cycle = int(spec.get("spc", 0))
     if n_steps is None:
-        n_steps = int(spec["cycles"]) * int(spec["spc"])
+        n_steps = int(spec["n_steps"]) if "n_steps" in spec else int(spec["cycles"]) * int(spec["spc"])
     p.n_steps = int(n_steps)
     p.force = _FORCE[spec["force"]]
     for s in range(MAX_PARAMS):
@@ -219,6 +221,10 @@ def make_problem(spec: dict, n_steps: int | None = None) -> Problem:
         p.lo[dd] = float(lo)
         p.hi[dd] = float(hi)
         p.log_scale[dd] = int(bool(lg))
+    if spec.get("drive") == "chirp":          # base-motion inversion from rest
+        p.drive_mode = 1
+        p.dt_s = float(spec["dt"])
+        p.drive_a_m, p.drive_f_hz, p.drive_g_hz_s = (float(v) for v in spec["drive_params"])
     return p
 
 
@@ -593,7 +599,7 @@ def decode_result(result_bytes) -> dict:
     r = Result.from_buffer_copy(raw[:C.sizeof(Result)])
     return dict(x=np.array(r.x[:]), theta=np.array(r.theta[:]), S=r.S, S_f64=r.S_f64,
                 J_rel=r.J_rel, iters=r.iters, winner=r.winner, nonfinite=r.nonfinite,
-                status=r.status, defect=r.defect, segments=r.segments)
+                status=r.status, defect=r.defect, segments=r.segments, drive=np.array(r.drive[:]))
 
 
 def synth_records(prob: Problem, x_truth, off, sub: int, sigma_m: float, seed: int,

@@ -84,6 +84,7 @@ __device__ __forceinline__ Coef<T> make_coef(const KConst<T>& K, const X* xd) {
 #pragma unroll
     for (int s = 0; s < AFM_MAXD; ++s) th[s] = K.fixed[s];
     for (int d = 0; d < K.D; ++d) {
+        if (K.slot[d] >= AFM_MAXD) continue;   // base-motion slot (kern_drive.cu)
         double v = K.lo[d] + (double)xd[d] * K.span[d];
         v = K.logs[d] ? exp10(v) : v;
         th[K.slot[d]] = v;

@@ -46,6 +46,8 @@ struct KConst {
     int slot[AFM_MAXD], logs[AFM_MAXD];
     double lo[AFM_MAXD], span[AFM_MAXD], fixed[AFM_MAXD];
     double k, s1, tau;
+    int drive_mode;                 // 1: per-particle base motion from rest (kern_drive.cu)
+    double drv[3];                  // fixed base amplitude [m], frequency [Hz], chirp [Hz/s]
 };
 
 // Finite-element cantilever (cubic Hermite elements, clamped node removed)

@@ -142,7 +142,8 @@ void fill_kconst(const afm_problem& pr, int spc, int n_steps, KConst<T>& K) {
     Setup s;
     modal_setup(pr, spc, s);
     std::memset(&K, 0, sizeof(K));
-    const double tau = s.h / 6.0, nm = 1e-9;
+    const bool drv = pr.drive_mode == 1;
+    const double tau = (drv ? pr.dt_s : s.h) / 6.0, nm = 1e-9;
     const double w1t = s.w[0] * tau;
     for (int i = 0; i < AFM_MAXM; ++i) {
         if (i < s.m) {
@@ -152,8 +153,8 @@ void fill_kconst(const afm_problem& pr, int spc, int n_steps, KConst<T>& K) {
             K.wq[i] = (T)(s.w[i] * tau / pr.Q[i]);
             K.gam[i] = (T)s.gam[i];
             K.tip[i] = (T)1;
-            K.q0[i] = (T)(s.q0[i] / nm);
-            K.v0[i] = (T)(s.v0[i] * tau / nm);
+            K.q0[i] = drv ? (T)0 : (T)(s.q0[i] / nm);        // drive mode 1 starts at rest
+            K.v0[i] = drv ? (T)0 : (T)(s.v0[i] * tau / nm);
         }
     }
     K.Zc = (T)(pr.Zc_m / nm);
@@ -179,6 +180,10 @@ void fill_kconst(const afm_problem& pr, int spc, int n_steps, KConst<T>& K) {
     K.k = pr.k_N_per_m;
     K.s1 = w1t * w1t;
     K.tau = tau;
+    K.drive_mode = drv ? 1 : 0;
+    K.drv[0] = pr.drive_a_m;
+    K.drv[1] = pr.drive_f_hz;
+    K.drv[2] = pr.drive_g_hz_s;
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
@@ -460,11 +465,20 @@ afm_status check_problem(const afm_problem* pr) {
     if (!finite_pos(pr->k_N_per_m)) return fail(AFM_ERR_INVALID_ARG, "k_N_per_m must be > 0");
     for (int i = 0; i < m; ++i)
         if (!finite_pos(pr->Q[i])) return fail(AFM_ERR_INVALID_ARG, "Q[%d] must be > 0", i);
-    if (!finite_pos(pr->A0_m)) return fail(AFM_ERR_INVALID_ARG, "A0_m must be > 0");
+    const bool drv = pr->drive_mode == 1;
+    if (pr->drive_mode != 0 && !drv)
+        return fail(AFM_ERR_INVALID_ARG, "drive_mode %d is neither 0 nor 1", pr->drive_mode);
+    if (drv) {
+        if (pr->model == AFM_FE_HERMITE)
+            return fail(AFM_ERR_UNSUPPORTED, "drive_mode 1 runs on the modal models");
+        if (!finite_pos(pr->dt_s)) return fail(AFM_ERR_INVALID_ARG, "drive_mode 1 needs dt_s > 0");
+    } else {
+        if (!finite_pos(pr->A0_m)) return fail(AFM_ERR_INVALID_ARG, "A0_m must be > 0");
+        if (pr->steps_per_cycle < 4 || pr->steps_per_cycle > AFM_TAB_MAX / 2)
+            return fail(AFM_ERR_INVALID_ARG, "steps_per_cycle %d outside 4..%d",
+                        pr->steps_per_cycle, AFM_TAB_MAX / 2);
+    }
     if (!std::isfinite(pr->Zc_m)) return fail(AFM_ERR_INVALID_ARG, "Zc_m must be finite");
-    if (pr->steps_per_cycle < 4 || pr->steps_per_cycle > AFM_TAB_MAX / 2)
-        return fail(AFM_ERR_INVALID_ARG, "steps_per_cycle %d outside 4..%d", pr->steps_per_cycle,
-                    AFM_TAB_MAX / 2);
     if (pr->n_steps < 1) return fail(AFM_ERR_INVALID_ARG, "n_steps must be >= 1");
     if (pr->force < AFM_LINEAR_SPRING || pr->force > AFM_SPRING_DAMPER)
         return fail(AFM_ERR_INVALID_ARG, "unknown force %d", pr->force);
@@ -473,7 +487,8 @@ afm_status check_problem(const afm_problem* pr) {
     int used = 0;
     for (int d = 0; d < pr->n_free; ++d) {
         int s = pr->slot[d];
-        if (s < 0 || s >= AFM_MAX_PARAMS || (used >> s) & 1)
+        const int n_slots = drv ? AFM_DRIVE_SLOT + 3 : AFM_MAX_PARAMS;
+        if (s < 0 || s >= n_slots || (used >> s) & 1)
             return fail(AFM_ERR_INVALID_ARG, "slot[%d] = %d invalid or repeated", d, s);
         used |= 1 << s;
         if (!std::isfinite(pr->lo[d]) || !std::isfinite(pr->hi[d]) || !(pr->lo[d] < pr->hi[d]))
@@ -484,6 +499,9 @@ afm_status check_problem(const afm_problem* pr) {
     for (int s = 0; s < AFM_MAX_PARAMS; ++s)
         if (!((used >> s) & 1) && !std::isfinite(pr->fixed[s]))
             return fail(AFM_ERR_INVALID_ARG, "fixed[%d] must be finite", s);
+    if (drv && !(std::isfinite(pr->drive_a_m) && std::isfinite(pr->drive_f_hz) &&
+                 std::isfinite(pr->drive_g_hz_s)))
+        return fail(AFM_ERR_INVALID_ARG, "drive_a_m, drive_f_hz, drive_g_hz_s must be finite");
     if (pr->force == AFM_DMT || pr->force == AFM_DMT_KV) {
         // R (slot 2) and a0 (slot 3) must stay positive everywhere in the box
         for (int s = 2; s <= 3; ++s) {
@@ -503,6 +521,8 @@ afm_status check_problem(const afm_problem* pr) {
 afm_status modal_only(const afm_problem* pr, const char* what) {
     if (pr->model == AFM_FE_HERMITE)
         return fail(AFM_ERR_UNSUPPORTED, "%s: the FE beam runs in afm_forward_batch(_f64) and afm_invert", what);
+    if (pr->drive_mode != 0)
+        return fail(AFM_ERR_UNSUPPORTED, "%s: drive_mode 1 runs in afm_forward_batch(_f64) and afm_invert", what);
     return AFM_OK;
 }
 
@@ -586,7 +606,7 @@ InvLayout invert_layout(int P, int D) {
 int problem_modes(const afm_problem& pr) { return pr.model == AFM_POINT_MASS ? 1 : pr.n_modes; }
 
 size_t reeval_extra(const afm_problem& pr) {
-    if (pr.model == AFM_FE_HERMITE) return 0;
+    if (pr.model == AFM_FE_HERMITE || pr.drive_mode != 0) return 0;
     const int m = problem_modes(pr);
     if (!afm::reeval_supported(m, pr.n_steps)) return 0;
     return afm::reeval_bytes(m, pr.n_steps, pr.steps_per_cycle);
@@ -805,6 +825,11 @@ afm_status afm_forward_batch(afm_ctx* ctx, const afm_problem* prob, const float*
     }
     KConst<float> K;
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K);
+    if (prob->drive_mode == 1) {
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_drive_f32(K, x, P, defl, U, S, s); }),
+                 "drive forward kernel");
+        return AFM_OK;
+    }
     AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_f32(K, x, P, defl, U, S, nullptr, s); }),
              "forward kernel");
     return AFM_OK;
@@ -829,6 +854,10 @@ afm_status afm_forward_batch_f64(afm_ctx* ctx, const afm_problem* prob, const do
     }
     KConst<double> K;
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K);
+    if (prob->drive_mode == 1) {
+        AFM_CUDA(afm::launch_forward_drive_f64(K, x, P, defl, U, S, s), "drive forward f64 kernel");
+        return AFM_OK;
+    }
     AFM_CUDA(afm::launch_forward_f64(K, x, P, defl, U, S, nullptr, s), "forward f64 kernel");
     return AFM_OK;
 }
@@ -947,6 +976,13 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kf);
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, Kd);
     AFM_CUDA(afm::launch_pso_init(pc, sw, s), "pso init kernel");
+    if (prob->drive_mode == 1) {
+        for (int it = 0; it <= cfg->iters; ++it)
+            AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_invert_drive(Kf, pc, sw, U, history, it, s); }),
+                     "drive inversion kernel");
+        AFM_CUDA(afm::launch_drive_final(Kd, pc, sw, U, history, result, s), "drive final kernel");
+        return AFM_OK;
+    }
     for (int it = 0; it <= cfg->iters; ++it)
         AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_invert_iter(Kf, pc, sw, U, history, it, s); }),
                  "invert iteration kernel");

@@ -220,6 +220,7 @@ __global__ void batch_final_kernel(const KConst<double> K, const PsoConst pc, co
     r->defect = 0.0;
     r->segments = 0;
     r->reserved = 0;
+    for (int k = 0; k < 3; ++k) r->drive[k] = 0.0;
 }
 
 

@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
         res->defect = 0.0;
         res->segments = 0;
         res->reserved = 0;
+        for (int k = 0; k < 3; ++k) res->drive[k] = 0.0;
     }
 }
 

@@ -253,6 +253,7 @@ __global__ void invert_final_kernel(const KConst<double> K, const PsoConst pc, S
     res->defect = 0.0;
     res->segments = 0;
     res->reserved = 0;
+    for (int k = 0; k < 3; ++k) res->drive[k] = 0.0;
 }
 
 cudaError_t launch_invert_final(const KConst<double>& K, const PsoConst& pc, const SwarmPtrs& sw,

@@ -159,6 +159,7 @@ __global__ void polish_final_kernel(const KConst<double> K, int Kn, int iters,
     res->defect = 0.0;
     res->segments = 0;
     res->reserved = 0;
+    for (int k = 0; k < 3; ++k) res->drive[k] = 0.0;
 }
 
 cudaError_t launch_polish_cand(int D, int K, int J, const float* x, const float* G, double alpha0,

@@ -475,6 +475,7 @@ __global__ void __launch_bounds__(256) reeval_final_kernel(const KConst<double> 
     res->defect = segs > 0 ? defect : (defect <= kDefectTol ? 0.0 : defect);
     res->segments = segs;
     res->reserved = 0;
+    for (int k = 0; k < 3; ++k) res->drive[k] = 0.0;
 }
 
 // ---------------------------------------------------------------------------

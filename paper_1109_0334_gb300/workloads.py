@@ -94,8 +94,28 @@ WORKLOADS["f1_image"] = dict(
     fine=dict(P=64, iters=0, polish_k=4, polish_steps=6),             # the others
     seed=SEED_BASE + 8, **_CANTILEVER, **_PSO)
 
+# The paper's base-motion inversions (Sec. 4.1): App. A cantilever, 8 modes,
+# no tip force, base y_b = a sin(2 pi (f t + g t^2)) from rest, step 1e-7 s,
+# 1000 steps; truths a = 2 nm, f = 25 600 Hz (sine) or f = 10 kHz,
+# g = 2e7 Hz/s (chirp); the paper's search boxes.  Noise 0.5 % of a.
+_DRV = dict(model="modal_eb", n_modes=8, spc=400, drive="chirp", dt=1e-7, n_steps=1000,
+            force="linear_spring", fixed=[0.0, 0.0, 0.0, 0.0, 0.0], P=512, iters=30,
+            sigma=0.005 * 2e-9, **_APPA, **_PSO)
+_DA = (5, 0.0, 100e-9, False)          # base amplitude [m]
+WORKLOADS["f3_amp"] = dict(
+    name="App. A cantilever, 8 modes, base amplitude (1-D), 512 x 30",
+    free=[_DA], drive_params=(2e-9, 25600.0, 0.0), x_truth=[0.02], seed=SEED_BASE + 9, **_DRV)
+WORKLOADS["f3_amp_freq"] = dict(
+    name="App. A cantilever, 8 modes, base amplitude and frequency (2-D), 512 x 30",
+    free=[_DA, (6, 25100.0, 26100.0, False)], drive_params=(2e-9, 25600.0, 0.0),
+    x_truth=[0.02, 0.5], seed=SEED_BASE + 10, **_DRV)
+WORKLOADS["f3_chirp"] = dict(
+    name="App. A cantilever, 8 modes, chirp (a, f, g) (3-D), 512 x 30",
+    free=[_DA, (6, 7500.0, 12500.0, False), (7, 1.9e7, 2.1e7, False)],
+    drive_params=(2e-9, 1e4, 2e7), x_truth=[0.02, 0.5, 0.5], seed=SEED_BASE + 11, **_DRV)
+
 for _w in WORKLOADS.values():
-    _w["sigma"] = 0.005 * _w["A0"]    # 0.5 % of the free amplitude
+    _w.setdefault("sigma", 0.005 * _w["A0"])    # 0.5 % of the free amplitude
     _w["record_sub"] = 4
 
 
@@ -107,6 +127,8 @@ def get(name: str, **overrides) -> dict:
 
 
 def n_steps(w: dict) -> int:
+    if "n_steps" in w:
+        return int(w["n_steps"])
     cyc = w["cycles"]
     if isinstance(cyc, (tuple, list)):
         raise ValueError("per-pixel record lengths: use the pixel's own cycle count")
