@@ -282,6 +282,17 @@ int orc_forward(const orc_case* c, const double th[ORC_NSLOT], int n_steps, int 
     orc_modal md;
     if (orc_setup(&cf, &md)) return -1;
     int m = md.m, n2 = 2 * m;
+    /* deflection points: tip-normalised mode shapes phi_i(xi_k) */
+    int np = c->n_points;
+    double phi[4][ORC_MAXM];
+    if (np < 0 || np > 4 || (np > 0 && c->model != ORC_MODAL_EB)) return -1;
+    if (np > 0) {
+        double bL[ORC_MAXM], gam[ORC_MAXM];
+        if (orc_modal_factors(m, 501, bL, gam, NULL, NULL)) return -1;
+        for (int k = 0; k < np; ++k)
+            for (int i = 0; i < m; ++i)
+                phi[k][i] = orc_mode_shape(bL[i], c->point_xi[k]) / orc_mode_shape(bL[i], 1.0);
+    }
     double y[2 * ORC_MAXM], k1[2 * ORC_MAXM], k2[2 * ORC_MAXM], k3[2 * ORC_MAXM],
         k4[2 * ORC_MAXM], yt[2 * ORC_MAXM];
     for (int i = 0; i < m; ++i) { y[i] = md.eta0[i]; y[m + i] = md.etad0[i]; }
@@ -311,9 +322,17 @@ int orc_forward(const orc_case* c, const double th[ORC_NSLOT], int n_steps, int 
             for (int q = 0; q < n2; ++q)
                 y[q] = y[q] + (h / 6.0) * (k1[q] + 2.0 * k2[q] + 2.0 * k3[q] + k4[q]);
         }
-        double tip = 0.0;
-        for (int i = 0; i < m; ++i) tip += y[i];
-        u[n] = tip;
+        if (np > 0) {
+            for (int k = 0; k < np; ++k) {
+                double uk = 0.0;
+                for (int i = 0; i < m; ++i) uk += phi[k][i] * y[i];
+                u[(size_t)n * np + k] = uk;
+            }
+        } else {
+            double tip = 0.0;
+            for (int i = 0; i < m; ++i) tip += y[i];
+            u[n] = tip;
+        }
         if (state) memcpy(state + (size_t)(n + 1) * n2, y, sizeof(double) * n2);
     }
     return 0;
@@ -347,7 +366,7 @@ int orc_fe_forward(const orc_case* c, const double th[ORC_NSLOT], int n_steps, i
 
 static int forward_any(const orc_case* c, const double th[ORC_NSLOT], int n, double* u)
 {
-    if (c->model == ORC_FE_HERMITE) return orc_fe_forward(c, th, n, 1, u, NULL);
+    if (c->model == ORC_FE_HERMITE) return c->n_points ? -1 : orc_fe_forward(c, th, n, 1, u, NULL);
     return orc_forward(c, th, n, 1, u, NULL);
 }
 
@@ -356,9 +375,10 @@ int orc_misfit_x(const orc_case* c, const orc_pmap* pm, const double* x,
 {
     double th[ORC_NSLOT];
     orc_map(pm, x, th);
-    double* u = (double*)malloc(sizeof(double) * n);
+    const int nv = n * (c->n_points > 0 ? c->n_points : 1);   /* record values */
+    double* u = (double*)malloc(sizeof(double) * nv);
     int rc = forward_any(c, th, n, u);
-    *S = rc ? INFINITY : orc_misfit(U, u, n);
+    *S = rc ? INFINITY : orc_misfit(U, u, nv);
     free(u);
     return rc;
 }
@@ -506,7 +526,8 @@ int orc_record(const orc_case* c, const orc_pmap* pm, const double* x, int n,
     if (rc) return -1;
     if (sigma > 0.0) {
         uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
-        for (int j = 0; j < n; ++j) {
+        const int nv = n * (c->n_points > 0 ? c->n_points : 1);   /* record values */
+        for (int j = 0; j < nv; ++j) {
             uint32_t ctr[4] = {(uint32_t)(j / 2), 0, pixel, 4u << 16};
             uint32_t out[4];
             orc_philox4x32_10(ctr, key, out);
@@ -523,7 +544,7 @@ int orc_record(const orc_case* c, const orc_pmap* pm, const double* x, int n,
 /* The complex-step paths cover the force-law slots of the steady drive. */
 static int complex_step_unsupported(const orc_case* c, const orc_pmap* pm)
 {
-    if (c->drive != 0) return 1;
+    if (c->drive != 0 || c->n_points != 0) return 1;
     for (int d = 0; d < pm->D; ++d)
         if (pm->slot[d] < 0 || pm->slot[d] >= 5) return 1;
     return 0;

@@ -91,6 +91,11 @@ typedef struct {
      * g) in slots 5..7, starting at rest (R18; modal models only) */
     int drive;
     double dt;            /* drive 1: step [s] (spc is not used)                 */
+    /* deflection points (reading R19): n_points = 0 records the tip only;
+     * n_points in 1..4 records the deflection at x = point_xi[k] L, the
+     * record then holding n_points values per step (step-major) */
+    int n_points;
+    double point_xi[4];
 } orc_case;
 
 /* Derived modal quantities (SI). */

@@ -52,7 +52,7 @@ class Case(C.Structure):
                 ("n_elem", C.c_int), ("L", C.c_double), ("E", C.c_double),
                 ("rho", C.c_double), ("fe_k", C.c_double), ("fe_f1", C.c_double),
                 ("fe_Q", C.c_double), ("nm_beta", C.c_double), ("drive", C.c_int),
-                ("dt", C.c_double)]
+                ("dt", C.c_double), ("n_points", C.c_int), ("point_xi", C.c_double * 4)]
 
 
 class Modal(C.Structure):
@@ -175,7 +175,16 @@ def make_case(spec: dict) -> Case:
     c.nm_beta = float(spec.get("newmark_beta", 0.25))
     c.drive = 1 if spec.get("drive") == "chirp" else 0
     c.dt = float(spec.get("dt", 0.0))
+    pts = spec.get("points", ())
+    c.n_points = len(pts)
+    for k, xi in enumerate(pts):
+        c.point_xi[k] = float(xi)
     return c
+
+
+def n_values(case: Case) -> int:
+    """Record values per step: the deflection points, else the tip."""
+    return max(int(case.n_points), 1)
 
 
 def make_pmap(spec: dict) -> Pmap:
@@ -240,7 +249,7 @@ def force(kind: int, th, d: float, ddot: float = 0.0) -> float:
 
 def forward(case: Case, th, n_steps: int, sub: int = 1, want_state: bool = False):
     th = np.ascontiguousarray(th, dtype=np.float64)
-    u = np.zeros(n_steps)
+    u = np.zeros(n_steps * n_values(case))
     m = 1 if case.model == POINT_MASS else case.n_modes
     st = np.zeros((n_steps + 1, 2 * m)) if want_state else None
     rc = lib().orc_forward(C.byref(case), th, int(n_steps), int(sub), u,
@@ -268,7 +277,7 @@ def misfit_batch(case: Case, pm: Pmap, x_dp, U) -> np.ndarray:
     assert D == pm.D
     U = np.ascontiguousarray(U, dtype=np.float64)
     S = np.zeros(P)
-    lib().orc_misfit_batch(C.byref(case), C.byref(pm), x, P, U, len(U), S)
+    lib().orc_misfit_batch(C.byref(case), C.byref(pm), x, P, U, len(U) // n_values(case), S)
     return S
 
 
@@ -297,7 +306,8 @@ def invert(case: Case, pm: Pmap, U, P: int, iters: int, w: float, c1: float, c2:
     bx = np.zeros(pm.D)
     bS = C.c_double()
     hist = np.zeros(iters + 1)
-    lib().orc_invert(C.byref(case), C.byref(pm), U, len(U), C.byref(cfg), bx, C.byref(bS), hist)
+    lib().orc_invert(C.byref(case), C.byref(pm), U, len(U) // n_values(case), C.byref(cfg), bx,
+                     C.byref(bS), hist)
     return bx, bS.value, hist
 
 
@@ -311,7 +321,7 @@ def invert_boxed(case: Case, pm: Pmap, U, P: int, iters: int, w: float, c1: floa
     sd = np.ascontiguousarray(sd.reshape(-1, pm.D))
     bx = np.zeros(pm.D)
     bS = C.c_double()
-    rc = lib().orc_invert_boxed(C.byref(case), C.byref(pm), U, len(U), C.byref(cfg),
+    rc = lib().orc_invert_boxed(C.byref(case), C.byref(pm), U, len(U) // n_values(case), C.byref(cfg),
                                 np.ascontiguousarray(lo, dtype=np.float64),
                                 np.ascontiguousarray(hi, dtype=np.float64),
                                 sd if len(sd) else np.zeros(pm.D), len(sd), bx, C.byref(bS))
@@ -332,7 +342,7 @@ def cycles(seed: int, pixel: int, lo: int, hi: int) -> int:
 
 def record(case: Case, pm: Pmap, x, n: int, sub: int, sigma: float, seed: int,
            pixel: int = 0) -> np.ndarray:
-    U = np.zeros(n)
+    U = np.zeros(n * n_values(case))
     rc = lib().orc_record(C.byref(case), C.byref(pm), np.ascontiguousarray(x, dtype=np.float64),
                           n, sub, sigma, seed, pixel, U)
     if rc:

@@ -565,6 +565,49 @@ def test_polish_descends_to_a_stationary_point(orc):
 
 
 # --------------------------------------------------------------------------
+# Deflection points along the cantilever (reading R19)
+# --------------------------------------------------------------------------
+def _textbook_shape(bL, xi):
+    """Clamped-free Euler-Bernoulli mode shape, cosh - cos - s (sinh - sin),
+    normalised to 1 at the tip (moderate bL only)."""
+    s = (np.cosh(bL) + np.cos(bL)) / (np.sinh(bL) + np.sin(bL))
+    f = lambda z: np.cosh(bL * z) - np.cos(bL * z) - s * (np.sinh(bL * z) - np.sin(bL * z))
+    return f(xi) / f(1.0)
+
+
+def test_points_single_tip_point_is_the_tip_record(orc):
+    w = W.get("c2", cycles=6)
+    c, pm = orc.make_case(w), orc.make_pmap(w)
+    cp = orc.make_case(dict(w, points=(1.0,)))
+    th = orc.map_x(pm, np.full(4, 0.5))
+    n = W.n_steps(w)
+    np.testing.assert_allclose(orc.forward(cp, th, n), orc.forward(c, th, n), rtol=1e-14,
+                               atol=1e-14 * np.max(np.abs(orc.forward(c, th, n))))
+
+
+def test_points_free_steady_state_closed_form(orc):
+    """No tip force: the cantilever stays on its free steady state, whose
+    deflection at x = xi L is sum_i phi_i(xi) Im(a w^2 H_i e^{i (w t + psi)})
+    with the textbook mode shapes."""
+    w = W.get("c2", cycles=4, force="linear_spring", fixed=[0.0] * 5,
+              free=[(0, 1.0, 2.0, False)], points=(1 / 3, 2 / 3, 1.0))
+    c, pm = orc.make_case(w), orc.make_pmap(w)
+    md = orc.setup(c)
+    n = W.n_steps(w)
+    th = orc.map_x(pm, np.array([0.5]))
+    th[0] = 0.0                                     # spring constant 0: no tip force
+    u = orc.forward(c, th, n).reshape(n, 3)
+    m, wd = 3, md.wd
+    bL = [orc.beam_root(i + 1) for i in range(m)]      # roots are numbered from 1
+    t = np.arange(1, n + 1) * md.dt
+    Hs = [md.gam[i] / (md.w[i] ** 2 - wd ** 2 + 1j * wd * md.w[i] / 400.0) for i in range(m)]
+    for k, xi in enumerate((1 / 3, 2 / 3, 1.0)):
+        exact = sum(_textbook_shape(bL[i], xi) *
+                    np.imag(md.a * wd ** 2 * Hs[i] * np.exp(1j * (wd * t + md.psi))) for i in range(m))
+        assert np.max(np.abs(u[:, k] - exact)) <= 1e-6 * np.max(np.abs(exact))
+
+
+# --------------------------------------------------------------------------
 # Base-motion inversion: drive mode 1, y_b = a sin(2 pi (f t + g t^2)) from rest
 # (reading R18)
 # --------------------------------------------------------------------------
