@@ -578,6 +578,46 @@ def run_image(A, W, dev, flush):
 
 
 # ---------------------------------------------------------------------------
+# Deflection points along the cantilever (the paper's n_dp = 3)
+# ---------------------------------------------------------------------------
+def run_points(A, W, dev, flush):
+    """The same seeded cantilever and truth inverted from the tip record and
+    from records at L/3, 2L/3 and L (records: FP64 forward at dt/4, every
+    4th sample, plus noise)."""
+    import numpy as np
+    import torch
+    spec = W.get("f4_points")
+    D, N, npt = len(spec["free"]), W.n_steps(spec), len(spec["points"])
+    rng = np.random.default_rng(spec["seed"])
+    xt = rng.uniform(0.1, 0.9, size=(D, 1))
+    fine = A.make_problem(dict(spec, spc=spec["spc"] * 4), n_steps=4 * N)
+    d, _ = A.forward_batch_f64(fine, torch.from_numpy(xt).to(dev), None)
+    gen = torch.Generator(device=dev).manual_seed(spec["seed"])
+    rec = d.reshape(4 * N, npt)[3::4].float()
+    rec = (rec + (spec["sigma"] / 1e-9) * torch.randn(rec.shape, device=dev, generator=gen)).contiguous()
+    th_t = _theta_of(spec, xt[:, 0])
+    out = {"workload": spec["name"]}
+    for label, sp, U in (("tip_only", dict(spec, points=()), rec[:, -1].contiguous()),
+                         ("three_points", spec, rec.reshape(-1))):
+        prob = A.make_problem(sp)
+        cfg = A.make_pso(sp)
+        A.invert(prob, U, cfg)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res, _ = A.invert(prob, U, cfg)
+        e1.record()
+        e1.synchronize()
+        r = A.decode_result(res)
+        out[label] = {"ms_per_inversion": e0.elapsed_time(e1), "record_values": int(U.numel()),
+                      "ident_rel_err_vs_truth": ident_errors(list(r["theta"]), th_t)[:3],
+                      "S_f64_nm2": r["S_f64"], "status": r["status"]}
+    out["ident"] = "H R, E* sqrt(R), a0"
+    return out
+
+
+# ---------------------------------------------------------------------------
 # The paper's own experiments (App. A cantilever, 8 modes)
 # ---------------------------------------------------------------------------
 def run_paper_laws(A, W, dev, flush):
@@ -773,6 +813,9 @@ def run_ours(args):
     f1 = None
     if not args.no_image:
         f1 = run_image(A, W, dev, flush)
+    f4 = None
+    if not args.no_points:
+        f4 = run_points(A, W, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -806,6 +849,7 @@ def run_ours(args):
             "fe_inversion": c5,
             "paper_experiments": f2,
             "image_warm_start": f1,
+            "deflection_points": f4,
         }
         print(json.dumps(out))
     if world > 1:
@@ -956,6 +1000,7 @@ def main():
     ap.add_argument("--no-c5", action="store_true", help="skip the finite-element inversion")
     ap.add_argument("--no-f2", action="store_true", help="skip the paper's own experiments (tip-sample laws, base motion)")
     ap.add_argument("--no-image", action="store_true", help="skip the image warm-start comparison")
+    ap.add_argument("--no-points", action="store_true", help="skip the deflection-points inversion")
     ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint", "fe", "sens", "polish"],
                     default=None,
                     help="run one small untimed case for a profiler capture and exit")

@@ -44,6 +44,7 @@ extern "C" {
 #define AFM_MAX_MODES 8
 #define AFM_MAX_PARAMS 5
 #define AFM_DRIVE_SLOT 5        /* slots 5, 6, 7: base amplitude, frequency, chirp rate */
+#define AFM_MAX_POINTS 4        /* deflection points along the cantilever */
 #define AFM_MAX_SPC 2048
 
 typedef enum {
@@ -112,6 +113,13 @@ typedef struct {
     int drive_mode;
     double dt_s;
     double drive_a_m, drive_f_hz, drive_g_hz_s;
+    /* Deflection points (the paper's n_dp, Sec. 3.2): n_points = 0 records
+     * the tip; n_points in 1..AFM_MAX_POINTS records the deflection at
+     * x = point_xi[k] * L (0 < xi <= 1, MODAL_EB, drive_mode 0): records U
+     * are then [n_steps][n_points] and deflection outputs [n_steps][n_points][P];
+     * only afm_forward_batch(_f64) and afm_invert run in this mode. */
+    int n_points;
+    double point_xi[AFM_MAX_POINTS];
 } afm_problem;
 
 /* Particle-swarm settings (Sec. 3.4, Eq. 8). */

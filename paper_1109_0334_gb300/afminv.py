@@ -21,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libafminv.so")
 
-MAX_MODES, MAX_PARAMS = 8, 5
+MAX_MODES, MAX_PARAMS, MAX_POINTS = 8, 5, 4
 POINT_MASS, MODAL_EB, FE_HERMITE = 0, 1, 2
 LINEAR_SPRING, DMT, DMT_KV, HOOKE, SPRING_DAMPER = 0, 1, 2, 3, 4
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
@@ -42,7 +42,8 @@ class Problem(C.Structure):
                 ("lo", C.c_double * MAX_PARAMS), ("hi", C.c_double * MAX_PARAMS),
                 ("log_scale", C.c_int * MAX_PARAMS), ("drive_mode", C.c_int),
                 ("dt_s", C.c_double), ("drive_a_m", C.c_double), ("drive_f_hz", C.c_double),
-                ("drive_g_hz_s", C.c_double)]
+                ("drive_g_hz_s", C.c_double), ("n_points", C.c_int),
+                ("point_xi", C.c_double * MAX_POINTS)]
 
 
 class PsoCfg(C.Structure):
@@ -225,7 +226,16 @@ def make_problem(spec: dict, n_steps: int | None = None) -> Problem:
         p.drive_mode = 1
         p.dt_s = float(spec["dt"])
         p.drive_a_m, p.drive_f_hz, p.drive_g_hz_s = (float(v) for v in spec["drive_params"])
+    pts = spec.get("points", ())                # deflection points x / L along the cantilever
+    p.n_points = len(pts)
+    for k, xi in enumerate(pts):
+        p.point_xi[k] = float(xi)
     return p
+
+
+def n_values(prob: Problem) -> int:
+    """Record values per step: the deflection points, else the tip."""
+    return max(int(prob.n_points), 1)
 
 
 def make_pso(spec: dict, pixel: int = 0) -> PsoCfg:
@@ -244,7 +254,8 @@ def forward_batch(prob: Problem, x, U=None, want_defl: bool = True, want_S: bool
     import torch
     P = int(x.shape[1]) if x.dim() == 2 else int(x.shape[0])
     dev = x.device
-    defl = torch.empty((prob.n_steps, P), dtype=torch.float32, device=dev) if want_defl else None
+    defl = torch.empty((prob.n_steps * n_values(prob), P), dtype=torch.float32, device=dev) \
+        if want_defl else None
     S = torch.empty(P, dtype=torch.float32, device=dev) if (want_S and U is not None) else None
     _check(lib().afm_forward_batch(context(dev.index), C.byref(prob), _ptr(x), P, _ptr(defl),
                                    _ptr(U), _ptr(S), _stream(stream)))
@@ -256,7 +267,8 @@ def forward_batch_f64(prob: Problem, x, U=None, want_defl: bool = True, want_S: 
     import torch
     P = int(x.shape[1]) if x.dim() == 2 else int(x.shape[0])
     dev = x.device
-    defl = torch.empty((prob.n_steps, P), dtype=torch.float64, device=dev) if want_defl else None
+    defl = torch.empty((prob.n_steps * n_values(prob), P), dtype=torch.float64, device=dev) \
+        if want_defl else None
     S = torch.empty(P, dtype=torch.float64, device=dev) if (want_S and U is not None) else None
     _check(lib().afm_forward_batch_f64(context(dev.index), C.byref(prob), _ptr(x), P, _ptr(defl),
                                        _ptr(U), _ptr(S), _stream(stream)))

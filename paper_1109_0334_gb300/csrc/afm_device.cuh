@@ -379,6 +379,41 @@ __device__ __forceinline__ T integrate(const KConst<T>& K, const Coef<T>& c, con
     return S;
 }
 
+// integrate() with the misfit over K.np deflection points per step (K.phi:
+// tip-normalised mode shapes at the points);
+// U is [n][np] (step-major), defl [n][np][P].
+template <typename T, int M, int FORCE, typename TU = T>
+__device__ __forceinline__ T integrate_points(const KConst<T>& K, const Coef<T>& c, const T* tab,
+                                              const TU* __restrict__ U, T* __restrict__ defl,
+                                              int P, int p, int n) {
+    T q[M], v[M], cq[M], cv[M];
+    init_state<T, M>(K, q, v, cq, cv);
+    T S = (T)0, cS = (T)0;
+    int j = 0;
+    const int spc2 = K.spc2, np = K.np;
+    for (int s = 0; s < n; ++s) {
+        const T g0 = tab[j], gh = tab[j + 1], g1 = tab[j + 2];
+        j += 2;
+        if (j >= spc2) j = 0;
+        rk4_step<T, M, FORCE>(K, c, q, v, cq, cv, g0, gh, g1);
+        for (int k = 0; k < np; ++k) {
+            T uk = K.phi[k][0] * q[0];
+#pragma unroll
+            for (int i = 1; i < M; ++i) uk = fma(K.phi[k][i], q[i], uk);
+            const size_t idx = (size_t)s * np + k;
+            if (defl != nullptr) defl[idx * P + p] = uk;
+            if (U != nullptr) {
+                const T r = (T)U[idx] - uk;
+                const T y = fma(r, r, -cS);
+                const T t = add_rn(S, y);
+                cS = sub_rn(sub_rn(t, S), y);
+                S = t;
+            }
+        }
+    }
+    return S;
+}
+
 // K particles per thread sharing the record and drive loads: the K
 // independent RK4 recurrences interleave in one instruction stream, which
 // hides the dependency latency of each.  Arithmetic per particle is the same

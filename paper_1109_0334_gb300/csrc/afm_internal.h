@@ -48,6 +48,8 @@ struct KConst {
     double k, s1, tau;
     int drive_mode;                 // 1: per-particle base motion from rest (kern_drive.cu)
     double drv[3];                  // fixed base amplitude [m], frequency [Hz], chirp [Hz/s]
+    int np;                         // deflection points (kern_points.cu), 0: the tip
+    T phi[4][AFM_MAXM];             // tip-normalised mode shapes at the points
 };
 
 // Finite-element cantilever (cubic Hermite elements, clamped node removed)

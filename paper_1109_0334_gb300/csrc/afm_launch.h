@@ -154,6 +154,15 @@ cudaError_t launch_invert_drive(const KConst<float>& K, const PsoConst& pc, cons
                                 const float* U, float* history, int it, cudaStream_t st);
 cudaError_t launch_drive_final(const KConst<double>& K, const PsoConst& pc, const SwarmPtrs& sw,
                                const float* U, float* history, void* result, cudaStream_t st);
+// deflections at several points along the cantilever (n_points > 0, kern_points.cu)
+cudaError_t launch_forward_points_f32(const KConst<float>& K, const float* x, int P, float* defl,
+                                      const float* U, float* S, cudaStream_t st);
+cudaError_t launch_forward_points_f64(const KConst<double>& K, const double* x, int P, double* defl,
+                                      const double* U, double* S, cudaStream_t st);
+cudaError_t launch_invert_points(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
+                                 const float* U, float* history, int it, cudaStream_t st);
+cudaError_t launch_points_final(const KConst<double>& K, const PsoConst& pc, const SwarmPtrs& sw,
+                                const float* U, float* history, void* result, cudaStream_t st);
 // winner re-evaluation in FP64 and result record
 cudaError_t launch_invert_final(const KConst<double>& K, const PsoConst& pc, const SwarmPtrs& sw,
                                 const float* U, float* history, void* result, cudaStream_t st);

@@ -95,6 +95,21 @@ double participation(int i, double b) {
     return 4.0 * sigma / b * ((i % 2 == 1) ? 1.0 : -1.0);
 }
 
+// Clamped-free mode shape of root b at xi = x / L, normalised to 1 at the
+// tip: cosh - cos - s (sinh - sin) with s = (cosh b + cos b) / (sinh b +
+// sin b), its growing exponentials combined so that nothing large cancels:
+// cosh z - s sinh z = ((1 - s) e^z + (1 + s) e^-z) / 2 with
+// 1 - s = (sin b - cos b - e^-b) / (sinh b + sin b).
+double shape_raw(double b, double xi) {
+    const double den = std::sinh(b) + std::sin(b);
+    const double s = (std::cosh(b) + std::cos(b)) / den;
+    const double oms = (std::sin(b) - std::cos(b) - std::exp(-b)) / den;
+    const double z = b * xi;
+    return 0.5 * oms * std::exp(z) + 0.5 * (1.0 + s) * std::exp(-z) - std::cos(z) + s * std::sin(z);
+}
+
+double shape_tip_normalised(double b, double xi) { return shape_raw(b, xi) / shape_raw(b, 1.0); }
+
 struct Setup {
     int m;
     double w[AFM_MAXM], gam[AFM_MAXM];
@@ -184,6 +199,10 @@ void fill_kconst(const afm_problem& pr, int spc, int n_steps, KConst<T>& K) {
     K.drv[0] = pr.drive_a_m;
     K.drv[1] = pr.drive_f_hz;
     K.drv[2] = pr.drive_g_hz_s;
+    K.np = pr.n_points;
+    for (int k = 0; k < pr.n_points && k < AFM_MAX_POINTS; ++k)
+        for (int i = 0; i < s.m; ++i)
+            K.phi[k][i] = (T)shape_tip_normalised(beam_root(i + 1), pr.point_xi[k]);
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
@@ -479,6 +498,15 @@ afm_status check_problem(const afm_problem* pr) {
                         pr->steps_per_cycle, AFM_TAB_MAX / 2);
     }
     if (!std::isfinite(pr->Zc_m)) return fail(AFM_ERR_INVALID_ARG, "Zc_m must be finite");
+    if (pr->n_points < 0 || pr->n_points > AFM_MAX_POINTS)
+        return fail(AFM_ERR_INVALID_ARG, "n_points %d outside 0..%d", pr->n_points, AFM_MAX_POINTS);
+    if (pr->n_points > 0) {
+        if (pr->model != AFM_MODAL_EB || drv)
+            return fail(AFM_ERR_UNSUPPORTED, "deflection points need MODAL_EB and drive_mode 0");
+        for (int k = 0; k < pr->n_points; ++k)
+            if (!(pr->point_xi[k] > 0.0 && pr->point_xi[k] <= 1.0))
+                return fail(AFM_ERR_INVALID_ARG, "point_xi[%d] outside (0, 1]", k);
+    }
     if (pr->n_steps < 1) return fail(AFM_ERR_INVALID_ARG, "n_steps must be >= 1");
     if (pr->force < AFM_LINEAR_SPRING || pr->force > AFM_SPRING_DAMPER)
         return fail(AFM_ERR_INVALID_ARG, "unknown force %d", pr->force);
@@ -523,6 +551,8 @@ afm_status modal_only(const afm_problem* pr, const char* what) {
         return fail(AFM_ERR_UNSUPPORTED, "%s: the FE beam runs in afm_forward_batch(_f64) and afm_invert", what);
     if (pr->drive_mode != 0)
         return fail(AFM_ERR_UNSUPPORTED, "%s: drive_mode 1 runs in afm_forward_batch(_f64) and afm_invert", what);
+    if (pr->n_points != 0)
+        return fail(AFM_ERR_UNSUPPORTED, "%s: deflection points run in afm_forward_batch(_f64) and afm_invert", what);
     return AFM_OK;
 }
 
@@ -830,6 +860,11 @@ afm_status afm_forward_batch(afm_ctx* ctx, const afm_problem* prob, const float*
                  "drive forward kernel");
         return AFM_OK;
     }
+    if (prob->n_points > 0) {
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_points_f32(K, x, P, defl, U, S, s); }),
+                 "points forward kernel");
+        return AFM_OK;
+    }
     AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_f32(K, x, P, defl, U, S, nullptr, s); }),
              "forward kernel");
     return AFM_OK;
@@ -856,6 +891,10 @@ afm_status afm_forward_batch_f64(afm_ctx* ctx, const afm_problem* prob, const do
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, K);
     if (prob->drive_mode == 1) {
         AFM_CUDA(afm::launch_forward_drive_f64(K, x, P, defl, U, S, s), "drive forward f64 kernel");
+        return AFM_OK;
+    }
+    if (prob->n_points > 0) {
+        AFM_CUDA(afm::launch_forward_points_f64(K, x, P, defl, U, S, s), "points forward f64 kernel");
         return AFM_OK;
     }
     AFM_CUDA(afm::launch_forward_f64(K, x, P, defl, U, S, nullptr, s), "forward f64 kernel");
@@ -984,7 +1023,10 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
         return AFM_OK;
     }
     for (int it = 0; it <= cfg->iters; ++it)
-        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_invert_iter(Kf, pc, sw, U, history, it, s); }),
+        AFM_CUDA(timed_launch(ctx, s, [&] {
+                     return prob->n_points > 0 ? afm::launch_invert_points(Kf, pc, sw, U, history, it, s)
+                                               : afm::launch_invert_iter(Kf, pc, sw, U, history, it, s);
+                 }),
                  "invert iteration kernel");
     if (reeval_extra(*prob) > 0) {
         afm::ReevalPtrs R;
@@ -994,7 +1036,10 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
                  "FP64 re-evaluation kernels");
         return AFM_OK;
     }
-    AFM_CUDA(afm::launch_invert_final(Kd, pc, sw, U, history, result, s), "invert final kernel");
+    if (prob->n_points > 0)
+        AFM_CUDA(afm::launch_points_final(Kd, pc, sw, U, history, result, s), "points final kernel");
+    else
+        AFM_CUDA(afm::launch_invert_final(Kd, pc, sw, U, history, result, s), "invert final kernel");
     return AFM_OK;
 }
 

@@ -73,32 +73,51 @@ cudaError_t batch_sort(const int64_t* off, int n_pix, int* order, cudaStream_t s
 
 int batch_sort_max() { return SORT_MAX; }
 
+// The kernels of each force law are instantiated in kern_batch_<law>.cu (so
+// that they compile in parallel); this file only calls their entry points.
+#define AFM_BATCH_DECLARE(F)                                                                   \
+    template <> cudaError_t batch_occupancy_of<F>(int, int, int, int, int, int*);              \
+    template <> cudaError_t batch_launch_of<F>(const KConst<float>&, const PsoConst&,          \
+                                               const BatchArgs&, int, int, cudaStream_t);      \
+    template <> cudaError_t batch_final_of<F>(const KConst<double>&, const PsoConst&,          \
+                                              const BatchArgs&, cudaStream_t);
+AFM_BATCH_DECLARE(F_LINEAR)
+AFM_BATCH_DECLARE(F_DMT)
+AFM_BATCH_DECLARE(F_DMT_KV)
+AFM_BATCH_DECLARE(F_HOOKE)
+AFM_BATCH_DECLARE(F_SPRING_DAMPER)
+#undef AFM_BATCH_DECLARE
+
 
 
 template <typename F>
 static cudaError_t by_force(int force, F&& f) {
     switch (force) {
-        case F_LINEAR: return f(BatchOps<F_LINEAR>{});
-        case F_DMT: return f(BatchOps<F_DMT>{});
-        case F_DMT_KV: return f(BatchOps<F_DMT_KV>{});
-        case F_HOOKE: return f(BatchOps<F_HOOKE>{});
-        case F_SPRING_DAMPER: return f(BatchOps<F_SPRING_DAMPER>{});
+        case F_LINEAR: return f(std::integral_constant<int, F_LINEAR>{});
+        case F_DMT: return f(std::integral_constant<int, F_DMT>{});
+        case F_DMT_KV: return f(std::integral_constant<int, F_DMT_KV>{});
+        case F_HOOKE: return f(std::integral_constant<int, F_HOOKE>{});
+        case F_SPRING_DAMPER: return f(std::integral_constant<int, F_SPRING_DAMPER>{});
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t batch_occupancy(int m, int force, int kp, int P, int D, int spc2, int* blocks_per_sm) {
-    return by_force(force, [&](auto ops) { return decltype(ops)::occupancy(m, kp, P, D, spc2, blocks_per_sm); });
+    return by_force(force, [&](auto Fc) {
+        return batch_occupancy_of<decltype(Fc)::value>(m, kp, P, D, spc2, blocks_per_sm);
+    });
 }
 
 cudaError_t launch_batch(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a, int kp,
                          int grid, cudaStream_t st) {
-    return by_force(K.force, [&](auto ops) { return decltype(ops)::launch(K, pc, a, kp, grid, st); });
+    return by_force(K.force, [&](auto Fc) {
+        return batch_launch_of<decltype(Fc)::value>(K, pc, a, kp, grid, st);
+    });
 }
 
 cudaError_t launch_batch_final(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
                                cudaStream_t st) {
-    return by_force(K.force, [&](auto ops) { return decltype(ops)::final_(K, pc, a, st); });
+    return by_force(K.force, [&](auto Fc) { return batch_final_of<decltype(Fc)::value>(K, pc, a, st); });
 }
 
 }  // namespace afm

@@ -291,10 +291,17 @@ struct BatchOps {
     }
 };
 
-extern template struct BatchOps<F_LINEAR>;
-extern template struct BatchOps<F_DMT>;
-extern template struct BatchOps<F_DMT_KV>;
-extern template struct BatchOps<F_HOOKE>;
-extern template struct BatchOps<F_SPRING_DAMPER>;
+
+// Per-force entry points, each defined (as an explicit specialization) in
+// its kern_batch_<law>.cu so that kern_batch.cu dispatches without
+// instantiating any kernel.
+template <int FORCE>
+cudaError_t batch_occupancy_of(int m, int kp, int P, int D, int spc2, int* blocks);
+template <int FORCE>
+cudaError_t batch_launch_of(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a, int kp,
+                            int grid, cudaStream_t st);
+template <int FORCE>
+cudaError_t batch_final_of(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
+                           cudaStream_t st);
 
 }  // namespace afm

@@ -1,7 +1,20 @@
-// kern_batch_sd.cu -- explicit instantiation of the batched inversion kernels for
+// kern_batch_sd.cu -- the batched inversion kernels instantiated for
 // F_SPRING_DAMPER (kept apart so the build compiles them in parallel).
 #include "kern_batch.cuh"
 
 namespace afm {
-template struct BatchOps<F_SPRING_DAMPER>;
+template <>
+cudaError_t batch_occupancy_of<F_SPRING_DAMPER>(int m, int kp, int P, int D, int spc2, int* blocks) {
+    return BatchOps<F_SPRING_DAMPER>::occupancy(m, kp, P, D, spc2, blocks);
+}
+template <>
+cudaError_t batch_launch_of<F_SPRING_DAMPER>(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a,
+                                  int kp, int grid, cudaStream_t st) {
+    return BatchOps<F_SPRING_DAMPER>::launch(K, pc, a, kp, grid, st);
+}
+template <>
+cudaError_t batch_final_of<F_SPRING_DAMPER>(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
+                                 cudaStream_t st) {
+    return BatchOps<F_SPRING_DAMPER>::final_(K, pc, a, st);
+}
 }  // namespace afm

@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(256) reeval_guess_kernel(const KConst<float> K
     build_drive_table(Kf, tabf);
     build_drive_table(Kd, R.tab);
     double acc = 0.0;
-    for (int n = threadIdx.x; n < Kd.n_steps; n += blockDim.x) acc += (double)U[n] * (double)U[n];
+    const int nv = Kd.n_steps * (Kd.np > 0 ? Kd.np : 1);   // record values
+    for (int n = threadIdx.x; n < nv; n += blockDim.x) acc += (double)U[n] * (double)U[n];
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -324,11 +325,21 @@ __global__ void __launch_bounds__(32) reeval_pass_kernel(const KConst<double> K,
         j += 2;
         if (j >= K.spc2) j = 0;
         step64<M, FORCE, TANGENT>(K, c, cf, q, v, g0, gh, g1, rec + lane + (s - n0) * kRec * 32);
-        double u = q[0];
+        if (K.np > 0) {   // deflection points
+            for (int k = 0; k < K.np; ++k) {
+                double uk = K.phi[k][0] * q[0];
 #pragma unroll
-        for (int i = 1; i < M; ++i) u += q[i];
-        const double r = (double)U[s] - u;
-        S = fma(r, r, S);
+                for (int i = 1; i < M; ++i) uk = fma(K.phi[k][i], q[i], uk);
+                const double r = (double)U[(size_t)s * K.np + k] - uk;
+                S = fma(r, r, S);
+            }
+        } else {
+            double u = q[0];
+#pragma unroll
+            for (int i = 1; i < M; ++i) u += q[i];
+            const double r = (double)U[s] - u;
+            S = fma(r, r, S);
+        }
     }
 #pragma unroll
     for (int i = 0; i < M; ++i) {
@@ -450,8 +461,10 @@ __global__ void __launch_bounds__(256) reeval_final_kernel(const KConst<double> 
     const double defect = rd[0];
     int segs = R.B;
     if (!(defect <= kDefectTol) || !isfinite(S64)) {
-        S64 = integrate<double, M, FORCE, float>(K, winner_coef(w), R.tab, U, nullptr, 0, 0,
-                                                 K.n_steps);
+        S64 = K.np > 0 ? integrate_points<double, M, FORCE, float>(K, winner_coef(w), R.tab, U,
+                                                                   nullptr, 0, 0, K.n_steps)
+                       : integrate<double, M, FORCE, float>(K, winner_coef(w), R.tab, U, nullptr,
+                                                            0, 0, K.n_steps);
         segs = 0;
     }
     double th[AFM_MAXD];

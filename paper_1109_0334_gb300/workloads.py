@@ -114,6 +114,12 @@ WORKLOADS["f3_chirp"] = dict(
     free=[_DA, (6, 7500.0, 12500.0, False), (7, 1.9e7, 2.1e7, False)],
     drive_params=(2e-9, 1e4, 2e7), x_truth=[0.02, 0.5, 0.5], seed=SEED_BASE + 11, **_DRV)
 
+# Deflection records at three points of the 3-mode cantilever (the paper's
+# n_dp = 3, Sec. 3.2): x = L/3, 2L/3 and the tip.
+WORKLOADS["f4_points"] = dict(WORKLOADS["c2"], name="3-mode EB DMT, deflections at L/3, 2L/3, L, "
+                              "512 particles x 50 updates", points=(1.0 / 3.0, 2.0 / 3.0, 1.0),
+                              cycles=40, P=512, iters=50, seed=SEED_BASE + 12)
+
 for _w in WORKLOADS.values():
     _w.setdefault("sigma", 0.005 * _w["A0"])    # 0.5 % of the free amplitude
     _w["record_sub"] = 4

@@ -29,11 +29,12 @@ def oracle_record(orc, spec, pixel: int = 0, n: int | None = None):
 
 
 def oracle_defl_nm(orc, spec, x_dp, n: int | None = None):
-    """Oracle tip deflection [n][P] in nm for coordinates x [D][P]."""
+    """Oracle deflection [n * values per step][P] in nm (the tip, or the
+    workload's deflection points) for coordinates x [D][P]."""
     c, pm = oracle_case(orc, spec)
     n = W.n_steps(spec) if n is None else n
     x_dp = np.asarray(x_dp, dtype=np.float64)
-    out = np.empty((n, x_dp.shape[1]))
+    out = np.empty((n * orc.n_values(c), x_dp.shape[1]))
     for p in range(x_dp.shape[1]):
         th = orc.map_x(pm, x_dp[:, p])
         out[:, p] = orc.forward(c, th, n) / NM
