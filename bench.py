@@ -119,6 +119,7 @@ def measured_peaks() -> dict:
 KERNEL_SOURCES = {
     "invert_iter_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_invert.cu"],
     "invert_pair_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_pair.cu"],
+    "invert_modes_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_modes.cu"],
     "fwd_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_forward.cu"],
     "batch_kernel": ["afm_device.cuh", "afm_internal.h", "afm_launch.h", "kern_batch.cuh",
                      "kern_batch.cu", "kern_batch_dmt.cu"],
@@ -757,6 +758,41 @@ def run_ours(args):
            "d2h_bytes_per_step": int(res.numel() + hist.numel() * 4),
            "ms_per_inversion": E_ms / args.steps}
 
+    # the same record by a short swarm + Levenberg-Marquardt polish, and the
+    # accuracy of both against the seeded truth (ms per inversion at equal error)
+    accuracy = None
+    if "lm_polish" in spec:
+        lp = spec["lm_polish"]
+        cfg_lm = A.make_pso(dict(spec, iters=lp["iters"]), pixel=pixel)
+        lm_ms = []
+        for k in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r_lm = A.invert_polished(prob, U, cfg_lm, lp["polish_k"], lp["polish_steps"],
+                                     lp["n_cand"], method="lm")
+            e1.record(stream)
+            e1.synchronize()
+            lm_ms.append(e0.elapsed_time(e1))
+        r_lm = A.decode_result(r_lm[0])
+        th_truth = _theta_of(spec, x_truth[:, 0])
+        var = (spec["sigma"] / 1e-9) ** 2
+        S_best = min(r["S_f64"], r_lm["S_f64"])
+
+        def acc(rr):
+            th = list(rr["theta"])
+            return {"dchi2_vs_best": (rr["S_f64"] - S_best) / var,
+                    "ident_rel_err_vs_truth": [abs(a / b - 1) for a, b in
+                                               zip(_dmt_comb(th), _dmt_comb(th_truth))]}
+        accuracy = {"ident": "H R, E* sqrt(R), a0 (the combinations a DMT record determines)",
+                    "plain_pso": dict(acc(r), ms_per_inversion=T_ms / args.steps),
+                    "lm_polished": dict(acc(r_lm), ms_per_inversion=lm_ms[-1],
+                                        config=f"{P} particles x {lp['iters']} updates + "
+                                               f"{lp['polish_steps']} Levenberg-Marquardt steps "
+                                               f"on the best {lp['polish_k']} ({lp['n_cand']} "
+                                               "damping values per step)")}
+
     # roofline of the dominant kernel (fused iteration kernel)
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
@@ -767,8 +803,8 @@ def run_ours(args):
     achieved = ops_launch / avg_launch_s
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
             "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
-            "traffic": ncu_traffic("invert_pair_kernel", args.workload),
-            "kernel": "invert_pair_kernel<3,DMT> (two lanes per particle)",
+            "traffic": ncu_traffic("invert_modes_kernel", args.workload),
+            "kernel": "invert_modes_kernel<3,DMT,2> (modes of a particle over two lanes)",
             "ops_per_particle_step": fp32_ops_per_step(m, spec["force"]),
             "launches_timed": kern_n, "avg_launch_ms": avg_launch_s * 1e3,
             "kernel_share_of_step": kern_ms / sum(step_ms),
@@ -843,6 +879,7 @@ def run_ours(args):
                        "S_f64_segments": r["segments"], "S_f64_join_defect": r["defect"],
                        "x": list(r["x"][:D]), "x_truth": list(x_truth[:, 0]),
                        "status": r["status"], "theta": list(theta)},
+            "accuracy": accuracy,
             "batched_forward": batched,
             "batched_inversion": c3,
             "polished_inversion": c4,

@@ -172,6 +172,31 @@ typedef struct afm_ctx afm_ctx;
 /* Binds a CUDA device (queries its SM count).  Owns no device memory. */
 afm_status afm_ctx_create(int device, afm_ctx** out);
 afm_status afm_ctx_destroy(afm_ctx* ctx);
+
+/* Lanes per particle of the fused inversion iteration (afm_invert,
+ * afm_invert_polished).  A swarm too small to fill the GPU is latency-bound
+ * along each particle's RK4 recurrence (Sec. 3.2); spreading a particle over
+ * several lanes of a warp shortens the chain.  Every variant is bit-identical
+ * to the one-lane arithmetic; a variant the problem does not support runs
+ * the automatic choice.
+ *   AFM_LANES_AUTO    the library's choice (default)
+ *   AFM_LANES_ONE     one lane per particle
+ *   AFM_LANES_STAGES  two lanes, the tip forces of RK4 stages 1/3 and 2/4
+ *                     evaluated by one lane each (rate-free force laws,
+ *                     1 or 3 modes, P <= 9728)
+ *   AFM_LANES_MODES2  two lanes, the modes split between them (rate-free
+ *                     laws, 2 or 3 modes, P <= 9728)
+ *   AFM_LANES_MODES4  four lanes, one mode each (rate-free laws, 2 or 3
+ *                     modes, P <= 4864)
+ * Returns AFM_ERR_INVALID_ARG for an unknown value. */
+typedef enum {
+    AFM_LANES_AUTO = 0,
+    AFM_LANES_ONE = 1,
+    AFM_LANES_STAGES = 2,
+    AFM_LANES_MODES2 = 3,
+    AFM_LANES_MODES4 = 4
+} afm_lanes;
+afm_status afm_set_lanes(afm_ctx* ctx, int lanes);
 /* Message of the last failed call on this thread ("" if none). */
 const char* afm_last_error(void);
 const char* afm_status_string(int status);

@@ -104,6 +104,7 @@ def lib():
             L.afm_status_string.restype = C.c_char_p
             L.afm_status_string.argtypes = [i]
             L.afm_profile_enable.argtypes = [vp, i]
+            L.afm_set_lanes.argtypes = [vp, i]
             L.afm_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
             L.afm_forward_batch.argtypes = [vp, C.POINTER(Problem), vp, i, vp, vp, vp, vp]
             L.afm_forward_batch_f64.argtypes = [vp, C.POINTER(Problem), vp, i, vp, vp, vp, vp]
@@ -169,6 +170,15 @@ def context(device: int | None = None):
 def profile_enable(on: bool = True, device=None) -> None:
     """Bracket the hot kernels with CUDA events (see afm_profile_enable)."""
     _check(lib().afm_profile_enable(context(device), int(bool(on))))
+
+
+LANES = {"auto": 0, "one": 1, "stages": 2, "modes2": 3, "modes4": 4}
+
+
+def set_lanes(lanes: str = "auto", device=None) -> None:
+    """Lanes per particle of the fused inversion iteration (see afm_set_lanes):
+    'auto', 'one', 'stages', 'modes2' or 'modes4'; all are bit-identical."""
+    _check(lib().afm_set_lanes(context(device), LANES[lanes]))
 
 
 def profile_read(device=None):

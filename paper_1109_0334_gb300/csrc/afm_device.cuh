@@ -148,7 +148,9 @@ __device__ __forceinline__ T tip_force(const Coef<T>& c, T d, T dd) {
 }
 
 // Partial derivatives of the tip force with respect to the gap (Fd), the gap
-// rate (Fr) and the four coefficients (Fc[0..3]) at (d, d').
+// rate (Fr) and the four coefficients (Fc[0..3]) at (d, d').  Reciprocals and
+// square roots use the hardware approximations of tip_force (a relative
+// error of a few FP32 ulps, far below the tangents' own rounding).
 template <int FORCE>
 __device__ __forceinline__ void force_partials(const Coef<float>& c, float d, float dd, float& Fd,
                                                float& Fr, float* Fc) {
@@ -161,13 +163,13 @@ __device__ __forceinline__ void force_partials(const Coef<float>& c, float d, fl
     } else if (FORCE == F_DMT || FORCE == F_DMT_KV) {
         const bool contact = d < c.c3;
         const float dm = fmaxf(d, c.c3);
-        const float r = 1.f / dm;
+        const float r = rcp_fast(dm);
         const float r2 = r * r;
         Fc[1] = -r2;
         if (contact) {
             const float del = c.c3 - d;
-            const float sq = sqrtf(del);
-            const float isq = 1.f / sq;
+            const float sq = sqrt_fast(del);
+            const float isq = rcp_fast(sq);
             Fd = -1.5f * c.c0 * sq;
             Fc[0] = del * sq;
             Fc[3] = 1.5f * c.c0 * sq + 2.f * c.c1 * r2 * r;

@@ -84,6 +84,12 @@ cudaError_t launch_adjoint(const KConst<float>& K, const float* x, int P, const 
 cudaError_t launch_sens(const KConst<float>& K, const float* x, int P, const float* U, float* S,
                         double* H, double* b, cudaStream_t st, const int64_t* off = nullptr,
                         const int* order = nullptr, int per_slot = 1);
+// the same pass with one lane per parameter direction (kern_lm_lanes.cu);
+// launch_sens uses it when P x lanes fits one warp per SM sub-partition
+bool sens_lanes_preferred(int P, int D);
+cudaError_t launch_sens_lanes(const KConst<float>& K, const float* x, int P, const float* U,
+                              float* S, double* H, double* b, cudaStream_t st, const int64_t* off,
+                              const int* order, int per_slot);
 cudaError_t launch_lm_cand(int D, int K, int J, const float* x, const double* H, const double* b,
                            double lam0, double ratio, float* Xc, cudaStream_t st);
 cudaError_t launch_lm_select(int D, int K, int J, float* x, float* S, const float* Xc,
@@ -137,14 +143,23 @@ cudaError_t launch_pso_init(const PsoConst& pc, const SwarmPtrs& sw, cudaStream_
 cudaError_t launch_pso_best(const PsoConst& pc, const SwarmPtrs& sw, const float* S, int it,
                             cudaStream_t st);
 cudaError_t launch_pso_move(const PsoConst& pc, const SwarmPtrs& sw, int it, cudaStream_t st);
-// fused inversion iteration (it = 0: initial evaluation)
+// fused inversion iteration (it = 0: initial evaluation); `lanes` picks the
+// lanes-per-particle variant (afm_lanes of afminv.h; all are bit-identical,
+// a variant the problem does not support runs the automatic choice)
 cudaError_t launch_invert_iter(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
-                               const float* U, float* history, int it, cudaStream_t st);
-// the same iteration with two lanes per particle (rate-free laws, 1 or 3
-// modes, P <= 9728); launch_invert_iter selects it by itself
+                               const float* U, float* history, int it, cudaStream_t st,
+                               int lanes = 0);
+// the same iteration with two lanes per particle, the RK4 stage forces split
+// between them (rate-free laws, 1 or 3 modes, P <= 9728)
 bool pair_supported(int m, int force, int P);
 cudaError_t launch_invert_pair(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
                                const float* U, float* history, int it, cudaStream_t st);
+// the same iteration with the modes of a particle spread over 2 or 4 lanes
+// (rate-free laws, 2 or 3 modes, P <= 19456 / lanes)
+bool modes_supported(int m, int force, int P, int lanes);
+cudaError_t launch_invert_modes(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
+                                const float* U, float* history, int it, int lanes,
+                                cudaStream_t st);
 // base-motion inversion (drive_mode 1, kern_drive.cu)
 cudaError_t launch_forward_drive_f32(const KConst<float>& K, const float* x, int P, float* defl,
                                      const float* U, float* S, cudaStream_t st);

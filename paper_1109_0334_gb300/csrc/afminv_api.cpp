@@ -38,6 +38,8 @@ struct afm_ctx {
     std::vector<afm_batch_graph> batch_graphs;
     // kernel timing (afm_profile_*): events around each fused iteration launch
     bool profiling = false;
+    // lanes per particle of the fused inversion iteration (afm_lanes)
+    int lanes = AFM_LANES_AUTO;
     std::vector<cudaEvent_t> ev_pool;   // reusable events
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
 };
@@ -813,6 +815,15 @@ afm_status afm_profile_enable(afm_ctx* ctx, int on) {
     return AFM_OK;
 }
 
+afm_status afm_set_lanes(afm_ctx* ctx, int lanes) {
+    g_err[0] = 0;
+    if (!ctx) return fail(AFM_ERR_INVALID_ARG, "context is NULL");
+    if (lanes < AFM_LANES_AUTO || lanes > AFM_LANES_MODES4)
+        return fail(AFM_ERR_INVALID_ARG, "unknown lanes variant %d", lanes);
+    ctx->lanes = lanes;
+    return AFM_OK;
+}
+
 afm_status afm_profile_read(afm_ctx* ctx, double* ms, int* launches) {
     g_err[0] = 0;
     afm_status st = check_ctx(ctx);
@@ -1025,7 +1036,8 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
     for (int it = 0; it <= cfg->iters; ++it)
         AFM_CUDA(timed_launch(ctx, s, [&] {
                      return prob->n_points > 0 ? afm::launch_invert_points(Kf, pc, sw, U, history, it, s)
-                                               : afm::launch_invert_iter(Kf, pc, sw, U, history, it, s);
+                                               : afm::launch_invert_iter(Kf, pc, sw, U, history, it, s,
+                                                                         ctx->lanes);
                  }),
                  "invert iteration kernel");
     if (reeval_extra(*prob) > 0) {
@@ -1268,7 +1280,9 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     AFM_CUDA(afm::launch_pso_init(pc, sw, s), "pso init kernel");
     for (int it = 0; it <= cfg->iters; ++it)
-        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_invert_iter(Kf, pc, sw, U, history, it, s); }),
+        AFM_CUDA(timed_launch(ctx, s, [&] {
+                     return afm::launch_invert_iter(Kf, pc, sw, U, history, it, s, ctx->lanes);
+                 }),
                  "invert iteration kernel");
     const int fin = (cfg->iters + 1) & 1;
     AFM_CUDA(afm::launch_topk(sw.pbS, sw.pb[fin], P, D, polish_k, xk, ik, s), "top-k kernel");

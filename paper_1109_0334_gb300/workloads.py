@@ -37,7 +37,11 @@ WORKLOADS = {
     "c2": dict(name="3-mode EB DMT, 4 unknowns, 1024 particles x 100 updates",
                model="modal_eb", n_modes=3, spc=256, cycles=100, force="dmt",
                free=[_E, _H, _R, _A0], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
-               P=1024, iters=100, seed=SEED_BASE + 2, **_CANTILEVER, **_PSO),
+               P=1024, iters=100, seed=SEED_BASE + 2,
+               # the same record by a short swarm and Levenberg-Marquardt
+               # polish of its best particles
+               lm_polish=dict(iters=10, polish_k=8, polish_steps=8, n_cand=8),
+               **_CANTILEVER, **_PSO),
     # 4096 independent pixels, 20..200 cycles each, 256 particles x 60 updates.
     "c3": dict(name="4096 pixels, 3-mode EB DMT, 256 particles x 60 updates",
                model="modal_eb", n_modes=3, spc=256, cycles=(20, 200), force="dmt",

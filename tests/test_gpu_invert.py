@@ -135,24 +135,32 @@ def test_invert_c2_full_size_parity(orc, afm):
     _check_inversion(orc, spec, U_m, r, np.array(gold["x"]), gold["S_m2"], hist)
 
 
+@pytest.mark.parametrize("lanes", ["auto", "one", "stages", "modes2", "modes4"])
 @pytest.mark.parametrize("name,over", [
     ("c2", dict(cycles=12)),
     ("c1", dict(cycles=12)),
+    ("c2", dict(cycles=12, n_modes=2)),
     ("c2", dict(cycles=12, force="linear_spring", fixed=[0.0] * 5,
                 free=[(0, 2.0, 20.0, False), (1, 10e-9, 20e-9, False)])),
     ("c2", dict(cycles=12, force="hooke", fixed=[0.0] * 5,
                 free=[(0, 0.5, 8.0, True), (1, -2e-9, 4e-9, False)])),
 ])
-def test_two_lane_iteration_is_bit_identical(orc, afm, name, over):
-    """Small swarms of rate-free laws run two lanes per particle (stage
-    forces split between the lanes); the result must be bit-identical to the
-    one-lane arithmetic of the batched-pixel kernel on the same pixel."""
+def test_multi_lane_iteration_is_bit_identical(orc, afm, name, over, lanes):
+    """Small swarms of rate-free laws run several lanes per particle (RK4
+    stage forces or modes split between the lanes); every variant must be
+    bit-identical to the one-lane arithmetic of the batched-pixel kernel on
+    the same pixel."""
     spec = W.get(name, P=77, iters=6, **over)
     U32, _, _ = oracle_record(orc, spec)
     prob = afm.make_problem(spec)
     cfg = afm.make_pso(spec)
     Ut = torch.from_numpy(U32).cuda()
-    r1, h1 = afm.invert(prob, Ut, cfg)
+    afm.set_lanes(lanes)
+    try:
+        r1, h1 = afm.invert(prob, Ut, cfg)
+        torch.cuda.synchronize()
+    finally:
+        afm.set_lanes("auto")
     off = torch.tensor([0, len(U32)], dtype=torch.int64, device="cuda")
     rb, _ = afm.invert_batch(prob, Ut, off, cfg, particles_per_thread=1)
     torch.cuda.synchronize()

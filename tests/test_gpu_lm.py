@@ -21,6 +21,28 @@ def afm():
     return afminv
 
 
+@pytest.mark.parametrize("name", ["c1", "c2", "c4"])
+def test_lane_split_sensitivities_are_bit_identical(orc, afm, name):
+    """Few candidates run one lane per parameter direction (kern_lm_lanes.cu),
+    many run one thread per candidate: S, H and b must agree bit for bit."""
+    spec = W.get(name, cycles=4)
+    U32, _, xt = oracle_record(orc, spec)
+    D = len(spec["free"])
+    lanes = 2 if D <= 2 else 4 if D <= 4 else 8
+    P_big = 152 * 4 * 32 // lanes + 3          # past the lane-split limit
+    x = np.clip(xt[:, None] + W.sample_x(D, P_big, seed=4, lo=-0.3, hi=0.3), 0.02, 0.98)
+    x = np.ascontiguousarray(x.astype(np.float32))
+    prob = afm.make_problem(spec)
+    Ug = torch.from_numpy(U32).cuda()
+    few = 11
+    S1, H1, b1 = afm.normal_equations(prob, torch.from_numpy(np.ascontiguousarray(x[:, :few])).cuda(), Ug)
+    S2, H2, b2 = afm.normal_equations(prob, torch.from_numpy(x).cuda(), Ug)
+    torch.cuda.synchronize()
+    assert torch.equal(S1, S2[:few])
+    assert torch.equal(H1, H2[:few])
+    assert torch.equal(b1, b2[:few])
+
+
 @pytest.mark.parametrize("name,over", [("c2", dict(cycles=20)), ("c4", dict(cycles=20)),
                                        ("c1", dict(cycles=20))])
 def test_normal_equations_match_oracle_and_adjoint(orc, afm, name, over):
