@@ -23,7 +23,11 @@
 namespace afm {
 
 constexpr int FEN = AFM_FE_MAXN;
-constexpr int FE_THREADS = 256;
+// 64 threads (8 particles in FP32) per block: a C5 swarm of 8 192 particles
+// is 1 024 blocks, spread over 152 SMs within 4 % of even (256-thread blocks
+// left 48 SMs with half the load of the others)
+constexpr int FE_THREADS = 64;
+constexpr int FE_MIN_BLOCKS = 8;   // caps registers at 128 per thread
 // lanes per particle: AFM_FE_LANES in FP32 (throughput), a whole warp in FP64
 // (latency: one trajectory, the FP64 re-evaluation)
 template <typename T>
@@ -31,10 +35,24 @@ struct FeLanes {
     static constexpr int value = sizeof(T) == 8 ? 32 : AFM_FE_LANES;
 };
 
+// Per-mode step coefficients, one 16-byte-aligned record per mode so that a
+// lane fetches them with one vector load.
+template <typename T>
+struct alignas(16) FeQ4 {
+    T b1, d2, g, f;
+};
+
+// Drive term of the Newmark step at phase index j of the period: the base
+// acceleration enters as y(t+) + 2 y(t) + y(t-), evaluated in FP64.
 template <typename T>
 __device__ __forceinline__ void fe_table(const FeConst& F, T* tab) {
-    for (int j = threadIdx.x; j < F.spc; j += blockDim.x)
-        tab[j] = (T)(F.drive_amp * sin(6.283185307179586476925 * (double)j / (double)F.spc + F.drive_phase));
+    const double w = 6.283185307179586476925 / (double)F.spc;
+    for (int j = threadIdx.x; j < F.spc; j += blockDim.x) {
+        const double y0 = sin(w * (double)j + F.drive_phase);
+        const double yp = sin(w * (double)(j + 1) + F.drive_phase);
+        const double ym = sin(w * (double)(j - 1) + F.drive_phase);
+        tab[j] = (T)(F.drive_amp * (yp + 2.0 * y0 + ym));
+    }
 }
 
 // Tip force and its slope in the gap (laws without rate dependence); the
@@ -87,7 +105,7 @@ __device__ __forceinline__ T fe_newton(const Coef<T>& c, T Zc, T base, T cz, int
 // MODE 2: FP64 re-evaluation of an inversion's winner into afm_result.
 // ---------------------------------------------------------------------------
 template <typename T, typename TU, int FORCE, int MODE>
-__global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
+__global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
     const FeConst F, const PsoConst pc, SwarmPtrs sw, const T* __restrict__ xin, int P,
     T* __restrict__ defl, const TU* __restrict__ U, T* __restrict__ S_out,
     float* __restrict__ history, int it, afm_result* __restrict__ res) {
@@ -95,21 +113,20 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
     constexpr int FEM = FEN / FEL;               // modes per lane
     constexpr int FE_PPB = FE_THREADS / FEL;     // particles per block
     extern __shared__ __align__(16) unsigned char fe_smem[];
-    T* cb1 = reinterpret_cast<T*>(fe_smem);
-    T* cd2 = cb1 + FEN;
-    T* cg = cd2 + FEN;
-    T* cf = cg + FEN;
-    T* cpt = cf + FEN;
+    FeQ4<T>* cq = reinterpret_cast<FeQ4<T>*>(fe_smem);
+    T* cpt = reinterpret_cast<T*>(cq + FEN);
     T* cb1lo = cpt + FEN;
     T* tab = cb1lo + FEN;
     const int tid = threadIdx.x, lane = tid & (FEL - 1), grp = tid / FEL;
     for (int i = tid; i < FEN; i += blockDim.x) {
-        cb1[i] = (T)F.b1[i];
-        cd2[i] = (T)F.d2[i];
-        cg[i] = (T)F.g[i];
-        cf[i] = (T)F.f[i];
+        FeQ4<T> c4;
+        c4.b1 = (T)F.b1[i];
+        c4.d2 = (T)F.d2[i];
+        c4.g = (T)F.g[i];
+        c4.f = (T)F.f[i];
+        cq[i] = c4;
         cpt[i] = (T)F.pt[i];
-        cb1lo[i] = (T)(F.b1[i] - (double)cb1[i]);
+        cb1lo[i] = (T)(F.b1[i] - (double)c4.b1);
     }
     fe_table<T>(F, tab);
     const int D = F.pm.D;
@@ -185,22 +202,26 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
     fe_force<FORCE, T>(cfc, Zc + (T)F.utipm, Fm, dF);
     T S = (T)0, cS = (T)0, u2 = (T)0;
     const int spc = F.spc;
-    const int newton_it = 3;   // the tip coupling is a contraction of ~1e-4: 3 steps are exact
+    // the tip coupling is a contraction of ~1e-4: Newton from the uncoupled
+    // deflection is converged to FP32 rounding after 2 steps, to FP64 after 3
+    const int newton_it = sizeof(T) == 8 ? 3 : 2;
     int jn = 0;
     for (int n = 0; n < F.n_steps; ++n) {
-        const int jp = jn + 1 == spc ? 0 : jn + 1, jm = jn == 0 ? spc - 1 : jn - 1;
-        const T G = tab[jp] + (T)2 * tab[jn] + tab[jm];
+        const int jp = jn + 1 == spc ? 0 : jn + 1;
+        const T G = tab[jn];
         const T Fo = (T)2 * Fn + Fm;
-        T incs[FEM];
+        T incs[FEM], cfs[FEM];
         T tsum = (T)0;
 #pragma unroll
         for (int j = 0; j < FEM; ++j) {
             const int i = lane + FEL * j;
-            T inc = fma(cb1[i], z[j], cd2[i] * dz[j]);
+            const FeQ4<T> c4 = cq[i];
+            T inc = fma(c4.b1, z[j], c4.d2 * dz[j]);
             if (j == 0) inc = fma(cb1lo[i], z[j], inc);
-            inc = fma(cg[i], G, inc);
-            inc = fma(cf[i], Fo, inc);
+            inc = fma(c4.g, G, inc);
+            inc = fma(c4.f, Fo, inc);
             incs[j] = inc;
+            cfs[j] = c4.f;
             tsum = fma(cpt[i], z[j] + ((dz[j] + inc) - cz[j]), tsum);
         }
 #pragma unroll
@@ -210,8 +231,7 @@ __global__ void __launch_bounds__(FE_THREADS) fe_modal_kernel(
         // compensated updates of both the increment and the modal coordinate
 #pragma unroll
         for (int j = 0; j < FEM; ++j) {
-            const int i = lane + FEL * j;
-            kahan_add(dz[j], cdz[j], fma(cf[i], Fp, incs[j]));
+            kahan_add(dz[j], cdz[j], fma(cfs[j], Fp, incs[j]));
             kahan_add(z[j], cz[j], dz[j]);
         }
         Fm = Fn;
@@ -303,7 +323,7 @@ cudaError_t fe_dispatch(int force, Fn&& f) {
 
 template <typename T>
 size_t fe_smem(const FeConst& F) {
-    return sizeof(T) * (6 * (size_t)FEN + (size_t)F.spc);
+    return sizeof(FeQ4<T>) * (size_t)FEN + sizeof(T) * (2 * (size_t)FEN + (size_t)F.spc);
 }
 
 template <typename T, typename TU, int MODE, typename... Args>
