@@ -237,11 +237,17 @@ afm_status afm_misfit(afm_ctx* ctx, const float* defl, const float* U, int N, in
  * afm_pso_step: given the misfits S_new [P] (device) of the current x,
  *   (1) personal bests: pbest <- x where S_new < pbest_S (strictly);
  *   (2) global best = lowest pbest_S, lowest particle index on ties;
- *   (3) v <- w v + c1 r1 (pbest - x) + c2 r2 (gbest - x), x <- x + v, a
- *       coordinate leaving [0,1] is clamped and its velocity zeroed; r1, r2
- *       per particle and dimension from counter (particle, iter, pixel,
- *       2<<16 | d/2), words 2d mod 4 and 2d+1 mod 4.
- *   iter = 0 performs (1)-(2) only (the initial evaluation). */
+ *   (3) unless iter == cfg->iters (the final evaluation): the move of
+ *       swarm generation iter + 1, v <- w v + c1 r1 (pbest - x) + c2 r2
+ *       (gbest - x), x <- x + v, a coordinate leaving [0,1] is clamped and
+ *       its velocity zeroed; r1, r2 per particle and dimension from counter
+ *       (particle, iter + 1, pixel, 2<<16 | d/2), words 2d mod 4 and
+ *       2d+1 mod 4.
+ *   Evaluating the misfits of the current x and calling afm_pso_step with
+ *   iter = 0, 1, ..., iters reproduces afm_invert's swarm bit for bit.  The
+ *   swarm struct is the whole state: copied out after any step and restored
+ *   later, it resumes the run exactly (the draws are keyed by particle,
+ *   generation and pixel). */
 afm_status afm_pso_init(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw, void* stream);
 afm_status afm_pso_step(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw,
                         const float* S_new, uint32_t iter, void* stream);

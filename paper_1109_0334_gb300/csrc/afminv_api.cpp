@@ -2,6 +2,7 @@
 // per-problem set-up in double precision on the host (modal constants of
 // Eq. 2, drive and initial state, scaled units), and the launch sequences.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <complex>
@@ -45,6 +46,16 @@ struct afm_ctx {
 };
 
 namespace {
+
+// NVTX range over each compute entry point (a tracing aid: near-free when no
+// profiler is attached; the NVTX v3 headers need no library)
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+#define AFM_TRACE(name) TraceRange afm_trace_range_(name)
 
 thread_local char g_err[512] = "";
 
@@ -848,6 +859,7 @@ afm_status afm_profile_read(afm_ctx* ctx, double* ms, int* launches) {
 
 afm_status afm_forward_batch(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
                              float* defl, const float* U, float* S, void* stream) {
+    AFM_TRACE("afm_forward_batch");
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
@@ -883,6 +895,7 @@ afm_status afm_forward_batch(afm_ctx* ctx, const afm_problem* prob, const float*
 
 afm_status afm_forward_batch_f64(afm_ctx* ctx, const afm_problem* prob, const double* x, int P,
                                  double* defl, const double* U, double* S, void* stream) {
+    AFM_TRACE("afm_forward_batch_f64");
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
@@ -914,6 +927,7 @@ afm_status afm_forward_batch_f64(afm_ctx* ctx, const afm_problem* prob, const do
 
 afm_status afm_misfit(afm_ctx* ctx, const float* defl, const float* U, int N, int P, float* S,
                       void* stream) {
+    AFM_TRACE("afm_misfit");
     g_err[0] = 0;
     afm_status st = check_ctx(ctx);
     if (st) return st;
@@ -938,6 +952,7 @@ static afm_status swarm_ptrs(const afm_swarm* sw, afm::SwarmPtrs& p) {
 }
 
 afm_status afm_pso_init(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw, void* stream) {
+    AFM_TRACE("afm_pso_init");
     g_err[0] = 0;
     afm_status st = check_ctx(ctx);
     if (st) return st;
@@ -954,6 +969,7 @@ afm_status afm_pso_init(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw, voi
 
 afm_status afm_pso_step(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw, const float* S_new,
                         uint32_t iter, void* stream) {
+    AFM_TRACE("afm_pso_step");
     g_err[0] = 0;
     afm_status st = check_ctx(ctx);
     if (st) return st;
@@ -986,6 +1002,7 @@ afm_status afm_invert_workspace_size(const afm_problem* prob, const afm_pso_cfg*
 afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
                       const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
                       afm_result* result, float* history, void* stream) {
+    AFM_TRACE("afm_invert");
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
@@ -1068,6 +1085,7 @@ afm_status afm_adjoint_workspace_size(const afm_problem* prob, int P, size_t* by
 afm_status afm_adjoint(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
                        const float* U, float* S, float* dS_dx, void* workspace,
                        size_t workspace_bytes, void* stream) {
+    AFM_TRACE("afm_adjoint");
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
@@ -1092,6 +1110,7 @@ afm_status afm_adjoint(afm_ctx* ctx, const afm_problem* prob, const float* x, in
 
 afm_status afm_normal_equations(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
                                 const float* U, float* S, double* H, double* b, void* stream) {
+    AFM_TRACE("afm_normal_equations");
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
@@ -1203,6 +1222,7 @@ afm_status afm_polish_workspace_size(const afm_problem* prob, int K, int n_cand,
 afm_status afm_polish(afm_ctx* ctx, const afm_problem* prob, const float* U, float* x, float* S,
                       int K, int steps, int n_cand, int method, void* workspace,
                       size_t workspace_bytes, void* stream) {
+    AFM_TRACE("afm_polish");
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
@@ -1245,6 +1265,7 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
                                const afm_pso_cfg* cfg, int polish_k, int polish_steps, int n_cand,
                                int method, void* workspace, size_t workspace_bytes,
                                afm_result* result, float* history, void* stream) {
+    AFM_TRACE("afm_invert_polished");
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;
@@ -1405,6 +1426,7 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
                             const int64_t* off, int n_pix, uint32_t pixel0,
                             const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
                             afm_result* results, int* particles_per_thread, void* stream) {
+    AFM_TRACE("afm_invert_batch");
     g_err[0] = 0;
     if (n_pix >= 1 && workspace_bytes < batch_layout(n_pix).total)
         return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes,
@@ -1522,6 +1544,7 @@ afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* prob, cons
                                      void* workspace, size_t workspace_bytes,
                                      afm_result* results, int* particles_per_thread,
                                      void* stream) {
+    AFM_TRACE("afm_invert_batch_polished");
     g_err[0] = 0;
     const int n_run = select ? select->n_run : n_pix;
     afm_status st = check_batch_polish(prob, cfg, n_run, polish_k, n_cand, method);
@@ -1622,6 +1645,7 @@ afm_status afm_invert_image(afm_ctx* ctx, const afm_problem* prob, const float* 
                             const int64_t* off, uint32_t pixel0, const afm_image_cfg* icfg,
                             void* workspace, size_t workspace_bytes, afm_result* results,
                             void* stream) {
+    AFM_TRACE("afm_invert_image");
     g_err[0] = 0;
     if (!prob || !icfg) return fail(AFM_ERR_INVALID_ARG, "NULL prob or icfg");
     afm_status st = check_problem(prob);
@@ -1676,6 +1700,7 @@ afm_status afm_invert_image(afm_ctx* ctx, const afm_problem* prob, const float* 
 afm_status afm_synth_records(afm_ctx* ctx, const afm_problem* prob, const double* x_truth,
                              int n_pix, const int64_t* off, int sub, double sigma_m,
                              uint64_t seed, uint32_t pixel0, float* U_cat, void* stream) {
+    AFM_TRACE("afm_synth_records");
     g_err[0] = 0;
     afm_status st = check_problem(prob);
     if (st) return st;

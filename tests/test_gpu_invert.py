@@ -168,3 +168,47 @@ def test_multi_lane_iteration_is_bit_identical(orc, afm, name, over, lanes):
     assert a["winner"] == b["winner"] and a["S"] == b["S"]
     np.testing.assert_array_equal(a["x"], b["x"])
     assert np.all(np.diff(h1.cpu().numpy()) <= 0)
+
+
+def _stepwise(afm, prob, cfg, U, sw, first, last):
+    """Swarm evaluations first..last through the boundary's separate steps:
+    afm_forward_batch for the misfits, afm_pso_step for bests and move."""
+    for it in range(first, last + 1):
+        _, S = afm.forward_batch(prob, sw.x, U, want_defl=False)
+        afm.pso_step(cfg, sw, S, it)
+    return sw
+
+
+@pytest.mark.parametrize("name", ["c1", "c2"])
+def test_checkpoint_resume_is_bitwise(orc, afm, name):
+    """The swarm state (x, v, personal bests, global best key) is the whole
+    state of an inversion: copied to the host after evaluation k and
+    restored into fresh device buffers, the run continues bit for bit as an
+    uninterrupted one (Philox draws are keyed by particle, iteration and
+    pixel, so nothing else carries over).  The composed steps also give the
+    fused inversion's winner and misfit."""
+    spec = W.get(name, cycles=6, P=96, iters=9)
+    D = len(spec["free"])
+    U32, _, _ = oracle_record(orc, spec)
+    prob = afm.make_problem(spec)
+    cfg = afm.make_pso(spec)
+    U = torch.from_numpy(U32).cuda()
+    full = _stepwise(afm, prob, cfg, U, afm.pso_init(cfg, D), 0, spec["iters"])
+    part = _stepwise(afm, prob, cfg, U, afm.pso_init(cfg, D), 0, 4)
+    torch.cuda.synchronize()
+    saved = {k: getattr(part, k).cpu().clone() for k in ("x", "v", "pbest_x", "pbest_S", "gbest")}
+    del part
+    resumed = afm.SwarmState(**{k: t.cuda() for k, t in saved.items()})
+    resumed = _stepwise(afm, prob, cfg, U, resumed, 5, spec["iters"])
+    torch.cuda.synchronize()
+    for k in ("x", "v", "pbest_x", "pbest_S", "gbest"):
+        assert torch.equal(getattr(full, k), getattr(resumed, k)), k
+    # the fused inversion is the composition of the same steps
+    r, _ = afm.invert(prob, U, cfg)
+    torch.cuda.synchronize()
+    r = afm.decode_result(r)
+    key = int(full.gbest.cpu().numpy().view(np.uint64)[0])
+    g = key & 0xFFFFFFFF
+    assert r["winner"] == g
+    assert np.float32(r["S"]) == full.pbest_S.cpu().numpy()[g]
+    np.testing.assert_array_equal(np.float32(r["x"][:D]), full.pbest_x.cpu().numpy()[:, g])
