@@ -454,7 +454,54 @@ def run_c4(A, W, dev, flush):
                           "ms_per_inversion": ms_pso, "S_f64_nm2": r_pso["S_f64"],
                           "dchi2_vs_best": (r_pso["S_f64"] - S_best) / var,
                           "ident_rel_err_vs_truth": ident_errors(list(r_pso["theta"]), th_true)},
-            "ident": "H R, E* sqrt(R), a0, eta sqrt(R)"}
+            "ident": "H R, E* sqrt(R), a0, eta sqrt(R)",
+            "records_16": lm_vs_plain(A, W, "c4", U.device, flush)}
+
+
+def lm_vs_plain(A, W, name, dev, flush, n_rec=16, plain_iters=100):
+    """Plain swarm (plain_iters updates) against short swarm + LM polish
+    on n_rec seeded records (pixels 0..n_rec-1): median ms per inversion and
+    the fraction of records at delta chi^2 <= 1 against the better of the
+    two (statistically at the optimum)."""
+    import numpy as np
+    import torch
+    spec = W.get(name)
+    D, N = len(spec["free"]), W.n_steps(spec)
+    prob = A.make_problem(spec)
+    lp = spec["lm_polish"]
+    var = (spec["sigma"] / 1e-9) ** 2
+    off = torch.tensor([0, N], dtype=torch.int64, device=dev)
+    rows = []
+    for pix in range(n_rec):
+        rng = np.random.default_rng(spec["seed"] + 1000 * pix)
+        xt = rng.uniform(0.1, 0.9, size=(D, 1))
+        U = A.synth_records(prob, torch.from_numpy(xt).to(dev), off, spec["record_sub"],
+                            spec["sigma"], spec["seed"], pix)
+        cfg_p = A.make_pso(dict(spec, iters=plain_iters), pixel=pix)
+        cfg_l = A.make_pso(dict(spec, iters=lp["iters"]), pixel=pix)
+        runs = {"plain_pso": lambda: A.invert(prob, U, cfg_p),
+                "lm_polished": lambda: A.invert_polished(prob, U, cfg_l, lp["polish_k"],
+                                                         lp["polish_steps"], lp["n_cand"],
+                                                         method="lm")}
+        row = {}
+        for key, fn in runs.items():
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            e1.synchronize()
+            row[key] = (e0.elapsed_time(e1), A.decode_result(r[0])["S_f64"])
+        rows.append(row)
+    out = {"records": n_rec, "plain_config": f"{spec['P']} particles x {plain_iters} updates",
+           "lm_config": f"{spec['P']} particles x {lp['iters']} updates + {lp['polish_steps']} "
+                        f"Levenberg-Marquardt steps on the best {lp['polish_k']} "
+                        f"({lp['n_cand']} damping values per step)"}
+    for key in ("plain_pso", "lm_polished"):
+        d = np.array([(row[key][1] - min(v[1] for v in row.values())) / var for row in rows])
+        out[key] = {"median_ms_per_inversion": float(np.median([row[key][0] for row in rows])),
+                    "frac_dchi2_le_1": float(np.mean(d <= 1.0)), "max_dchi2": float(d.max())}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -793,6 +840,10 @@ def run_ours(args):
                                                f"on the best {lp['polish_k']} ({lp['n_cand']} "
                                                "damping values per step)")}
 
+    lm16 = None
+    if "lm_polish" in spec and world == 1 and args.workload == WORKLOAD:
+        lm16 = lm_vs_plain(A, W, args.workload, dev, flush)
+
     # roofline of the dominant kernel (fused iteration kernel)
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
@@ -880,6 +931,7 @@ def run_ours(args):
                        "x": list(r["x"][:D]), "x_truth": list(x_truth[:, 0]),
                        "status": r["status"], "theta": list(theta)},
             "accuracy": accuracy,
+            "accuracy_16_records": lm16,
             "batched_forward": batched,
             "batched_inversion": c3,
             "polished_inversion": c4,

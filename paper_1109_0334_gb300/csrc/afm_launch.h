@@ -94,6 +94,11 @@ cudaError_t launch_lm_cand(int D, int K, int J, const float* x, const double* H,
                            double lam0, double ratio, float* Xc, cudaStream_t st);
 cudaError_t launch_lm_select(int D, int K, int J, float* x, float* S, const float* Xc,
                              const float* Sc, cudaStream_t st);
+// the choice of the fused step (trial points through the sensitivity pass):
+// the point kept brings its H [D][D] and b [D] from Hc [K*J][D][D], bc [K*J][D]
+cudaError_t launch_lm_select_hb(int D, int K, int J, float* x, float* S, double* H, double* b,
+                                const float* Xc, const float* Sc, const double* Hc,
+                                const double* bc, cudaStream_t st);
 
 // image scans (kern_image.cu): coarse and fine pixel lists of a row-major
 // width x height image with coarse spacing `stride`; per fine pixel a box

@@ -1129,19 +1129,34 @@ afm_status afm_normal_equations(afm_ctx* ctx, const afm_problem* prob, const flo
 // Polish workspace.  Steepest descent: gradient [D][K], adjoint checkpoints
 // of K particles; Levenberg-Marquardt: normal equations H [K][D][D], b
 // [K][D] (FP64); both: trial points [D][K*J] and their misfits [K*J].
+// Fused Levenberg-Marquardt step (few candidates, `fused`): the trial points
+// go through the sensitivity pass instead of a plain forward, which gives
+// their misfits (the forward's, bit for bit) and their normal equations at
+// once, so the point kept carries its H and b into the next step; also H_c
+// [K*J][D][D], b_c [K*J][D].
 struct PolishLayout {
-    size_t G, ckpt, H, b, Xc, Sc, total;
+    size_t G, ckpt, H, b, Hc, bc, Xc, Sc, total;
+    bool fused;
 };
 
-PolishLayout polish_layout(const afm_problem& pr, int K, int J, int method) {
+// The fused step pays for the trial points' tangents; it wins while they fit
+// the GPU's sub-partitions (latency regime), as the lane-split sensitivities.
+bool lm_fused(int K, int J, int D) { return afm::sens_lanes_preferred(K * J, D); }
+
+PolishLayout polish_layout(const afm_problem& pr, int K, int J, int method, bool fused_ok) {
     PolishLayout L;
     const size_t D = (size_t)pr.n_free;
     const int m = pr.model == AFM_POINT_MASS ? 1 : pr.n_modes;
     size_t off = 0;
-    L.G = L.ckpt = L.H = L.b = 0;
+    L.G = L.ckpt = L.H = L.b = L.Hc = L.bc = 0;
+    L.fused = fused_ok && method == AFM_POLISH_LM && lm_fused(K, J, (int)D);
     if (method == AFM_POLISH_LM) {
         L.H = off; off += align256(sizeof(double) * (size_t)K * D * D);
         L.b = off; off += align256(sizeof(double) * (size_t)K * D);
+        if (L.fused) {
+            L.Hc = off; off += align256(sizeof(double) * (size_t)K * J * D * D);
+            L.bc = off; off += align256(sizeof(double) * (size_t)K * J * D);
+        }
     } else {
         L.G = off; off += align256(sizeof(float) * D * K);
         L.ckpt = off; off += align256(sizeof(float) * afm::adjoint_ckpt_floats(m, pr.n_steps, K));
@@ -1196,7 +1211,25 @@ afm_status polish_step(afm_ctx* ctx, const KConst<float>& K, int method, const f
 afm_status polish_run(afm_ctx* ctx, const afm_problem& pr, const KConst<float>& K, const float* U,
                       float* x, float* S, int Kn, int steps, int J, int method, char* ws,
                       cudaStream_t s) {
-    const PolishLayout L = polish_layout(pr, Kn, J, method);
+    const PolishLayout L = polish_layout(pr, Kn, J, method, true);
+    if (L.fused && steps > 0) {
+        float* Xc = reinterpret_cast<float*>(ws + L.Xc);
+        float* Sc = reinterpret_cast<float*>(ws + L.Sc);
+        double* H = reinterpret_cast<double*>(ws + L.H);
+        double* b = reinterpret_cast<double*>(ws + L.b);
+        double* Hc = reinterpret_cast<double*>(ws + L.Hc);
+        double* bc = reinterpret_cast<double*>(ws + L.bc);
+        const int D = K.D;
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_sens(K, x, Kn, U, S, H, b, s); }),
+                 "sensitivity kernel");
+        for (int st = 0; st < steps; ++st) {
+            AFM_CUDA(afm::launch_lm_cand(D, Kn, J, x, H, b, kLmLambda0, kLmRatio, Xc, s), "LM trial kernel");
+            AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_sens(K, Xc, Kn * J, U, Sc, Hc, bc, s); }),
+                     "sensitivity kernel");
+            AFM_CUDA(afm::launch_lm_select_hb(D, Kn, J, x, S, H, b, Xc, Sc, Hc, bc, s), "LM select kernel");
+        }
+        return AFM_OK;
+    }
     for (int st = 0; st < steps; ++st) {
         afm_status e = polish_step(ctx, K, method, U, nullptr, nullptr, 1, x, S, Kn, J, L, ws, s);
         if (e) return e;
@@ -1215,7 +1248,7 @@ afm_status afm_polish_workspace_size(const afm_problem* prob, int K, int n_cand,
     if (st) return st;
     if (method != AFM_POLISH_STEEPEST && method != AFM_POLISH_LM)
         return fail(AFM_ERR_INVALID_ARG, "unknown polish method %d", method);
-    *bytes = polish_layout(*prob, K, n_cand, method).total;
+    *bytes = polish_layout(*prob, K, n_cand, method, true).total;
     return AFM_OK;
 }
 
@@ -1256,7 +1289,7 @@ afm_status afm_invert_polished_workspace_size(const afm_problem* prob, const afm
     const size_t xk = align256(sizeof(float) * (size_t)prob->n_free * polish_k);
     const size_t sk = align256(sizeof(float) * (size_t)polish_k);
     const size_t ik = align256(sizeof(int) * (size_t)polish_k);
-    *bytes = inv + xk + sk + ik + polish_layout(*prob, polish_k, n_cand, method).total +
+    *bytes = inv + xk + sk + ik + polish_layout(*prob, polish_k, n_cand, method, true).total +
              reeval_extra(*prob);
     return AFM_OK;
 }
@@ -1311,7 +1344,7 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
         return st;
     if (reeval_extra(*prob) > 0) {
         afm::ReevalPtrs R;
-        afm::reeval_carve(pol + polish_layout(*prob, polish_k, n_cand, method).total, problem_modes(*prob),
+        afm::reeval_carve(pol + polish_layout(*prob, polish_k, n_cand, method, true).total, problem_modes(*prob),
                           prob->n_steps, prob->steps_per_cycle, &R);
         AFM_CUDA(afm::launch_reeval_pick_min(D, polish_k, xk, sk, ik, R.win, s), "winner pick kernel");
         AFM_CUDA(afm::launch_reeval(Kf, Kd, R, U, cfg->iters, sw.flags, result, s),
@@ -1501,7 +1534,7 @@ static BatchPolishLayout batch_polish_layout(const afm_problem& pr, const afm_ps
     L.Sk = off; off += align256(sizeof(float) * Nt);
     L.ik = off; off += align256(sizeof(int) * Nt);
     L.pol = off;
-    L.P = polish_layout(pr, (int)Nt, J, method);
+    L.P = polish_layout(pr, (int)Nt, J, method, false);
     L.total = off + L.P.total;
     return L;
 }

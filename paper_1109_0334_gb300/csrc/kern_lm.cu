@@ -225,6 +225,36 @@ __global__ void lm_select_kernel(int D, int K, int J, float* __restrict__ x, flo
     }
 }
 
+// lm_select_kernel for the fused step: the point kept also brings its normal
+// equations (computed by the sensitivity pass over the trial points).
+__global__ void lm_select_hb_kernel(int D, int K, int J, float* __restrict__ x, float* __restrict__ S,
+                                    double* __restrict__ H, double* __restrict__ b,
+                                    const float* __restrict__ Xc, const float* __restrict__ Sc,
+                                    const double* __restrict__ Hc, const double* __restrict__ bc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int jb = 0;
+    for (int j = 1; j < J; ++j)
+        if (Sc[(size_t)k * J + j] < Sc[(size_t)k * J + jb]) jb = j;
+    const float Sj = Sc[(size_t)k * J + jb];
+    if (Sj < S[k]) {
+        const size_t KJ = (size_t)K * J, c = (size_t)k * J + jb;
+        for (int d = 0; d < D; ++d) x[(size_t)d * K + k] = Xc[(size_t)d * KJ + c];
+        for (int e = 0; e < D * D; ++e) H[(size_t)k * D * D + e] = Hc[c * D * D + e];
+        for (int d = 0; d < D; ++d) b[(size_t)k * D + d] = bc[c * D + d];
+        S[k] = Sj;
+    }
+}
+
+cudaError_t launch_lm_select_hb(int D, int K, int J, float* x, float* S, double* H, double* b,
+                                const float* Xc, const float* Sc, const double* Hc,
+                                const double* bc, cudaStream_t st) {
+    const int threads = 64;
+    lm_select_hb_kernel<<<(K + threads - 1) / threads, threads, 0, st>>>(D, K, J, x, S, H, b, Xc,
+                                                                         Sc, Hc, bc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sens(const KConst<float>& K, const float* x, int P, const float* U, float* S,
                         double* H, double* b, cudaStream_t st, const int64_t* off, const int* order,
                         int per_slot) {
