@@ -853,6 +853,82 @@ static void jacobi_eig(double* A, int n, double* ev)
 
 int orc_fe_dofs(const orc_case* c) { return 2 * c->n_elem; }
 
+/* Double-double accumulation (hi + lo): s += a, and s += a * b exactly
+ * before the final rounding of each partial sum (Knuth's two-sum, the
+ * product's error from one fma). */
+static void dd_add(double* hi, double* lo, double a)
+{
+    double s = *hi + a;
+    double z = s - *hi;
+    double e = (*hi - (s - z)) + (a - z);
+    e += *lo;
+    *hi = s + e;
+    *lo = e - (*hi - s);
+}
+
+static void dd_add_prod(double* hi, double* lo, double a, double b)
+{
+    double p = a * b;
+    dd_add(hi, lo, p);
+    dd_add(hi, lo, fma(a, b, -p));
+}
+
+/* phi^T A phi in double-double: y = A phi row by row, then phi . y. */
+static double dd_quad(const double* A, int n, const double* phi, double* lo_out)
+{
+    double hi = 0.0, lo = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double yh = 0.0, yl = 0.0;
+        for (int j = 0; j < n; ++j) dd_add_prod(&yh, &yl, A[i * n + j], phi[j]);
+        dd_add_prod(&hi, &lo, phi[i], yh);
+        dd_add_prod(&hi, &lo, phi[i], yl);
+    }
+    *lo_out = lo;
+    return hi;
+}
+
+/* Reading R13 drives the beam at its own first frequency.  An FP64
+ * eigensolver fixes the lowest eigenvalues of K x = w^2 M x only to about
+ * eps * lambda_max / lambda (a few 1e-9 for 32 elements), and the resonant
+ * response (Q = 400) turns that into ~1e-6 of the deflection over 50
+ * cycles.  So each eigenvalue in use is refined: its eigenvector by inverse
+ * iteration at the solver's value, then the Rayleigh quotient
+ * phi^T K phi / phi^T M phi with both forms summed in double-double, exact
+ * to rounding (the quotient's error is quadratic in the eigenvector's). */
+static double rayleigh_refined(const orc_fe_mats* fe, double sigma)
+{
+    int n = fe->n;
+    double* A = (double*)malloc(sizeof(double) * n * n);
+    int* piv = (int*)malloc(sizeof(int) * n);
+    double* x = (double*)malloc(sizeof(double) * n);
+    double* y = (double*)malloc(sizeof(double) * n);
+    double shift = sigma;
+    for (int tries = 0; tries < 8; ++tries) {
+        for (int i = 0; i < n * n; ++i) A[i] = fe->K[i] - shift * fe->M[i];
+        if (lu_factor(A, n, piv) == 0) break;
+        shift = sigma * (1.0 - 1e-12 * (double)(tries + 1));   /* exactly singular: step off */
+    }
+    for (int i = 0; i < n; ++i) x[i] = 1.0;
+    for (int it = 0; it < 4; ++it) {
+        for (int i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int j = 0; j < n; ++j) t += fe->M[i * n + j] * x[j];
+            y[i] = t;
+        }
+        lu_solve(A, n, piv, y);
+        double nrm = 0.0;
+        for (int i = 0; i < n; ++i) nrm = fmax(nrm, fabs(y[i]));
+        for (int i = 0; i < n; ++i) x[i] = y[i] / nrm;
+    }
+    double kl, ml;
+    double kh = dd_quad(fe->K, n, x, &kl);
+    double mh = dd_quad(fe->M, n, x, &ml);
+    double lam = kh / mh;
+    lam += lam * (kl / kh - ml / mh);
+    free(A); free(piv); free(x); free(y);
+    return lam;
+}
+
 /* Section from the targets: 3 E I / L^3 = k and the Euler-Bernoulli first
  * frequency (beta_1 L)^2 sqrt(E I / (mu L^4)) = 2 pi f1; rho A = mu. */
 static int fe_build(const orc_case* c, orc_fe_mats* fe)
@@ -922,8 +998,8 @@ static int fe_build(const orc_case* c, orc_fe_mats* fe)
         }
     double* ev = (double*)malloc(sizeof(double) * n);
     jacobi_eig(B, n, ev);
-    fe->w1 = sqrt(ev[0]);
-    fe->w2 = sqrt(ev[1]);
+    fe->w1 = sqrt(rayleigh_refined(fe, ev[0]));
+    fe->w2 = n > 1 ? sqrt(rayleigh_refined(fe, ev[1])) : 3.0 * fe->w1;
     free(ev); free(B); free(T); free(Lc);
     /* Rayleigh: 1/(2Q) = alpha/(2 w_i) + beta w_i / 2, i = 1, 2 */
     double z = 1.0 / (2.0 * c->fe_Q);

@@ -115,3 +115,23 @@ def identifiable_check(orc, spec, U_m, x_ref, S_ref, x_test, rel_param=0.005):
     err = float(proj[ident].max()) if ident.any() else 0.0
     S_t = orc.misfit_batch(c, pm, np.asarray(x_test, dtype=np.float64).reshape(-1, 1), U_m)[0]
     return err, int(ident.sum()), float(S_t), widths
+
+
+def law_combinations(orc, spec, x):
+    """The parameter combinations a DMT-family law depends on (Sec. 3.3 force
+    law: van der Waals -H R / (6 d^2), Hertz (4/3) E* sqrt(R) (a0 - d)^1.5,
+    Kelvin-Voigt eta sqrt(R) sqrt(a0 - d) d'): H R, E* sqrt(R), a0 and, with
+    contact damping, eta sqrt(R).  Along R with these fixed the force, and
+    so the misfit, is exactly constant: R alone is not determined."""
+    pm = orc.make_pmap(spec)
+    th = orc.map_x(pm, np.asarray(x, dtype=np.float64))
+    comb = [th[1] * th[2], th[0] * math.sqrt(th[2]), th[3]]
+    if spec["force"] == "dmt_kv":
+        comb.append(th[4] * math.sqrt(th[2]))
+    return np.array(comb)
+
+
+def combination_error(orc, spec, x_ref, x_test):
+    """Largest relative difference of the law's combinations."""
+    a, b = law_combinations(orc, spec, x_ref), law_combinations(orc, spec, x_test)
+    return float(np.max(np.abs(b / a - 1)))

@@ -58,7 +58,9 @@ def test_fe_forward_f64_parity(orc, afm):
     defl, _ = afm.forward_batch_f64(prob, torch.from_numpy(x).cuda(), None)
     torch.cuda.synchronize()
     ref = _oracle_fe_defl(orc, spec, x, n)
-    assert rel_l2(defl.cpu().numpy(), ref, axis=0).max() <= 1e-7
+    # both sides take the first frequency exact to rounding (reading R13);
+    # what remains is the modal formulation's own FP64 rounding
+    assert rel_l2(defl.cpu().numpy(), ref, axis=0).max() <= 2e-8
 
 
 @pytest.mark.parametrize("force,free", [

@@ -882,3 +882,143 @@ def test_fe_newmark_second_order(orc):
     order = math.log2(np.max(np.abs(e[0] - e[1])) / np.max(np.abs(e[1] - e[2])))
     assert order > 1.8
     assert r[2][1] < r[1][1] < r[0][1] < 1e-3
+
+
+def test_dmt_kv_depends_on_r_only_through_its_combinations(orc):
+    """The DMT law with Kelvin-Voigt damping (Sec. 3.3) enters the dynamics
+    only through H R, E* sqrt(R), a0 and eta sqrt(R): scaling R by s with
+    H / s, E* / sqrt(s) and eta / sqrt(s) leaves the trajectory unchanged up
+    to rounding, in and out of contact.  A wrong power of R anywhere (a
+    dropped sqrt, R for sqrt(R)) moves it at once."""
+    spec = W.get("c4", cycles=6)
+    c = orc.make_case(spec)
+    n = 6 * spec["spc"]
+    th = np.array([1.2e9, 6e-20, 12e-9, 0.3e-9, 300.0, 0.0, 0.0, 0.0])
+    u0 = orc.forward(c, th, n)
+    # the record reaches contact, so every term of the law is exercised
+    d_min = c.Zc + np.min(u0)
+    assert d_min < th[3]
+    for s in (0.5, 2.5):
+        ts = th.copy()
+        ts[2] *= s
+        ts[1] /= s
+        ts[0] /= math.sqrt(s)
+        ts[4] /= math.sqrt(s)
+        us = orc.forward(c, ts, n)
+        assert np.max(np.abs(us - u0)) <= 1e-9 * np.max(np.abs(u0))
+    # breaking one combination changes the trajectory well above rounding
+    tb = th.copy()
+    tb[2] *= 2.0
+    tb[1] /= 2.0
+    tb[0] /= 2.0                      # E* R instead of E* sqrt(R)
+    ub = orc.forward(c, tb, n)
+    assert np.max(np.abs(ub - u0)) >= 1e-4 * np.max(np.abs(u0))
+
+
+def _ld_inverse(A):
+    """Inverse of a small dense matrix by Gauss-Jordan with partial pivoting,
+    in the array's own (extended) precision."""
+    n = A.shape[0]
+    G = np.concatenate([A, np.eye(n, dtype=A.dtype)], axis=1)
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(G[k:, k])))
+        G[[k, p]] = G[[p, k]]
+        G[k] /= G[k, k]
+        for i in range(n):
+            if i != k:
+                G[i] -= G[i, k] * G[k]
+    return G[:, n:]
+
+
+_EXTENDED = np.finfo(np.longdouble).eps < 1e-18
+
+
+@pytest.mark.skipif(not _EXTENDED, reason="needs an extended-precision long double")
+def test_fe_first_frequency_exact_to_rounding(orc):
+    """Reading R13 drives the FE beam at its own first frequency, which an
+    FP64 eigensolver fixes only to ~eps lambda_max / lambda_1 (~3e-9 here).
+    The oracle's w1^2 and w2^2 equal the generalized eigenvalues of its K, M
+    computed in extended precision (inverse iteration, Rayleigh quotient)."""
+    spec = W.get("c5", cycles=1)
+    c = orc.make_case(spec)
+    M, K, _, geom = orc.fe_matrices(c)
+    LD = np.longdouble
+    ML, KL = M.astype(LD), K.astype(LD)
+    lam64 = scipy.linalg.eigh(K, M, eigvals_only=True)
+    for k, w in ((0, geom[3]), (1, geom[4])):
+        Ainv = _ld_inverse(KL - LD(lam64[k]) * ML)
+        x = np.ones(K.shape[0], dtype=LD)
+        for _ in range(4):
+            x = Ainv @ (ML @ x)
+            x /= np.max(np.abs(x))
+        lam = (x @ KL @ x) / (x @ ML @ x)
+        assert abs(float(LD(w) * LD(w) / lam - 1)) <= 1e-13
+    # the FP64 eigensolver alone is off by far more (what the refinement is for)
+    assert abs(lam64[0] / float(geom[3]) ** 2 - 1) > 1e-11
+
+
+@pytest.mark.skipif(not _EXTENDED, reason="needs an extended-precision long double")
+def test_fe_recursion_rounding_against_extended_precision(orc):
+    """The oracle's FP64 FE solve (three-term Newmark recursion in physical
+    coordinates, Newton for the implicit tip force) against the same
+    recursion carried out in extended precision: over 20 cycles the FP64
+    rounding stays below 1e-8 of the deflection."""
+    spec = W.get("c5", cycles=20)
+    c, pm = orc.make_case(spec), orc.make_pmap(spec)
+    th = orc.map_x(pm, np.array([0.4, 0.6, 0.5, 0.5]))
+    N = W.n_steps(spec)
+    u64, setup = orc.fe_forward(c, th, N, want_setup=True)
+    w1, a, psi, h = (float(setup[i]) for i in (0, 4, 5, 6))
+    M, K, Cm, _ = orc.fe_matrices(c)
+    n = M.shape[0]
+    tip = n - 2
+    r = np.zeros(n)
+    r[0::2] = 1.0
+    Mr = M @ r
+    X = np.linalg.solve(K - w1 * w1 * M + 1j * w1 * Cm, Mr.astype(complex))
+    LD = np.longdouble
+    u0 = (a * w1 * w1 * X * np.exp(1j * psi)).imag.astype(LD)
+    um = (a * w1 * w1 * X * np.exp(1j * (psi - w1 * h))).imag.astype(LD)
+    hL = LD(h)
+    q = hL * hL / LD(4)
+    ML, KL, CL = M.astype(LD), K.astype(LD), Cm.astype(LD)
+    Sinv = _ld_inverse(ML + hL / LD(2) * CL + q * KL)
+    P1 = LD(2) * ML - hL * hL / LD(2) * KL
+    P2 = ML - hL / LD(2) * CL + q * KL
+    s = Sinv[:, tip].copy()
+    E_, H_, R_, a0_ = (LD(v) for v in th[:4])
+    Zc = LD(c.Zc)
+
+    def F(d):
+        if d > a0_:
+            return -H_ * R_ / (LD(6) * d * d)
+        de = a0_ - d
+        return LD(4) / LD(3) * E_ * np.sqrt(R_) * de * np.sqrt(de) - H_ * R_ / (LD(6) * a0_ * a0_)
+
+    def dF(d):
+        if d > a0_:
+            return H_ * R_ / (LD(3) * d * d * d)
+        return LD(-2) * E_ * np.sqrt(R_) * np.sqrt(a0_ - d)
+
+    MrL = Mr.astype(LD)
+    Fm, F0 = F(Zc + um[tip]), F(Zc + u0[tip])
+    spc = c.spc
+    aw, wh, psiL = LD(a) * LD(w1) * LD(w1), LD(w1) * hL, LD(psi)
+    out = np.zeros(N)
+    for step in range(N):
+        G = (aw * np.sin(wh * LD((step + 1) % spc) + psiL) + LD(2) * aw * np.sin(wh * LD(step % spc) + psiL)
+             + aw * np.sin(wh * LD((step - 1 + spc) % spc) + psiL))
+        rhs = q * MrL * G + P1 @ u0 - P2 @ um
+        rhs[tip] += q * (LD(2) * F0 + Fm)
+        sol = Sinv @ rhs
+        z = sol[tip]
+        for _ in range(60):
+            dz = (z - sol[tip] - q * s[tip] * F(Zc + z)) / (LD(1) - q * s[tip] * dF(Zc + z))
+            z -= dz
+            if abs(dz) <= LD(1e-19) * (abs(z) + LD(1e-30)):
+                break
+        Fp = F(Zc + z)
+        um, u0 = u0, sol + q * s * Fp
+        Fm, F0 = F0, Fp
+        out[step] = float(u0[tip])
+    assert np.linalg.norm(u64 - out) <= 1e-8 * np.linalg.norm(out)
