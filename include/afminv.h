@@ -337,8 +337,11 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
  * pixels per candidate (synchronous: make that call before any capture of
  * `stream`) and caches the fastest in the context.  The choice used is
  * written back to *particles_per_thread if non-NULL.
- * workspace: device, >= afm_invert_batch_workspace_size(n_pix), 256-aligned. */
-afm_status afm_invert_batch_workspace_size(int n_pix, size_t* bytes);
+ * workspace: device, >= afm_invert_batch_workspace_size(prob, n_pix),
+ * 256-aligned (the queue, and the FP64 re-evaluation of every pixel's winner
+ * by multiple shooting: ~250 bytes per 32-step segment of the longest record
+ * and pixel, 1.6 GB for 4096 records of 51 200 steps). */
+afm_status afm_invert_batch_workspace_size(const afm_problem* prob, int n_pix, size_t* bytes);
 afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
                             const int64_t* off, int n_pix, uint32_t pixel0,
                             const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,

@@ -126,7 +126,7 @@ def lib():
                                                              i, i, i, C.POINTER(C.c_size_t)]
             L.afm_invert_polished.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), i, i,
                                               i, i, vp, C.c_size_t, vp, vp, vp]
-            L.afm_invert_batch_workspace_size.argtypes = [i, C.POINTER(C.c_size_t)]
+            L.afm_invert_batch_workspace_size.argtypes = [C.POINTER(Problem), i, C.POINTER(C.c_size_t)]
             L.afm_invert_batch.argtypes = [vp, C.POINTER(Problem), vp, vp, i, u32,
                                            C.POINTER(PsoCfg), vp, C.c_size_t, vp,
                                            C.POINTER(C.c_int), vp]
@@ -491,9 +491,9 @@ def invert_polished(prob: Problem, U, cfg: PsoCfg, polish_k: int = 32, polish_st
     return result, history
 
 
-def invert_batch_workspace_size(n_pix: int) -> int:
+def invert_batch_workspace_size(prob: Problem, n_pix: int) -> int:
     n = C.c_size_t()
-    _check(lib().afm_invert_batch_workspace_size(int(n_pix), C.byref(n)))
+    _check(lib().afm_invert_batch_workspace_size(C.byref(prob), int(n_pix), C.byref(n)))
     return int(n.value)
 
 
@@ -505,7 +505,7 @@ def invert_batch(prob: Problem, U_cat, off, cfg: PsoCfg, pixel0: int = 0,
     import torch
     dev = U_cat.device
     n_pix = int(off.shape[0]) - 1
-    nbytes = invert_batch_workspace_size(n_pix)
+    nbytes = invert_batch_workspace_size(prob, n_pix)
     if workspace is None or workspace.numel() < nbytes:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     if results is None:

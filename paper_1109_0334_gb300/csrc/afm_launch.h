@@ -65,8 +65,6 @@ cudaError_t batch_sort(const int64_t* off, int n_pix, int* order, cudaStream_t s
 cudaError_t batch_occupancy(int m, int force, int kp, int P, int D, int spc2, int* blocks_per_sm);
 cudaError_t launch_batch(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a, int kp,
                          int grid, cudaStream_t st);
-cudaError_t launch_batch_final(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
-                               cudaStream_t st);
 
 // discrete adjoint (gradient of the misfit wrt the normalised parameters)
 // Ragged form (off != nullptr): particle p belongs to queue slot p / per_slot,
@@ -205,6 +203,24 @@ struct ReevalPtrs {
     double* sumU2;        // [1]
     int B;
 };
+// The same for every queue slot of a batch (kern_reeval_batch.cu): slot i
+// owns segments [i maxB, (i + 1) maxB) of the segment arrays.
+struct ReevalBatch {
+    double* coef;   // [n_pix][4] FP64 force coefficients of each slot's winner
+    double* tab;    // [spc2 + 1] FP64 drive table
+    double* Z;      // [n_pix * maxB][2m] segment start states (corrected in place)
+    double* E;      // [n_pix * maxB][2m] segment end states
+    float* J;       // [n_pix * maxB][2m][2m] segment tangent maps (FP32)
+    double* Sb;     // [n_pix * maxB] segment misfit shares
+    double* u2;     // [n_pix] sum of U^2 of each slot's record
+    int maxB;       // segments of the longest record (problem n_steps)
+};
+size_t reeval_batch_bytes(int m, int n_steps, int spc, int n_pix);
+void reeval_batch_carve(void* base, int m, int n_steps, int spc, int n_pix, ReevalBatch* R);
+// fills each slot's result record (S_f64, J_rel, theta, status, defect,
+// segments) from the parameters already in it
+cudaError_t launch_reeval_batch(const KConst<float>& Kf, const KConst<double>& Kd,
+                                const ReevalBatch& R, const BatchArgs& a, cudaStream_t st);
 bool reeval_supported(int m, int n_steps);
 size_t reeval_bytes(int m, int n_steps, int spc);
 void reeval_carve(void* base, int m, int n_steps, int spc, ReevalPtrs* R);

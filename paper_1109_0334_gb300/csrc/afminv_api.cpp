@@ -712,6 +712,14 @@ BatchLayout batch_layout(int n_pix) {
     return L;
 }
 
+// The queue, then the FP64 re-evaluation of every slot's winner (segments
+// for the longest record, problem n_steps).
+size_t batch_ws_bytes(const afm_problem& pr, int n_run) {
+    return batch_layout(n_run).total +
+           align256(afm::reeval_batch_bytes(problem_modes(pr), pr.n_steps, pr.steps_per_cycle,
+                                            n_run));
+}
+
 template <typename T>
 void append_bytes(std::vector<unsigned char>& v, const T& x) {
     const unsigned char* p = reinterpret_cast<const unsigned char*>(&x);
@@ -1401,10 +1409,12 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
     return AFM_OK;
 }
 
-afm_status afm_invert_batch_workspace_size(int n_pix, size_t* bytes) {
+afm_status afm_invert_batch_workspace_size(const afm_problem* prob, int n_pix, size_t* bytes) {
     g_err[0] = 0;
     if (!bytes || n_pix < 1) return fail(AFM_ERR_INVALID_ARG, "n_pix >= 1 and bytes needed");
-    *bytes = batch_layout(n_pix).total;
+    afm_status st = check_problem(prob);
+    if (st) return st;
+    *bytes = batch_ws_bytes(*prob, n_pix);
     return AFM_OK;
 }
 
@@ -1420,6 +1430,7 @@ struct BatchSetup {
     KConst<double> Kd;
     afm::PsoConst pc;
     afm::BatchArgs a;
+    afm::ReevalBatch R;   // FP64 re-evaluation of the winners (after the queue)
     int kp, grid;
 };
 
@@ -1442,11 +1453,14 @@ afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat
     if (smem > 200 * 1024)
         return fail(AFM_ERR_INVALID_ARG, "swarm state of %zu bytes exceeds shared memory", smem);
     // queue (and sort order) sized for the pixels inverted
-    const BatchLayout L = batch_layout(select != nullptr ? select->n_run : n_pix);
+    const int n_run = select != nullptr ? select->n_run : n_pix;
+    const BatchLayout L = batch_layout(n_run);
     char* ws = static_cast<char*>(workspace);
     BatchSetup& B = *out;
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, B.Kf);
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, B.Kd);
+    afm::reeval_batch_carve(ws + L.total, problem_modes(*prob), prob->n_steps,
+                            prob->steps_per_cycle, n_run, &B.R);
     B.pc = pso_const(*cfg, prob->n_free);
     afm::BatchArgs& a = B.a;
     std::memset(&a, 0, sizeof(a));   // also the padding: the struct is part of a graph key
@@ -1506,9 +1520,11 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
                             afm_result* results, int* particles_per_thread, void* stream) {
     AFM_TRACE("afm_invert_batch");
     g_err[0] = 0;
-    if (n_pix >= 1 && workspace_bytes < batch_layout(n_pix).total)
+    afm_status st0;
+    if ((st0 = check_problem(prob))) return st0;
+    if (n_pix >= 1 && workspace_bytes < batch_ws_bytes(*prob, n_pix))
         return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes,
-                    batch_layout(n_pix).total);
+                    batch_ws_bytes(*prob, n_pix));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     BatchSetup B;
     afm_status st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, cfg, workspace, results,
@@ -1539,7 +1555,7 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
         cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), c);
         if (e == cudaSuccess && a.order) e = afm::batch_sort(off, n_pix, const_cast<int*>(a.order), c);
         if (e == cudaSuccess) e = afm::launch_batch(Kf, pc, a, kp, grid, c);
-        if (e == cudaSuccess) e = afm::launch_batch_final(Kd, pc, a, c);
+        if (e == cudaSuccess) e = afm::launch_reeval_batch(Kf, Kd, B.R, a, c);
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(c, &graph);
         if (e != cudaSuccess) {
@@ -1573,7 +1589,7 @@ static BatchPolishLayout batch_polish_layout(const afm_problem& pr, const afm_ps
                                              int Kc, int J, int method) {
     BatchPolishLayout L;
     const size_t D = (size_t)pr.n_free, P = (size_t)cfg.P, Nt = (size_t)n_pix * Kc;
-    size_t off = batch_layout(n_pix).total;
+    size_t off = batch_ws_bytes(pr, n_pix);
     L.pb = off; off += align256(sizeof(float) * (size_t)n_pix * (D + 1) * P);
     L.xk = off; off += align256(sizeof(float) * D * Nt);
     L.Sk = off; off += align256(sizeof(float) * Nt);
@@ -1664,7 +1680,7 @@ static afm_status batch_polished_run(afm_ctx* ctx, const afm_problem* prob, cons
             return st;
     AFM_CUDA(afm::launch_pick_pix(n_pix, D, Kc, xk, Sk, ik, a.order, cfg->iters, results, s),
              "winner pick kernel");
-    AFM_CUDA(afm::launch_batch_final(B.Kd, B.pc, a, s), "batch FP64 kernel");
+    AFM_CUDA(afm::launch_reeval_batch(B.Kf, B.Kd, B.R, a, s), "batch FP64 re-evaluation");
     return AFM_OK;
 }
 

@@ -5,7 +5,8 @@
 // personal bests in shared memory, the global best reduced with warp shuffles
 // and one shared-memory pass, every swarm evaluation the fused RK4 (Eq. 2) +
 // misfit (Eq. 5) time loop with KP particles per thread.  No block waits on
-// another block.  A second kernel re-evaluates every pixel's winner in FP64.
+// another block.  Every pixel's winner is then re-evaluated in FP64 by
+// multiple shooting in time (kern_reeval_batch.cu).
 // The kernels are in kern_batch.cuh; this file holds the force dispatch, the
 // queue-order sort and the shared helpers.
 #include <type_traits>
@@ -78,9 +79,7 @@ int batch_sort_max() { return SORT_MAX; }
 #define AFM_BATCH_DECLARE(F)                                                                   \
     template <> cudaError_t batch_occupancy_of<F>(int, int, int, int, int, int*);              \
     template <> cudaError_t batch_launch_of<F>(const KConst<float>&, const PsoConst&,          \
-                                               const BatchArgs&, int, int, cudaStream_t);      \
-    template <> cudaError_t batch_final_of<F>(const KConst<double>&, const PsoConst&,          \
-                                              const BatchArgs&, cudaStream_t);
+                                               const BatchArgs&, int, int, cudaStream_t);
 AFM_BATCH_DECLARE(F_LINEAR)
 AFM_BATCH_DECLARE(F_DMT)
 AFM_BATCH_DECLARE(F_DMT_KV)
@@ -113,11 +112,6 @@ cudaError_t launch_batch(const KConst<float>& K, const PsoConst& pc, const Batch
     return by_force(K.force, [&](auto Fc) {
         return batch_launch_of<decltype(Fc)::value>(K, pc, a, kp, grid, st);
     });
-}
-
-cudaError_t launch_batch_final(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
-                               cudaStream_t st) {
-    return by_force(K.force, [&](auto Fc) { return batch_final_of<decltype(Fc)::value>(K, pc, a, st); });
 }
 
 }  // namespace afm

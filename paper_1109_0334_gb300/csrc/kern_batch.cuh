@@ -185,45 +185,6 @@ __global__ void __launch_bounds__(1024) batch_kernel(const KConst<float> K, cons
     }
 }
 
-// ---------------------------------------------------------------------------
-// FP64 re-evaluation of every pixel's winner: one thread per pixel, pixels
-// taken in queue order so that a warp holds records of similar length.
-// ---------------------------------------------------------------------------
-template <int M, int FORCE>
-__global__ void batch_final_kernel(const KConst<double> K, const PsoConst pc, const BatchArgs a) {
-    extern __shared__ __align__(16) double smd[];
-    build_drive_table(K, smd);
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n_pix) return;
-    const int pix = a.order != nullptr ? a.order[i] : i;
-    const int64_t o = a.off[pix];
-    const int n = (int)(a.off[pix + 1] - o);
-    const float* U = a.U + o;
-    afm_result* r = a.res + pix;
-    double xd[AFM_MAXD];
-    for (int d = 0; d < AFM_MAXD; ++d) xd[d] = r->x[d];
-    Coef<double> c = make_coef<double, double>(K, xd);
-    const double S64 = integrate<double, M, FORCE, float>(K, c, smd, U, nullptr, 0, 0, n);
-    double u2 = 0.0;
-    for (int s = 0; s < n; ++s) u2 += (double)U[s] * (double)U[s];
-    double th[AFM_MAXD];
-    for (int s = 0; s < AFM_MAXD; ++s) th[s] = K.fixed[s];
-    for (int d = 0; d < pc.D; ++d) {
-        double v = K.lo[d] + xd[d] * K.span[d];
-        th[K.slot[d]] = K.logs[d] ? exp10(v) : v;
-    }
-    for (int s = 0; s < AFM_MAXD; ++s) r->theta[s] = th[s];
-    r->S_f64 = S64;
-    r->J_rel = u2 > 0.0 ? sqrt(S64 / u2) : 0.0;
-    r->status = (isfinite(S64) && r->nonfinite == 0) ? AFM_OK : AFM_ERR_NONFINITE;
-    r->defect = 0.0;
-    r->segments = 0;
-    r->reserved = 0;
-    for (int k = 0; k < 3; ++k) r->drive[k] = 0.0;
-}
-
-
 // Launch helpers of one force law (explicitly instantiated per force).
 template <int FORCE>
 struct BatchOps {
@@ -272,23 +233,6 @@ struct BatchOps {
             return cudaGetLastError();
         });
     }
-
-    static cudaError_t final_(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
-                              cudaStream_t st) {
-        const size_t smem = sizeof(double) * (size_t)(K.spc2 + 1);
-        const int threads = 32;
-        const int blocks = (a.n_pix + threads - 1) / threads;
-        return by_mk(K.m, 1, [&](auto Mc, auto) -> cudaError_t {
-            auto kern = batch_final_kernel<decltype(Mc)::value, FORCE>;
-            if (smem > 48 * 1024) {
-                cudaError_t e = cudaFuncSetAttribute(
-                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e != cudaSuccess) return e;
-            }
-            kern<<<blocks, threads, smem, st>>>(K, pc, a);
-            return cudaGetLastError();
-        });
-    }
 };
 
 
@@ -300,8 +244,5 @@ cudaError_t batch_occupancy_of(int m, int kp, int P, int D, int spc2, int* block
 template <int FORCE>
 cudaError_t batch_launch_of(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a, int kp,
                             int grid, cudaStream_t st);
-template <int FORCE>
-cudaError_t batch_final_of(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
-                           cudaStream_t st);
 
 }  // namespace afm

@@ -12,9 +12,4 @@ cudaError_t batch_launch_of<F_DMT>(const KConst<float>& K, const PsoConst& pc, c
                                   int kp, int grid, cudaStream_t st) {
     return BatchOps<F_DMT>::launch(K, pc, a, kp, grid, st);
 }
-template <>
-cudaError_t batch_final_of<F_DMT>(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
-                                 cudaStream_t st) {
-    return BatchOps<F_DMT>::final_(K, pc, a, st);
-}
 }  // namespace afm

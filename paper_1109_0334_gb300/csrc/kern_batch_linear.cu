@@ -12,9 +12,4 @@ cudaError_t batch_launch_of<F_LINEAR>(const KConst<float>& K, const PsoConst& pc
                                   int kp, int grid, cudaStream_t st) {
     return BatchOps<F_LINEAR>::launch(K, pc, a, kp, grid, st);
 }
-template <>
-cudaError_t batch_final_of<F_LINEAR>(const KConst<double>& K, const PsoConst& pc, const BatchArgs& a,
-                                 cudaStream_t st) {
-    return BatchOps<F_LINEAR>::final_(K, pc, a, st);
-}
 }  // namespace afm

@@ -115,7 +115,7 @@ __global__ void fwd_ragged_kernel(const KConst<float> K, const float* __restrict
 
 // Per slot: the polished candidate of lowest misfit (first on ties) becomes
 // the pixel's winner (x, FP32 S, swarm index); the FP64 re-evaluation of
-// batch_final_kernel follows.
+// kern_reeval_batch.cu follows.
 __global__ void pick_pix_kernel(int n_pix, int D, int Kc, const float* __restrict__ xk,
                                 const float* __restrict__ Sk, const int* __restrict__ ik,
                                 const int* __restrict__ order, int iters,

@@ -93,6 +93,8 @@ def test_batch_oracle_parity_and_autotune(orc, afm):
         assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2
         assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2
         assert abs(r["J_rel"] - np.sqrt(S_g / np.sum(U_m ** 2))) <= 1e-9
+        # the FP64 value came from multiple shooting over 32-step segments
+        assert r["segments"] == -(-len(U_m) // 32) and r["defect"] <= 1e-9
 
 
 def test_batch_edge_cases(orc, afm):
