@@ -1035,6 +1035,18 @@ def run_probe(args):
         torch.cuda.synchronize()
         print(json.dumps({"S_mean": float(S.mean()), "G_absmax": float(G.abs().max())}))
         return
+    if args.probe == "polish_full":
+        # the full 4096-pixel LM-polished batch, twice (the second after tuning)
+        spec, prob, U, off, total, _ = c3_inputs(A, W, torch.device("cuda"))
+        lp = spec["lm_polish"]
+        cfg = A.make_pso(dict(spec, iters=lp["iters"]))
+        for _ in range(2):
+            res, kp = A.invert_batch_polished(prob, U, off, cfg, lp["polish_k"], lp["polish_steps"],
+                                              lp["n_cand"], method="lm")
+        torch.cuda.synchronize()
+        out = A.decode_results(res)
+        print(json.dumps({"pixels": len(out), "kp": kp, "ok": sum(r["status"] == 0 for r in out)}))
+        return
     if args.probe == "polish":
         # one pixel wave of the LM-polished batch (records shortened tenfold)
         props = torch.cuda.get_device_properties(0)
@@ -1093,7 +1105,8 @@ def main():
     ap.add_argument("--no-f2", action="store_true", help="skip the paper's own experiments (tip-sample laws, base motion)")
     ap.add_argument("--no-image", action="store_true", help="skip the image warm-start comparison")
     ap.add_argument("--no-points", action="store_true", help="skip the deflection-points inversion")
-    ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint", "fe", "sens", "polish"],
+    ap.add_argument("--probe", choices=["invert", "forward", "batch", "adjoint", "fe", "sens", "polish",
+                                        "polish_full"],
                     default=None,
                     help="run one small untimed case for a profiler capture and exit")
     ap.add_argument("--probe-iters", type=int, default=2)
