@@ -792,7 +792,7 @@ afm_status set_error(afm_status st, const char* msg) { return fail(st, "%s", msg
 
 afm_status prepare_invert(afm_ctx* ctx, const afm_problem* prob, const afm_pso_cfg* cfg,
                           KConst<float>* Kf, KConst<double>* Kd, PsoConst* pc,
-                          size_t* scratch_bytes, int* device) {
+                          size_t* scratch_bytes, size_t* reeval_bytes, int* device) {
     afm_status st = check_problem(prob);
     if (st) return st;
     if ((st = modal_only(prob, "afm_invert_noalloc"))) return st;
@@ -802,6 +802,7 @@ afm_status prepare_invert(afm_ctx* ctx, const afm_problem* prob, const afm_pso_c
     fill_kconst(*prob, prob->steps_per_cycle, prob->n_steps, *Kd);
     *pc = pso_const(*cfg, prob->n_free);
     *scratch_bytes = invert_layout(cfg->P, prob->n_free).total;
+    *reeval_bytes = reeval_extra(*prob);
     *device = ctx->device;
     return AFM_OK;
 }

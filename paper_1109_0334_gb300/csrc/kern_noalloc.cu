@@ -15,7 +15,7 @@ namespace detail {
 afm_status set_error(afm_status st, const char* msg);
 afm_status prepare_invert(afm_ctx* ctx, const afm_problem* prob, const afm_pso_cfg* cfg,
                           KConst<float>* Kf, KConst<double>* Kd, PsoConst* pc,
-                          size_t* scratch_bytes, int* device);
+                          size_t* scratch_bytes, size_t* reeval_bytes, int* device);
 void carve_swarm(void* base, int P, int D, SwarmPtrs* sw);
 }  // namespace detail
 }  // namespace afm
@@ -60,9 +60,10 @@ extern "C" afm_status afm_invert_noalloc(afm_ctx* ctx, const afm_problem* prob, 
     afm::KConst<float> Kf;
     afm::KConst<double> Kd;
     afm::PsoConst pc;
-    size_t need = 0;
+    size_t need = 0, reeval = 0;
     int device = 0;
-    afm_status st = afm::detail::prepare_invert(ctx, prob, cfg, &Kf, &Kd, &pc, &need, &device);
+    afm_status st = afm::detail::prepare_invert(ctx, prob, cfg, &Kf, &Kd, &pc, &need, &reeval,
+                                                &device);
     if (st) return st;
     if (!U || !result) return afm::detail::set_error(AFM_ERR_INVALID_ARG, "NULL U or result");
     if (need > kScratchBytes)
@@ -78,7 +79,17 @@ extern "C" afm_status afm_invert_noalloc(afm_ctx* ctx, const afm_problem* prob, 
     cudaError_t e = afm::launch_pso_init(pc, sw, s);
     for (int it = 0; e == cudaSuccess && it <= pc.iters; ++it)
         e = afm::launch_invert_iter(Kf, pc, sw, U, history, it, s);
-    if (e == cudaSuccess) e = afm::launch_invert_final(Kd, pc, sw, U, history, result, s);
+    // the winner's FP64 re-evaluation by multiple shooting where the rest of
+    // the scratch holds its segments, else one sequential FP64 pass
+    const size_t at = (need + 255) & ~size_t(255);
+    if (e == cudaSuccess && reeval > 0 && at + reeval <= kScratchBytes) {
+        afm::ReevalPtrs R;
+        afm::reeval_carve(static_cast<char*>(base) + at, Kd.m, Kd.n_steps, Kd.spc2 / 2, &R);
+        e = afm::launch_reeval_pick_swarm(pc, sw, history, R.win, s);
+        if (e == cudaSuccess) e = afm::launch_reeval(Kf, Kd, R, U, pc.iters, sw.flags, result, s);
+    } else if (e == cudaSuccess) {
+        e = afm::launch_invert_final(Kd, pc, sw, U, history, result, s);
+    }
     if (e != cudaSuccess) return afm::detail::set_error(AFM_ERR_CUDA, cudaGetErrorString(e));
     return AFM_OK;
 }
