@@ -421,9 +421,12 @@ afm_status afm_invert_image(afm_ctx* ctx, const afm_problem* prob, const float* 
  * fixed array of AFM_NOALLOC_SCRATCH_BYTES inside the library's device data
  * (held by every GPU that loads the library until the process exits)
  * instead of a caller workspace; the caller still passes U, result and
- * history.  The swarm must fit: afm_invert_workspace_size() <=
- * AFM_NOALLOC_SCRATCH_BYTES (about P * D <= 200 000), else
- * AFM_ERR_INVALID_ARG.  It calls no cudaMalloc/cudaFree.
+ * history.  The swarm state must fit (about P * D <= 200 000), else
+ * AFM_ERR_INVALID_ARG.  The winner's FP64 re-evaluation runs by multiple
+ * shooting in the rest of the array when its segments fit (~440 bytes per
+ * 32 steps of record for 3 modes: records up to ~200 000 steps next to a
+ * C2-size swarm), else as one sequential FP64 pass (~7 us per step); the
+ * result's `segments` says which.  It calls no cudaMalloc/cudaFree.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) once; make that first call before any stream
  *     capture.
