@@ -919,11 +919,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded truth, GPU-made record at dt/4 + 0.5% A0 noise)",
-            "config": {"workload": "c2: 3-mode Euler-Bernoulli cantilever, DMT 4 unknowns, "
-                                   "1024 particles x 100 updates, 100 cycles x 256 steps",
-                       "particles": P, "updates": iters, "record_steps": N, "modes": m,
-                       "force": spec["force"], "per_rank": "one pixel inversion per step",
-                       "l2": "flushed between steps (256 MiB write)"},
+            "config": dict(workload_config(spec), per_rank="one pixel inversion per step",
+                           l2="flushed between steps (256 MiB write)"),
             "ms_per_inversion": T_ms / args.steps / 1.0,
             # init + (iters + 1) fused iterations + the FP64 re-evaluation
             # (pick, guess, 2 x (segment pass + join correction), final pass, result)
@@ -952,6 +949,16 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # Reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
+def workload_config(spec) -> dict:
+    """The benchmark's workload description, shared by both arms."""
+    from paper_1109_0334_gb300 import workloads as W
+    m = 1 if spec["model"] == "point_mass" else spec["n_modes"]
+    return {"workload": "c2: 3-mode Euler-Bernoulli cantilever, DMT 4 unknowns, "
+                        "1024 particles x 100 updates, 100 cycles x 256 steps",
+            "particles": spec["P"], "updates": spec["iters"], "record_steps": W.n_steps(spec),
+            "modes": m, "force": spec["force"]}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -973,8 +980,10 @@ def run_reference(args):
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "c2 (one whole-swarm evaluation per step)",
-                      "particles": spec["P"], "record_steps": n},
+           "config": dict(workload_config(spec),
+                          per_rank="one whole-swarm evaluation (1024 particles x 25 600 steps) "
+                                   "per step, FP64 oracle on the host cores",
+                          l2="host run"),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                             "sample": f"per step: {desc}"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
