@@ -212,3 +212,25 @@ def test_checkpoint_resume_is_bitwise(orc, afm, name):
     assert r["winner"] == g
     assert np.float32(r["S"]) == full.pbest_S.cpu().numpy()[g]
     np.testing.assert_array_equal(np.float32(r["x"][:D]), full.pbest_x.cpu().numpy()[:, g])
+
+
+@pytest.mark.parametrize("P", [1, 2, 31, 33])
+def test_degenerate_and_ragged_swarm_sizes(orc, afm, P):
+    """Swarms of one particle, and sizes that leave the last lane group or
+    warp partly empty: the automatic multi-lane iteration equals the
+    one-lane arithmetic of the batched-pixel kernel bit for bit, and the
+    history never rises."""
+    spec = W.get("c2", cycles=8, P=P, iters=4)
+    U32, _, _ = oracle_record(orc, spec)
+    prob = afm.make_problem(spec)
+    cfg = afm.make_pso(spec)
+    Ut = torch.from_numpy(U32).cuda()
+    r1, h1 = afm.invert(prob, Ut, cfg)
+    off = torch.tensor([0, len(U32)], dtype=torch.int64, device="cuda")
+    rb, _ = afm.invert_batch(prob, Ut, off, cfg, particles_per_thread=1)
+    torch.cuda.synchronize()
+    a, b = afm.decode_result(r1), afm.decode_results(rb)[0]
+    assert a["status"] == 0 and 0 <= a["winner"] < P
+    assert a["winner"] == b["winner"] and a["S"] == b["S"]
+    np.testing.assert_array_equal(a["x"], b["x"])
+    assert np.all(np.diff(h1.cpu().numpy()) <= 0)
