@@ -858,7 +858,7 @@ def run_ours(args):
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
             "unit": "T FP32 lane-ops/s", "frac": achieved / peak_ops,
             "traffic": ncu_traffic("invert_modes_kernel", args.workload),
-            "kernel": "invert_modes_kernel<3,DMT,2> (modes of a particle over two lanes)",
+            "kernel": "invert_modes_kernel<3,DMT,3> (one lane per mode of a particle)",
             "ops_per_particle_step": fp32_ops_per_step(m, spec["force"]),
             "launches_timed": kern_n, "avg_launch_ms": avg_launch_s * 1e3,
             "kernel_share_of_step": kern_ms / sum(step_ms),

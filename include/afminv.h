@@ -188,13 +188,16 @@ afm_status afm_ctx_destroy(afm_ctx* ctx);
  *                     laws, 2 or 3 modes, P <= 9728)
  *   AFM_LANES_MODES4  four lanes, one mode each (rate-free laws, 2 or 3
  *                     modes, P <= 4864)
+ *   AFM_LANES_MODES3  three lanes, one mode each, ten particles per warp
+ *                     (rate-free laws, 2 or 3 modes, P <= 6080)
  * Returns AFM_ERR_INVALID_ARG for an unknown value. */
 typedef enum {
     AFM_LANES_AUTO = 0,
     AFM_LANES_ONE = 1,
     AFM_LANES_STAGES = 2,
     AFM_LANES_MODES2 = 3,
-    AFM_LANES_MODES4 = 4
+    AFM_LANES_MODES4 = 4,
+    AFM_LANES_MODES3 = 5
 } afm_lanes;
 afm_status afm_set_lanes(afm_ctx* ctx, int lanes);
 /* Message of the last failed call on this thread ("" if none). */

@@ -172,12 +172,13 @@ def profile_enable(on: bool = True, device=None) -> None:
     _check(lib().afm_profile_enable(context(device), int(bool(on))))
 
 
-LANES = {"auto": 0, "one": 1, "stages": 2, "modes2": 3, "modes4": 4}
+LANES = {"auto": 0, "one": 1, "stages": 2, "modes2": 3, "modes4": 4, "modes3": 5}
 
 
 def set_lanes(lanes: str = "auto", device=None) -> None:
     """Lanes per particle of the fused inversion iteration (see afm_set_lanes):
-    'auto', 'one', 'stages', 'modes2' or 'modes4'; all are bit-identical."""
+    'auto', 'one', 'stages', 'modes2', 'modes3' or 'modes4'; all are
+    bit-identical."""
     _check(lib().afm_set_lanes(context(device), LANES[lanes]))
 
 

@@ -883,7 +883,7 @@ afm_status afm_profile_enable(afm_ctx* ctx, int on) {
 afm_status afm_set_lanes(afm_ctx* ctx, int lanes) {
     g_err[0] = 0;
     if (!ctx) return fail(AFM_ERR_INVALID_ARG, "context is NULL");
-    if (lanes < AFM_LANES_AUTO || lanes > AFM_LANES_MODES4)
+    if (lanes < AFM_LANES_AUTO || lanes > AFM_LANES_MODES3)
         return fail(AFM_ERR_INVALID_ARG, "unknown lanes variant %d", lanes);
     ctx->lanes = lanes;
     return AFM_OK;

@@ -197,16 +197,24 @@ cudaError_t launch_invert_iter(const KConst<float>& K, const PsoConst& pc, const
     // small swarms of rate-free force laws: several lanes per particle
     // (kern_modes.cu: modes split; kern_pair.cu: RK4 stage forces split).
     // Automatic choice, by measurement on the 3-mode DMT swarm of 1024
-    // particles (per launch: one lane 4.58 ms, stages 4.53, modes over 4
-    // lanes 4.40, modes over 2 lanes 4.30): modes over 2 lanes, else stages.
+    // particles (per launch: one lane 4.59 ms, stages 4.53, modes over 4
+    // lanes 4.41, over 2 lanes 4.30, over 3 lanes 3.66): one mode per lane
+    // for 3 modes, modes over 2 lanes for 2, else stages.
     const bool m2 = modes_supported(K.m, K.force, pc.P, 2);
     const bool m4 = modes_supported(K.m, K.force, pc.P, 4);
+    const bool m3 = modes_supported(K.m, K.force, pc.P, 3);
     const bool st2 = pair_supported(K.m, K.force, pc.P);
     const bool ok = lanes == AFM_LANES_ONE || (lanes == AFM_LANES_STAGES && st2) ||
-                    (lanes == AFM_LANES_MODES2 && m2) || (lanes == AFM_LANES_MODES4 && m4);
-    if (!ok) lanes = m2 ? AFM_LANES_MODES2 : st2 ? AFM_LANES_STAGES : AFM_LANES_ONE;
+                    (lanes == AFM_LANES_MODES2 && m2) || (lanes == AFM_LANES_MODES4 && m4) ||
+                    (lanes == AFM_LANES_MODES3 && m3);
+    if (!ok)
+        lanes = (K.m == 3 && m3) ? AFM_LANES_MODES3
+                : m2             ? AFM_LANES_MODES2
+                : st2            ? AFM_LANES_STAGES
+                                 : AFM_LANES_ONE;
     if (lanes == AFM_LANES_MODES2) return launch_invert_modes(K, pc, sw, U, history, it, 2, st);
     if (lanes == AFM_LANES_MODES4) return launch_invert_modes(K, pc, sw, U, history, it, 4, st);
+    if (lanes == AFM_LANES_MODES3) return launch_invert_modes(K, pc, sw, U, history, it, 3, st);
     if (lanes == AFM_LANES_STAGES) return launch_invert_pair(K, pc, sw, U, history, it, st);
     const int threads = pc.P <= 152 * 32 * 4 ? 32 : 128;
     const int blocks = (pc.P + threads - 1) / threads;

@@ -1,5 +1,5 @@
 // kern_modes.cu -- the fused inversion iteration with the modes of a particle
-// spread over L lanes (L = 2 or 4), for swarms too small to fill the GPU.
+// spread over L lanes (L = 2, 3 or 4), for swarms too small to fill the GPU.
 //
 // A swarm of ~1000 particles fills a few dozen warps, so the RK4 recurrence
 // of each particle (Sec. 3.2) runs at the latency of its dependency chain,
@@ -33,20 +33,39 @@ struct Slots {
 };
 
 // The force-independent part of accel's acceleration for one slot, then the
-// force through one final rounding (fma with tip 1 rounds as accel's add_rn;
-// tip 0 keeps an empty slot at rest).
-template <int S>
+// force through one final rounding, as accel's non-contractible add_rn.
+// With empty slots in the group the force enters as fma(tip, F, a) (tip 1
+// rounds as a + F, tip 0 keeps the slot at rest); with none, tip is known to
+// be 1 and the compiler would fold that fma into an add it may then fuse
+// with a force law ending in a product, so add_rn is written out.
+template <int S, bool ALL_REAL>
 __device__ __forceinline__ float slot_accel(const Slots<S>& C, int k, float q, float v, float g,
                                             float F) {
     float ai = fmaf(-C.wq[k], v, C.gam[k] * g);
     ai = fmaf(-C.w2lo[k], q, ai);
     ai = fmaf(-C.w2[k], q, ai);
-    return fmaf(C.tip[k], F, ai);
+    return ALL_REAL ? add_rn(ai, F) : fmaf(C.tip[k], F, ai);
 }
 
-// Sum of the partial sums of the L lanes of a group (xor butterfly).
+// Lanes of a warp per group: 32 / L groups per warp (L = 3: ten groups,
+// lanes 30 and 31 idle).
+template <int L>
+__device__ __forceinline__ int group_base(int wl) {
+    return L == 3 ? (wl / 3) * 3 : wl & ~(L - 1);
+}
+
+// Sum of the partial sums of the L lanes of a group in the one-lane order:
+// xor butterfly for L = 2, 4 ((p0 + p1) + (p2 + p3), p3 = 0 for three
+// modes); for L = 3 the three partials read at once, ((p0 + p1) + p2).
 template <int L>
 __device__ __forceinline__ float group_sum(float p) {
+    if (L == 3) {
+        const int g = group_base<3>(threadIdx.x & 31);
+        const float a = __shfl_sync(0xffffffffu, p, g);
+        const float b = __shfl_sync(0xffffffffu, p, g + 1);
+        const float c = __shfl_sync(0xffffffffu, p, g + 2);
+        return (a + b) + c;
+    }
     p = p + __shfl_xor_sync(0xffffffffu, p, 1);
     if (L == 4) p = p + __shfl_xor_sync(0xffffffffu, p, 2);
     return p;
@@ -66,6 +85,7 @@ __device__ __forceinline__ float integrate_modes(const KConst<float>& K, const C
                                                  const float* tab, const float* __restrict__ U,
                                                  int n, int lane) {
     constexpr int S = (M + L - 1) / L;
+    constexpr bool R = S * L == M;   // every slot holds a mode
     Slots<S> C;
     float q[S], v[S], cq[S], cv[S];
 #pragma unroll
@@ -111,9 +131,9 @@ __device__ __forceinline__ float integrate_modes(const KConst<float>& K, const C
         float a1[S], a2[S], vs2[S], qs3[S], vs3[S], qs4[S];
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            a1[k] = slot_accel<S>(C, k, q[k], v[k], g0, F1);
+            a1[k] = slot_accel<S, R>(C, k, q[k], v[k], g0, F1);
             vs2[k] = fmaf(3.f, a1[k], v[k]);
-            a2[k] = slot_accel<S>(C, k, qs2[k], vs2[k], gh, F2);
+            a2[k] = slot_accel<S, R>(C, k, qs2[k], vs2[k], gh, F2);
             qs3[k] = fmaf(3.f, vs2[k], q[k]);
             vs3[k] = fmaf(3.f, a2[k], v[k]);
             qs4[k] = fmaf(6.f, vs3[k], q[k]);
@@ -125,9 +145,9 @@ __device__ __forceinline__ float integrate_modes(const KConst<float>& K, const C
         const float F4 = tip_force<FORCE, float>(c, K.Zc + u4, 0.f);
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            const float a3 = slot_accel<S>(C, k, qs3[k], vs3[k], gh, F3);
+            const float a3 = slot_accel<S, R>(C, k, qs3[k], vs3[k], gh, F3);
             const float vs4 = fmaf(6.f, a3, v[k]);
-            const float a4 = slot_accel<S>(C, k, qs4[k], vs4, g1, F4);
+            const float a4 = slot_accel<S, R>(C, k, qs4[k], vs4, g1, F4);
             float Kq = v[k];
             Kq = fmaf(2.f, vs2[k], Kq);
             Kq = fmaf(2.f, vs3[k], Kq);
@@ -162,8 +182,11 @@ __global__ void invert_modes_kernel(const KConst<float> K, const PsoConst pc, Sw
     build_drive_table(K, tab);
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p0 = t / L;
-    const int lane = t % L;
+    constexpr int G = 32 / L;                       // particle groups per warp
+    const int wl = threadIdx.x & 31;
+    const bool in_group = wl < G * L;               // L = 3: lanes 30, 31 idle
+    const int p0 = in_group ? (t >> 5) * G + wl / L : pc.P;
+    const int lane = in_group ? wl - group_base<L>(wl) : 0;
     const bool owner = p0 < pc.P && lane == 0;
     const int p = min(p0, pc.P - 1);
     const int rd = it & 1, wr = (it + 1) & 1;
@@ -219,16 +242,17 @@ __global__ void invert_modes_kernel(const KConst<float> K, const PsoConst pc, Sw
 }
 
 bool modes_supported(int m, int force, int P, int lanes) {
-    return (lanes == 2 || lanes == 4) && (m == 2 || m == 3) &&
-           (force == F_LINEAR || force == F_DMT || force == F_HOOKE) && P <= 152 * 4 * 32 / lanes;
+    return (lanes == 2 || lanes == 3 || lanes == 4) && (m == 2 || m == 3) &&
+           (force == F_LINEAR || force == F_DMT || force == F_HOOKE) &&
+           P <= 152 * 4 * (32 / lanes);
 }
 
 cudaError_t launch_invert_modes(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
                                 const float* U, float* history, int it, int lanes,
                                 cudaStream_t st) {
     if (!modes_supported(K.m, K.force, pc.P, lanes)) return cudaErrorInvalidValue;
-    const int threads = 32;
-    const int blocks = (lanes * pc.P + threads - 1) / threads;
+    const int threads = 32, per_warp = 32 / lanes;
+    const int blocks = (pc.P + per_warp - 1) / per_warp;
     const size_t smem = sizeof(float) * (size_t)(K.spc2 + 1);
     auto go = [&](auto Mc, auto Fc, auto Lc) -> cudaError_t {
         invert_modes_kernel<decltype(Mc)::value, decltype(Fc)::value, decltype(Lc)::value>
@@ -237,6 +261,7 @@ cudaError_t launch_invert_modes(const KConst<float>& K, const PsoConst& pc, cons
     };
     auto byL = [&](auto Mc, auto Fc) -> cudaError_t {
         if (lanes == 2) return go(Mc, Fc, std::integral_constant<int, 2>{});
+        if (lanes == 3) return go(Mc, Fc, std::integral_constant<int, 3>{});
         return go(Mc, Fc, std::integral_constant<int, 4>{});
     };
     auto byF = [&](auto Mc) -> cudaError_t {

@@ -135,12 +135,14 @@ def test_invert_c2_full_size_parity(orc, afm):
     _check_inversion(orc, spec, U_m, r, np.array(gold["x"]), gold["S_m2"], hist)
 
 
-@pytest.mark.parametrize("lanes", ["auto", "one", "stages", "modes2", "modes4"])
+@pytest.mark.parametrize("lanes", ["auto", "one", "stages", "modes2", "modes3", "modes4"])
 @pytest.mark.parametrize("name,over", [
     ("c2", dict(cycles=12)),
     ("c1", dict(cycles=12)),
     ("c2", dict(cycles=12, n_modes=2)),
     ("c2", dict(cycles=12, force="linear_spring", fixed=[0.0] * 5,
+                free=[(0, 2.0, 20.0, False), (1, 10e-9, 20e-9, False)])),
+    ("c2", dict(cycles=12, n_modes=2, force="linear_spring", fixed=[0.0] * 5,
                 free=[(0, 2.0, 20.0, False), (1, 10e-9, 20e-9, False)])),
     ("c2", dict(cycles=12, force="hooke", fixed=[0.0] * 5,
                 free=[(0, 0.5, 8.0, True), (1, -2e-9, 4e-9, False)])),
