@@ -85,6 +85,12 @@ cudaError_t launch_sens(const KConst<float>& K, const float* x, int P, const flo
 // the same pass with one lane per parameter direction (kern_lm_lanes.cu);
 // launch_sens uses it when P x lanes fits one warp per SM sub-partition
 bool sens_lanes_preferred(int P, int D);
+// ... and with one lane per (direction, mode) pair for three modes and
+// rate-free laws (kern_lm_lanes.cu), preferred over the above where it fits
+bool sens_modes_supported(int m, int force, int P, int D);
+cudaError_t launch_sens_modes(const KConst<float>& K, const float* x, int P, const float* U,
+                              float* S, double* H, double* b, cudaStream_t st, const int64_t* off,
+                              const int* order, int per_slot);
 cudaError_t launch_sens_lanes(const KConst<float>& K, const float* x, int P, const float* U,
                               float* S, double* H, double* b, cudaStream_t st, const int64_t* off,
                               const int* order, int per_slot);

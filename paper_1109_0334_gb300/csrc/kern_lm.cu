@@ -258,6 +258,8 @@ cudaError_t launch_lm_select_hb(int D, int K, int J, float* x, float* S, double*
 cudaError_t launch_sens(const KConst<float>& K, const float* x, int P, const float* U, float* S,
                         double* H, double* b, cudaStream_t st, const int64_t* off, const int* order,
                         int per_slot) {
+    if (sens_modes_supported(K.m, K.force, P, K.D))
+        return launch_sens_modes(K, x, P, U, S, H, b, st, off, order, per_slot);
     if (sens_lanes_preferred(P, K.D))
         return launch_sens_lanes(K, x, P, U, S, H, b, st, off, order, per_slot);
     const int blocks = (P + kThreads - 1) / kThreads;

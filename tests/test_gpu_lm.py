@@ -23,7 +23,7 @@ def afm():
 
 @pytest.mark.parametrize("name", ["c1", "c2", "c4"])
 def test_lane_split_sensitivities_are_bit_identical(orc, afm, name):
-    """Few candidates run one lane per parameter direction (kern_lm_lanes.cu),
+    """Few candidates run several lanes per candidate (kern_lm_lanes.cu),
     many run one thread per candidate: S, H and b must agree bit for bit."""
     spec = W.get(name, cycles=4)
     U32, _, xt = oracle_record(orc, spec)
@@ -35,12 +35,20 @@ def test_lane_split_sensitivities_are_bit_identical(orc, afm, name):
     prob = afm.make_problem(spec)
     Ug = torch.from_numpy(U32).cuda()
     few = 11
-    S1, H1, b1 = afm.normal_equations(prob, torch.from_numpy(np.ascontiguousarray(x[:, :few])).cuda(), Ug)
-    S2, H2, b2 = afm.normal_equations(prob, torch.from_numpy(x).cuda(), Ug)
+    # few candidates: one lane per (direction, mode) for three modes and a
+    # rate-free law, else one lane per direction; a middle size past the
+    # first layout's limit takes the second
+    sizes = [few, 152 * 4 * 32 // (3 * D) + 1, P_big]
+    out = []
+    for n in sizes:
+        xs = torch.from_numpy(np.ascontiguousarray(x[:, :n])).cuda()
+        out.append(afm.normal_equations(prob, xs, Ug))
     torch.cuda.synchronize()
-    assert torch.equal(S1, S2[:few])
-    assert torch.equal(H1, H2[:few])
-    assert torch.equal(b1, b2[:few])
+    S2, H2, b2 = out[-1]
+    for S1, H1, b1 in out[:-1]:
+        assert torch.equal(S1[:few], S2[:few])
+        assert torch.equal(H1[:few], H2[:few])
+        assert torch.equal(b1[:few], b2[:few])
 
 
 @pytest.mark.parametrize("name,over", [("c2", dict(cycles=20)), ("c4", dict(cycles=20)),
