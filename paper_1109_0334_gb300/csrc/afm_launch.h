@@ -183,8 +183,17 @@ cudaError_t launch_forward_points_f32(const KConst<float>& K, const float* x, in
                                       const float* U, float* S, cudaStream_t st);
 cudaError_t launch_forward_points_f64(const KConst<double>& K, const double* x, int P, double* defl,
                                       const double* U, double* S, cudaStream_t st);
+// (lanes: AFM_LANES_ONE runs one lane per particle, any other value one
+// mode per lane where points_modes_supported; bit-identical)
 cudaError_t launch_invert_points(const KConst<float>& K, const PsoConst& pc, const SwarmPtrs& sw,
-                                 const float* U, float* history, int it, cudaStream_t st);
+                                 const float* U, float* history, int it, cudaStream_t st,
+                                 int lanes = 0);
+// the points iteration with one mode per lane (rate-free laws, 2 or 3
+// modes, lanes = modes, P <= 19456 / modes)
+bool points_modes_supported(int m, int force, int P, int np);
+cudaError_t launch_invert_points_modes(const KConst<float>& K, const PsoConst& pc,
+                                       const SwarmPtrs& sw, const float* U, float* history, int it,
+                                       cudaStream_t st);
 cudaError_t launch_points_final(const KConst<double>& K, const PsoConst& pc, const SwarmPtrs& sw,
                                 const float* U, float* history, void* result, cudaStream_t st);
 // winner re-evaluation in FP64 and result record

@@ -1106,7 +1106,7 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
     }
     for (int it = 0; it <= cfg->iters; ++it)
         AFM_CUDA(timed_launch(ctx, s, [&] {
-                     return prob->n_points > 0 ? afm::launch_invert_points(Kf, pc, sw, U, history, it, s)
+                     return prob->n_points > 0 ? afm::launch_invert_points(Kf, pc, sw, U, history, it, s, ctx->lanes)
                                                : afm::launch_invert_iter(Kf, pc, sw, U, history, it, s,
                                                                          ctx->lanes);
                  }),

@@ -17,6 +17,12 @@
 // for three modes, q0 + q1 for two) and every per-mode operation is
 // rk4_step's, so the result is bit-identical to the one-lane kernels (the
 // batched-pixel kernel, afm_forward_batch).
+//
+// Records at several points along the beam (the n_dp points of Sec. 3.2)
+// need every mode at every step: with one mode per lane (L = M) the lanes
+// read the group's M modes with M shuffles, which also give the stage-1 tip
+// deflection in the one-lane order, and each lane forms the point
+// deflections and the misfit as integrate_points does.
 #include <type_traits>
 
 #include "afm_device.cuh"
@@ -79,13 +85,17 @@ __device__ __forceinline__ float slot_sum(const float* x) {
     return s;
 }
 
-// Forward solve + compensated misfit of one particle on a lane group.
-template <int M, int FORCE, int L>
+// Forward solve + compensated misfit of one particle on a lane group; with
+// NP > 0 the misfit runs over the NP point deflections of each step (NP = 0:
+// the tip).  The record values of step s are loaded during step s - 1.
+template <int M, int FORCE, int L, int NP>
 __device__ __forceinline__ float integrate_modes(const KConst<float>& K, const Coef<float>& c,
                                                  const float* tab, const float* __restrict__ U,
                                                  int n, int lane) {
     constexpr int S = (M + L - 1) / L;
     constexpr bool R = S * L == M;   // every slot holds a mode
+    constexpr bool POINTS = NP > 0;
+    static_assert(!POINTS || L == M, "point records need one mode per lane");
     Slots<S> C;
     float q[S], v[S], cq[S], cv[S];
 #pragma unroll
@@ -106,23 +116,55 @@ __device__ __forceinline__ float integrate_modes(const KConst<float>& K, const C
     int j = 0;
     const int spc2 = K.spc2;
     float Un = 0.f;
+    float Up[POINTS ? NP : 1];
+#pragma unroll
+    for (int k = 0; k < (POINTS ? NP : 1); ++k) Up[k] = (POINTS && n > 0) ? U[k] : 0.f;
     for (int s = 0; s <= n; ++s) {
         float qs2[S];
 #pragma unroll
         for (int k = 0; k < S; ++k) qs2[k] = fmaf(3.f, v[k], q[k]);
         // round 1: the step's start deflection (the previous step's output)
         // and the stage-2 deflection
-        const float u1 = group_sum<L>(slot_sum<S>(q));
-        const float u2 = group_sum<L>(slot_sum<S>(qs2));
-        if (s > 0) {
-            const float r = Un - u1;
-            const float y = fmaf(r, r, -cS);
-            const float t = add_rn(S2, y);
-            cS = sub_rn(sub_rn(t, S2), y);
-            S2 = t;
+        float u1, u2;
+        if constexpr (POINTS) {
+            const int g = group_base<L>(threadIdx.x & 31);
+            float qa[M];
+#pragma unroll
+            for (int i = 0; i < M; ++i) qa[i] = __shfl_sync(0xffffffffu, q[0], g + i);
+            u1 = qa[0];
+#pragma unroll
+            for (int i = 1; i < M; ++i) u1 += qa[i];
+            u2 = group_sum<L>(slot_sum<S>(qs2));
+            if (s > 0) {
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    float uk = K.phi[k][0] * qa[0];
+#pragma unroll
+                    for (int i = 1; i < M; ++i) uk = fmaf(K.phi[k][i], qa[i], uk);
+                    const float r = Up[k] - uk;
+                    const float y = fmaf(r, r, -cS);
+                    const float t = add_rn(S2, y);
+                    cS = sub_rn(sub_rn(t, S2), y);
+                    S2 = t;
+                }
+                if (s < n) {
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) Up[k] = U[(size_t)s * NP + k];
+                }
+            }
+        } else {
+            u1 = group_sum<L>(slot_sum<S>(q));
+            u2 = group_sum<L>(slot_sum<S>(qs2));
+            if (s > 0) {
+                const float r = Un - u1;
+                const float y = fmaf(r, r, -cS);
+                const float t = add_rn(S2, y);
+                cS = sub_rn(sub_rn(t, S2), y);
+                S2 = t;
+            }
         }
         if (s == n) break;
-        Un = U[s];
+        if constexpr (!POINTS) Un = U[s];
         const float g0 = tab[j], gh = tab[j + 1], g1 = tab[j + 2];
         j += 2;
         if (j >= spc2) j = 0;
@@ -173,7 +215,7 @@ __device__ __forceinline__ unsigned long long modes_key(float S, int p) {
 // of a group move the particle identically (lane 0 stores), integrate it
 // together, and lane 0 updates the bests.  Groups beyond P run the last
 // particle without storing (the shuffles need every lane).
-template <int M, int FORCE, int L>
+template <int M, int FORCE, int L, int NP>
 __global__ void invert_modes_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
                                     const float* __restrict__ U, float* __restrict__ history,
                                     int it) {
@@ -216,7 +258,7 @@ __global__ void invert_modes_kernel(const KConst<float> K, const PsoConst pc, Sw
             }
     }
     const Coef<float> c = make_coef<float, float>(K, x);
-    float s = integrate_modes<M, FORCE, L>(K, c, tab, U, K.n_steps, lane);
+    float s = integrate_modes<M, FORCE, L, NP>(K, c, tab, U, K.n_steps, lane);
     unsigned long long key = ~0ull;
     if (owner) {
         if (!(s < INFINITY)) {
@@ -255,7 +297,7 @@ cudaError_t launch_invert_modes(const KConst<float>& K, const PsoConst& pc, cons
     const int blocks = (pc.P + per_warp - 1) / per_warp;
     const size_t smem = sizeof(float) * (size_t)(K.spc2 + 1);
     auto go = [&](auto Mc, auto Fc, auto Lc) -> cudaError_t {
-        invert_modes_kernel<decltype(Mc)::value, decltype(Fc)::value, decltype(Lc)::value>
+        invert_modes_kernel<decltype(Mc)::value, decltype(Fc)::value, decltype(Lc)::value, 0>
             <<<blocks, threads, smem, st>>>(K, pc, sw, U, history, it);
         return cudaGetLastError();
     };
@@ -269,6 +311,44 @@ cudaError_t launch_invert_modes(const KConst<float>& K, const PsoConst& pc, cons
             case F_LINEAR: return byL(Mc, std::integral_constant<int, F_LINEAR>{});
             case F_DMT: return byL(Mc, std::integral_constant<int, F_DMT>{});
             case F_HOOKE: return byL(Mc, std::integral_constant<int, F_HOOKE>{});
+        }
+        return cudaErrorInvalidValue;
+    };
+    if (K.m == 2) return byF(std::integral_constant<int, 2>{});
+    return byF(std::integral_constant<int, 3>{});
+}
+
+bool points_modes_supported(int m, int force, int P, int np) {
+    return np >= 1 && np <= 4 && modes_supported(m, force, P, m);
+}
+
+// The deflection-points iteration with one mode per lane (L = M).
+cudaError_t launch_invert_points_modes(const KConst<float>& K, const PsoConst& pc,
+                                       const SwarmPtrs& sw, const float* U, float* history, int it,
+                                       cudaStream_t st) {
+    if (!points_modes_supported(K.m, K.force, pc.P, K.np)) return cudaErrorInvalidValue;
+    const int per_warp = 32 / K.m;
+    const int blocks = (pc.P + per_warp - 1) / per_warp;
+    const size_t smem = sizeof(float) * (size_t)(K.spc2 + 1);
+    auto go = [&](auto Mc, auto Fc, auto Nc) -> cudaError_t {
+        constexpr int M = decltype(Mc)::value;
+        invert_modes_kernel<M, decltype(Fc)::value, M, decltype(Nc)::value>
+            <<<blocks, 32, smem, st>>>(K, pc, sw, U, history, it);
+        return cudaGetLastError();
+    };
+    auto byN = [&](auto Mc, auto Fc) -> cudaError_t {
+        switch (K.np) {
+            case 1: return go(Mc, Fc, std::integral_constant<int, 1>{});
+            case 2: return go(Mc, Fc, std::integral_constant<int, 2>{});
+            case 3: return go(Mc, Fc, std::integral_constant<int, 3>{});
+        }
+        return go(Mc, Fc, std::integral_constant<int, 4>{});
+    };
+    auto byF = [&](auto Mc) -> cudaError_t {
+        switch (K.force) {
+            case F_LINEAR: return byN(Mc, std::integral_constant<int, F_LINEAR>{});
+            case F_DMT: return byN(Mc, std::integral_constant<int, F_DMT>{});
+            case F_HOOKE: return byN(Mc, std::integral_constant<int, F_HOOKE>{});
         }
         return cudaErrorInvalidValue;
     };

@@ -72,3 +72,35 @@ def test_points_inversion(orc, afm):
     assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2
     # the FP64 re-evaluation over the points ran as multiple shooting
     assert r["segments"] == -(-W.n_steps(spec) // 32) and r["defect"] <= 1e-9
+
+
+@pytest.mark.parametrize("over", [
+    dict(),
+    dict(points=(0.25, 0.5, 0.75, 1.0)),
+    dict(n_modes=2, points=(0.5, 1.0), force="linear_spring", fixed=[0.0] * 5,
+         free=[(0, 2.0, 20.0, False), (1, 10e-9, 20e-9, False)]),
+    dict(force="hooke", fixed=[0.0] * 5, free=[(0, 0.5, 8.0, True), (1, -2e-9, 4e-9, False)]),
+])
+def test_points_inversion_one_mode_per_lane_is_bit_identical(orc, afm, over):
+    """The points iteration with one mode per lane (2 or 3 modes, rate-free
+    laws) against the one-lane kernel: the same swarm, bit for bit, on a
+    ragged swarm (77 particles: the last warp part-filled)."""
+    spec = W.get("f4_points", cycles=8, P=77, iters=6, **over)
+    U32, _, _ = oracle_record(orc, spec)
+    prob = afm.make_problem(spec)
+    cfg = afm.make_pso(spec)
+    Ut = torch.from_numpy(U32).cuda()
+    out = {}
+    for lanes in ("one", "auto"):
+        afm.set_lanes(lanes)
+        try:
+            r, h = afm.invert(prob, Ut, cfg)
+            torch.cuda.synchronize()
+        finally:
+            afm.set_lanes("auto")
+        out[lanes] = (afm.decode_result(r), h.cpu().numpy())
+    (a, ha), (b, hb) = out["one"], out["auto"]
+    assert a["status"] == 0 and b["status"] == 0
+    assert a["winner"] == b["winner"] and a["S"] == b["S"] and a["S_f64"] == b["S_f64"]
+    np.testing.assert_array_equal(a["x"], b["x"])
+    np.testing.assert_array_equal(ha, hb)
