@@ -49,6 +49,24 @@ def fp32_ops_per_step(m: int, force: str) -> int:
     return 4 * accel + 12 * m + 8 * m + (m - 1) + 5
 
 
+def fe_fp32_ops_per_step() -> int:
+    """FP32 add/mul/fma instructions per particle per step of the FP32 FE
+    kernel (DMT law, 64 modes on 8 lanes of 8 mode slots), counted from its
+    source.  Per lane: the force history term 1; per mode slot the increment
+    4 (+1 for slot 0's low word), the predicted tip term 4 compensated / 3
+    plain, the update 1 + 8 compensated (two Kahan sums) / 1 + 2 plain, slot
+    0 compensated and slots 1-7 plain; the group sum of the tip deflection 3;
+    one Newton step 15 (gap 1 + law 4.5, residual 2, update 2, gap 1 + law
+    4.5; the law's constant products hoisted, contact and free branches 5
+    and 4).  Lane 0 alone: the tip deflection and the compensated misfit 6.
+    ncu's FFMA + FADD + FMUL thread-instruction counters on a 10-cycle swarm
+    give 846 per particle-step (365 + 367 + 114) against these 862."""
+    slot0 = 4 + 1 + 4 + 1 + 8
+    slot_plain = 4 + 3 + 1 + 2
+    per_lane = 1 + slot0 + 7 * slot_plain + 3 + 15
+    return 8 * per_lane + 6
+
+
 # ---------------------------------------------------------------------------
 # nvidia-smi clock sampler (runs during the timed region)
 # ---------------------------------------------------------------------------
@@ -542,9 +560,7 @@ def run_c5(A, W, dev, peak_ops, flush, iters=None):
     ms = e0.elapsed_time(e1)
     r = A.decode_result(res)
     units = spec["P"] * (spec["iters"] + 1) * N
-    # FP32 lane-ops per particle-step of the FE kernel: 8 lanes x (8 modes x 13
-    # + tip sum/shuffles 6 + Newton 3 x 12 + misfit 5)
-    ops_ps = 8 * (8 * 13 + 6 + 36 + 5)
+    ops_ps = fe_fp32_ops_per_step()
     ach = spec["P"] * N * ops_ps / ((kms / max(kn, 1)) / 1e3)
     return {"workload": "c5: 32-element Hermite FE cantilever, Newmark beta=1/4, DMT 4 unknowns, "
                         "8192 particles x 60 updates, 50 cycles x 512 steps",
@@ -664,6 +680,21 @@ def run_points(A, W, dev, flush):
         out[label] = {"ms_per_inversion": e0.elapsed_time(e1), "record_values": int(U.numel()),
                       "ident_rel_err_vs_truth": ident_errors(list(r["theta"]), th_t)[:3],
                       "S_f64_nm2": r["S_f64"], "status": r["status"]}
+    # the same three-point inversion on the one-lane kernel (bit-identical)
+    prob, cfg, U = A.make_problem(spec), A.make_pso(spec), rec.reshape(-1)
+    A.set_lanes("one")
+    try:
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res, _ = A.invert(prob, U, cfg)
+        e1.record()
+        e1.synchronize()
+    finally:
+        A.set_lanes("auto")
+    r = A.decode_result(res)
+    out["three_points_one_lane"] = {"ms_per_inversion": e0.elapsed_time(e1),
+                                    "same_result": r["S_f64"] == out["three_points"]["S_f64_nm2"]}
     out["ident"] = "H R, E* sqrt(R), a0"
     return out
 

@@ -398,18 +398,23 @@ __device__ __forceinline__ T integrate_points(const KConst<T>& K, const Coef<T>&
         j += 2;
         if (j >= spc2) j = 0;
         rk4_step<T, M, FORCE>(K, c, q, v, cq, cv, g0, gh, g1);
-        for (int k = 0; k < np; ++k) {
-            T uk = K.phi[k][0] * q[0];
+        // unrolled to the largest point count (a uniform guard), so that the
+        // point deflections schedule alongside the step's arithmetic
 #pragma unroll
-            for (int i = 1; i < M; ++i) uk = fma(K.phi[k][i], q[i], uk);
-            const size_t idx = (size_t)s * np + k;
-            if (defl != nullptr) defl[idx * P + p] = uk;
-            if (U != nullptr) {
-                const T r = (T)U[idx] - uk;
-                const T y = fma(r, r, -cS);
-                const T t = add_rn(S, y);
-                cS = sub_rn(sub_rn(t, S), y);
-                S = t;
+        for (int k = 0; k < AFM_MAX_POINTS; ++k) {
+            if (k < np) {
+                T uk = K.phi[k][0] * q[0];
+#pragma unroll
+                for (int i = 1; i < M; ++i) uk = fma(K.phi[k][i], q[i], uk);
+                const size_t idx = (size_t)s * np + k;
+                if (defl != nullptr) defl[idx * P + p] = uk;
+                if (U != nullptr) {
+                    const T r = (T)U[idx] - uk;
+                    const T y = fma(r, r, -cS);
+                    const T t = add_rn(S, y);
+                    cS = sub_rn(sub_rn(t, S), y);
+                    S = t;
+                }
             }
         }
     }

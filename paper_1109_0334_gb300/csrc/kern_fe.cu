@@ -42,6 +42,18 @@ struct alignas(16) FeQ4 {
     T b1, d2, g, f;
 };
 
+// Which mode slots of a lane take compensated updates.  FP64: all.  FP32:
+// slot 0 only, the lowest AFM_FE_LANES modes, which hold the resonant
+// response and whose step increment is a small fraction of the coordinate
+// (omega h << 1), so that plain sums lose its low bits every step.  The
+// stiff modes above respond quasi-statically with amplitudes ~(omega_1 /
+// omega_i)^2 of the first mode's forced term and omega h ~ 1: their rounding
+// stays far below FP32 resolution of the tip deflection.
+template <typename T>
+__host__ __device__ constexpr bool fe_comp(int j) {
+    return sizeof(T) == 8 || j == 0;
+}
+
 // Drive term of the Newmark step at phase index j of the period: the base
 // acceleration enters as y(t+) + 2 y(t) + y(t-), evaluated in FP64.
 template <typename T>
@@ -223,17 +235,24 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
             inc = fma(c4.f, Fo, inc);
             incs[j] = inc;
             cfs[j] = c4.f;
-            tsum = fma(cpt[i], z[j] + ((dz[j] + inc) - cz[j]), tsum);
+            tsum = fma(cpt[i], fe_comp<T>(j) ? z[j] + ((dz[j] + inc) - cz[j]) : z[j] + (dz[j] + inc),
+                       tsum);
         }
 #pragma unroll
         for (int o = FEL / 2; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
         T Fp;
         fe_newton<FORCE, T>(cfc, Zc, tsum, ctip, newton_it, Fp);
         // compensated updates of both the increment and the modal coordinate
+        // (in FP32 for the lowest modes only)
 #pragma unroll
         for (int j = 0; j < FEM; ++j) {
-            kahan_add(dz[j], cdz[j], fma(cfs[j], Fp, incs[j]));
-            kahan_add(z[j], cz[j], dz[j]);
+            if (fe_comp<T>(j)) {
+                kahan_add(dz[j], cdz[j], fma(cfs[j], Fp, incs[j]));
+                kahan_add(z[j], cz[j], dz[j]);
+            } else {
+                dz[j] = dz[j] + fma(cfs[j], Fp, incs[j]);
+                z[j] = z[j] + dz[j];
+            }
         }
         Fm = Fn;
         Fn = Fp;

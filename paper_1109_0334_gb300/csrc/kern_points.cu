@@ -195,7 +195,7 @@ cudaError_t launch_invert_points(const KConst<float>& K, const PsoConst& pc, con
                                  int lanes) {
     // one mode per lane (kern_modes.cu) unless one lane is asked for; per
     // launch on the three-point, 3-mode DMT swarm of 512 particles over
-    // 10240 steps: one lane 4.06 ms, one mode per lane 2.22 ms
+    // 10240 steps: one lane 2.30 ms, one mode per lane 2.22 ms
     if (lanes != AFM_LANES_ONE && points_modes_supported(K.m, K.force, pc.P, K.np))
         return launch_invert_points_modes(K, pc, sw, U, history, it, st);
     const int threads = pc.P <= 152 * 32 * 4 ? 32 : 128;
