@@ -142,7 +142,8 @@ KERNEL_SOURCES = {
     "invert_pair_kernel": ["afm_device.cuh", "afm_internal.h", "kern_pair.cu"],
     "invert_modes_kernel": ["afm_device.cuh", "afm_internal.h", "kern_modes.cu"],
     "fwd_kernel": ["afm_device.cuh", "afm_internal.h", "kern_forward.cu"],
-    "batch_kernel": ["afm_device.cuh", "afm_internal.h", "kern_batch.cuh", "kern_batch.cu",
+    "fwd_x2_kernel": ["afm_device.cuh", "afm_internal.h", "afm_f32x2.cuh", "kern_forward.cu"],
+    "batch_kernel": ["afm_device.cuh", "afm_internal.h", "afm_f32x2.cuh", "kern_batch.cuh", "kern_batch.cu",
                      "kern_batch_dmt.cu"],
 }
 
@@ -916,7 +917,9 @@ def run_ours(args):
                    "value": Pb * N / ((ms_b / n_b) / 1e3), "unit": UNIT,
                    "roofline": {"bound": "alu", "achieved": ach_b / 1e12, "peak": peak_ops / 1e12,
                                 "unit": "T FP32 lane-ops/s", "frac": ach_b / peak_ops,
-                                                "traffic": ncu_traffic("fwd_kernel", "c2_batched")}}
+                                "kernel": "fwd_x2_kernel<3,DMT> (two particles per thread, "
+                                          "paired FP32 instructions)",
+                                "traffic": ncu_traffic("fwd_x2_kernel", "c2_batched")}}
 
     c3 = None
     if not args.no_c3:
@@ -1042,7 +1045,7 @@ def run_probe(args):
                                                  n_pix=props.multi_processor_count * 4,
                                                  cycles_div=10)
         cfg = A.make_pso(dict(spec, iters=args.probe_iters))
-        res, kp = A.invert_batch(prob, U, off, cfg)
+        res, kp = A.invert_batch(prob, U, off, cfg, particles_per_thread=args.probe_kp or 0)
         torch.cuda.synchronize()
         out = A.decode_results(res)
         print(json.dumps({"pixels": len(out), "kp": kp, "ok": sum(r["status"] == 0 for r in out)}))
@@ -1150,6 +1153,8 @@ def main():
                     default=None,
                     help="run one small untimed case for a profiler capture and exit")
     ap.add_argument("--probe-iters", type=int, default=2)
+    ap.add_argument("--probe-kp", type=int, default=None,
+                    help="particles per thread of the batch probe (default: autotuned)")
     ap.add_argument("--probe-particles", type=int, default=32768)
     args = ap.parse_args()
     if args.probe:

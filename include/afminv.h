@@ -174,7 +174,11 @@ afm_status afm_ctx_create(int device, afm_ctx** out);
 afm_status afm_ctx_destroy(afm_ctx* ctx);
 
 /* Lanes per particle of the fused inversion iteration (afm_invert,
- * afm_invert_polished).  A swarm too small to fill the GPU is latency-bound
+ * afm_invert_polished, deflection-point records included).  For
+ * afm_forward_batch, AFM_LANES_ONE also keeps one particle per thread where
+ * large FP32 DMT batches (1 or 3 modes, P >= 65536) otherwise run two
+ * particles per thread in paired FP32 instructions (bit-identical).
+ * A swarm too small to fill the GPU is latency-bound
  * along each particle's RK4 recurrence (Sec. 3.2); spreading a particle over
  * several lanes of a warp shortens the chain.  Every variant is bit-identical
  * to the one-lane arithmetic; a variant the problem does not support runs

@@ -137,7 +137,9 @@ __device__ __forceinline__ T tip_force(const Coef<T>& c, T d, T dd) {
         T fv = c.c1 * (r * r);
         T del = fmax(c.c3 - d, (T)0);
         T sq = sqrt_fast(del);
-        T F = c.c0 * (del * sq) - fv;
+        // explicit fma: the rounding does not depend on the compiler's
+        // contraction choice (the paired-lane step repeats it exactly)
+        T F = fma(c.c0, del * sq, -fv);
         if (FORCE == F_DMT_KV) F = F - c.c2 * (sq * dd);
         return F;
     } else if (FORCE == F_HOOKE) {

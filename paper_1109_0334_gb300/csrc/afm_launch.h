@@ -26,9 +26,13 @@ struct PsoConst {
     uint32_t pixel;
 };
 
-// forward + optional misfit
+// forward + optional misfit; lanes (afm_lanes): AFM_LANES_ONE keeps one
+// particle per thread, any other value pairs particles in paired FP32
+// instructions for large DMT batches (1 or 3 modes, P >= 65 536;
+// bit-identical)
 cudaError_t launch_forward_f32(const KConst<float>& K, const float* x, int P, float* defl,
-                               const float* U, float* S, int* flags, cudaStream_t st);
+                               const float* U, float* S, int* flags, cudaStream_t st,
+                               int lanes = 0);
 cudaError_t launch_forward_f64(const KConst<double>& K, const double* x, int P, double* defl,
                                const double* U, double* S, int* flags, cudaStream_t st);
 // standalone misfit of a time-major deflection array
@@ -59,6 +63,9 @@ struct BatchArgs {
     int n_seed;
 };
 int batch_threads(int P, int kp);
+// largest block of the batch kernel with kp particles per thread (the
+// paired-instruction kernels of kp = 2, 4 are built for up to 128 registers)
+int batch_max_threads(int kp);
 size_t batch_smem(int P, int D, int spc2);
 int batch_sort_max();
 cudaError_t batch_sort(const int64_t* off, int n_pix, int* order, cudaStream_t st);

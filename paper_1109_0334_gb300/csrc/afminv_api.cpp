@@ -727,7 +727,8 @@ void append_bytes(std::vector<unsigned char>& v, const T& x) {
 }
 
 // Autotuner of afm_invert_batch: times one swarm evaluation of the first wave
-// of pixels for each particles-per-thread choice and keeps the fastest.
+// of pixels for each particles-per-thread choice and keeps the one with the
+// lowest estimated batch time (the wave's time x the waves the batch needs).
 afm_status batch_tune(afm_ctx* ctx, const KConst<float>& Kf, const afm::PsoConst& pc,
                       const afm::BatchArgs& a, cudaStream_t s, int* kp_out, int* occ_out) {
     const auto key = std::make_tuple(Kf.m, Kf.force, pc.P, pc.D, Kf.spc2);
@@ -745,7 +746,7 @@ afm_status batch_tune(afm_ctx* ctx, const KConst<float>& Kf, const afm::PsoConst
     AFM_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
     for (int kp : {1, 2, 4}) {
         const int threads = afm::batch_threads(pc.P, kp);
-        if (threads > 1024 || (kp > 1 && Kf.m > 3)) continue;
+        if (threads > afm::batch_max_threads(kp) || (kp > 1 && Kf.m > 3)) continue;
         int occ = 0;
         if (afm::batch_occupancy(Kf.m, Kf.force, kp, pc.P, pc.D, Kf.spc2, &occ) != cudaSuccess ||
             occ < 1) {
@@ -764,6 +765,10 @@ afm_status batch_tune(afm_ctx* ctx, const KConst<float>& Kf, const afm::PsoConst
         AFM_CUDA(cudaEventSynchronize(e1), "cudaEventSynchronize");
         float ms = 0.f;
         AFM_CUDA(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        // the probe is one wave of the resident pixels (num_sms x occ, which
+        // differs between candidates): estimate the whole batch as that
+        // wave's time per resident pixel times the pixels
+        ms *= std::max(1.0f, (float)a.n_pix / (float)pa.n_pix);
         if (ms < best_ms) {
             best_ms = ms;
             best_kp = kp;
@@ -942,7 +947,7 @@ afm_status afm_forward_batch(afm_ctx* ctx, const afm_problem* prob, const float*
                  "points forward kernel");
         return AFM_OK;
     }
-    AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_f32(K, x, P, defl, U, S, nullptr, s); }),
+    AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_f32(K, x, P, defl, U, S, nullptr, s, ctx->lanes); }),
              "forward kernel");
     return AFM_OK;
 }
@@ -1494,7 +1499,7 @@ afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat
     const int want = particles_per_thread ? *particles_per_thread : 0;
     const afm::PsoConst& pc = B.pc;
     if (want == 1 || want == 2 || want == 4) {
-        if (afm::batch_threads(pc.P, want) > 1024 || (want > 1 && B.Kf.m > 3))
+        if (afm::batch_threads(pc.P, want) > afm::batch_max_threads(want) || (want > 1 && B.Kf.m > 3))
             return fail(AFM_ERR_INVALID_ARG, "particles_per_thread %d unsupported here", want);
         kp = want;
         AFM_CUDA(afm::batch_occupancy(B.Kf.m, B.Kf.force, kp, pc.P, pc.D, B.Kf.spc2, &occ),

@@ -17,6 +17,8 @@ namespace afm {
 
 int batch_threads(int P, int kp) { return ((P + kp - 1) / kp + 31) / 32 * 32; }
 
+int batch_max_threads(int kp) { return kp == 1 ? 1024 : 512; }
+
 size_t batch_smem(int P, int D, int spc2) {
     const size_t tab = (size_t)((spc2 + 1 + 3) & ~3);
     return sizeof(float) * (tab + 3 * (size_t)D * P);

@@ -4,6 +4,7 @@
 #pragma once
 #include "../../include/afminv.h"
 #include "afm_device.cuh"
+#include "afm_f32x2.cuh"
 #include "afm_launch.h"
 
 namespace afm {
@@ -29,7 +30,7 @@ __device__ __forceinline__ unsigned long long warp_min(unsigned long long k) {
 // Persistent swarm kernel.
 // ---------------------------------------------------------------------------
 template <int M, int FORCE, int KP>
-__global__ void __launch_bounds__(1024) batch_kernel(const KConst<float> K, const PsoConst pc,
+__global__ void __launch_bounds__(KP == 1 ? 1024 : 512) batch_kernel(const KConst<float> K, const PsoConst pc,
                                                      const BatchArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int P = pc.P, D = pc.D;
@@ -128,7 +129,11 @@ __global__ void __launch_bounds__(1024) batch_kernel(const KConst<float> K, cons
                 c[k] = make_coef<float, float>(K, x);
             }
             float S[KP];
-            integrate_multi<M, FORCE, KP>(K, c, tab, U, n, S);
+            // pairs of particles per paired FP32 instruction where the law allows
+            if constexpr (KP % 2 == 0 && M <= 4 && x2::Supported<FORCE>::value)
+                integrate_multi_x2<M, FORCE, KP>(K, c, tab, U, n, S);
+            else
+                integrate_multi<M, FORCE, KP>(K, c, tab, U, n, S);
             unsigned long long key = ~0ull;
 #pragma unroll
             for (int k = 0; k < KP; ++k) {

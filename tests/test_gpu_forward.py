@@ -141,3 +141,30 @@ def test_synth_records_match_oracle(orc, afm):
                          spec["seed"], p) / NM
         got = U[off[i]:off[i + 1]]
         assert rel_l2(got, ref) <= FWD_TOL
+
+
+@pytest.mark.parametrize("name,P", [("c2", 65537), ("c1", 65536)])
+def test_paired_particle_forward_is_bit_identical(orc, afm, name, P):
+    """Large FP32 DMT batches run two particles per thread in paired FP32
+    instructions: deflections and misfits equal the one-particle-per-thread
+    kernel's bit for bit (an odd batch ends in a half-filled pair), and a
+    sample of them matches the oracle."""
+    spec = W.get(name, cycles=2)
+    D = len(spec["free"])
+    x = torch.from_numpy(W.sample_x(D, P, seed=P)).cuda()
+    U32, _, _ = oracle_record(orc, spec)
+    Ug = torch.from_numpy(U32).cuda()
+    prob = afm.make_problem(spec)
+    out = {}
+    for lanes in ("one", "auto"):
+        afm.set_lanes(lanes)
+        try:
+            out[lanes] = afm.forward_batch(prob, x, Ug)
+            torch.cuda.synchronize()
+        finally:
+            afm.set_lanes("auto")
+    (d1, S1), (d2, S2) = out["one"], out["auto"]
+    assert torch.equal(d1, d2) and torch.equal(S1, S2)
+    idx = np.array([0, 1, P // 2, P - 2, P - 1])
+    ref = oracle_defl_nm(orc, spec, x.cpu().numpy()[:, idx])
+    assert rel_l2(d2.cpu().numpy()[:, idx], ref, axis=0).max() <= 1e-5
