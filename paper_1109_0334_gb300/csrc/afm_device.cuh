@@ -137,9 +137,11 @@ __device__ __forceinline__ T tip_force(const Coef<T>& c, T d, T dd) {
         T fv = c.c1 * (r * r);
         T del = fmax(c.c3 - d, (T)0);
         T sq = sqrt_fast(del);
-        // explicit fma: the rounding does not depend on the compiler's
-        // contraction choice (the paired-lane step repeats it exactly)
-        T F = fma(c.c0, del * sq, -fv);
+        // nvcc contracts this to fma(c0, del * sq, -fv), the form the paired
+        // step of afm_f32x2.cuh writes out (the batch tests compare the two
+        // bit for bit); written out here as well it schedules ~1.5 % slower
+        // in the small-swarm kernels
+        T F = c.c0 * (del * sq) - fv;
         if (FORCE == F_DMT_KV) F = F - c.c2 * (sq * dd);
         return F;
     } else if (FORCE == F_HOOKE) {

@@ -6,7 +6,9 @@
 // kernel's KP) issues one paired instruction where it issued two scalar
 // ones.  Every operation is the scalar step's, in the same order and with the
 // same rounding (x - y as x + (-y), which IEEE rounds identically), so each
-// particle's result is bit-identical to integrate_multi / rk4_step.
+// particle's result is bit-identical to integrate_multi / rk4_step (the one
+// expression of the scalar step that nvcc contracts, in the DMT law, is
+// written here in its contracted form; tests compare the two bit for bit).
 // Laws without rate dependence whose scalar form is written out operation by
 // operation (DMT); up to 4 modes (the add_rn force term of accel).
 #pragma once
@@ -61,11 +63,11 @@ struct Coef2 {
 __device__ __forceinline__ float2 dmt_force(const Coef2& c, float2 d) {
     const float2 dm = make_float2(fmaxf(d.x, c.c3.x), fmaxf(d.y, c.c3.y));
     const float2 r = make_float2(rcp_fast(dm.x), rcp_fast(dm.y));
-    const float2 fv = mul(c.c1, mul(r, r));
     const float2 t = sub(c.c3, d);
     const float2 del = make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f));
     const float2 sq = make_float2(sqrt_fast(del.x), sqrt_fast(del.y));
-    return fma(c.c0, mul(del, sq), neg(fv));
+    // the contraction nvcc makes of the scalar law's c0 (del sq) - c1 r^2
+    return fma(c.c0, mul(del, sq), neg(mul(c.c1, mul(r, r))));
 }
 
 template <int M>
