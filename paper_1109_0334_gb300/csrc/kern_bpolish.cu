@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "afm_device.cuh"
+#include "afm_f32x2.cuh"
 #include "afm_launch.h"
 
 namespace afm {
@@ -113,6 +114,36 @@ __global__ void fwd_ragged_kernel(const KConst<float> K, const float* __restrict
     S[p] = s;
 }
 
+// The same with candidates 2t and 2t + 1 on thread t in paired FP32
+// instructions (afm_f32x2.cuh; bit-identical): with an even number of
+// candidates per slot both belong to the same pixel and record.
+template <int M, int FORCE>
+__global__ void fwd_ragged_x2_kernel(const KConst<float> K, const float* __restrict__ x,
+                                     int Ptot, const float* __restrict__ U_cat,
+                                     const int64_t* __restrict__ off,
+                                     const int* __restrict__ order, int per_slot,
+                                     float* __restrict__ S) {
+    extern __shared__ __align__(16) float tab[];
+    build_drive_table(K, tab);
+    __syncthreads();
+    const int p = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (p >= Ptot) return;
+    const int slot = p / per_slot;
+    const int pix = order != nullptr ? order[slot] : slot;
+    const int64_t o = off[pix];
+    const int n = (int)(off[pix + 1] - o);
+    float xa[AFM_MAXD], xb[AFM_MAXD];
+    for (int d = 0; d < K.D; ++d) {
+        xa[d] = x[(size_t)d * Ptot + p];
+        xb[d] = x[(size_t)d * Ptot + p + 1];
+    }
+    const Coef<float> ca = make_coef<float, float>(K, xa);
+    const Coef<float> cb = make_coef<float, float>(K, xb);
+    const float2 s = integrate_x2<M, FORCE>(K, ca, cb, tab, U_cat + o, nullptr, Ptot, p, true, n);
+    S[p] = s.x < INFINITY ? s.x : INFINITY;
+    S[p + 1] = s.y < INFINITY ? s.y : INFINITY;
+}
+
 // Per slot: the polished candidate of lowest misfit (first on ties) becomes
 // the pixel's winner (x, FP32 S, swarm index); the FP64 re-evaluation of
 // kern_reeval_batch.cu follows.
@@ -155,6 +186,23 @@ cudaError_t launch_forward_ragged(const KConst<float>& K, const float* x, int Pt
     const int threads = Ptot <= 152 * 32 * 4 ? 32 : 128;
     const int blocks = (Ptot + threads - 1) / threads;
     const size_t smem = sizeof(float) * (size_t)(K.spc2 + 1);
+    // pairs of candidates for large DMT batches (the same rule as
+    // afm_forward_batch's paired kernel)
+    if (K.force == F_DMT && (K.m == 1 || K.m == 3) && per_slot % 2 == 0 && Ptot >= 65536) {
+        const int pairs = Ptot / 2;
+        auto go = [&](auto Mc) -> cudaError_t {
+            auto kern = fwd_ragged_x2_kernel<decltype(Mc)::value, F_DMT>;
+            if (smem > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(
+                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            kern<<<(pairs + 127) / 128, 128, smem, st>>>(K, x, Ptot, U_cat, off, order, per_slot, S);
+            return cudaGetLastError();
+        };
+        if (K.m == 1) return go(std::integral_constant<int, 1>{});
+        return go(std::integral_constant<int, 3>{});
+    }
     return dispatch_mf(K.m, K.force, [&](auto Mc, auto Fc) -> cudaError_t {
         auto kern = fwd_ragged_kernel<decltype(Mc)::value, decltype(Fc)::value>;
         if (smem > 48 * 1024) {

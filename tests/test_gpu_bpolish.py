@@ -119,3 +119,35 @@ def test_batch_polished_record_beyond_n_steps_keeps_swarm_winner(orc, afm):
             assert pol[i]["S"] == plain[i]["S"]
             np.testing.assert_array_equal(pol[i]["x"], plain[i]["x"])
         assert pol[i]["S_f64"] <= plain[i]["S_f64"] * (1 + 1e-9)
+
+
+def test_paired_trial_point_forward_matches_smaller_batches(orc, afm):
+    """512 pixels x 32 candidates x 4 damping values = 65 536 trial points per
+    Levenberg-Marquardt step take the paired-instruction forward (two
+    candidates of one pixel per thread); batches of 64 pixels (8 192 trial
+    points) take the one-candidate-per-thread kernel.  Every pixel's result
+    must be the same bit for bit."""
+    spec = W.get("c3", P=64, iters=2)
+    n_pix, sub = 512, 64
+    pixels = list(range(n_pix))
+    U_cat, off, recs = _records(orc, spec, pixels, cyc_div=100)
+    prob = afm.make_problem(spec, n_steps=int(max(np.diff(off))))
+    cfg = afm.make_pso(spec)
+    Kc, steps, J = 32, 2, 4
+    res, _ = afm.invert_batch_polished(prob, torch.from_numpy(U_cat).cuda(),
+                                       torch.from_numpy(off).cuda(), cfg, polish_k=Kc,
+                                       polish_steps=steps, n_cand=J, method="lm")
+    torch.cuda.synchronize()
+    full = afm.decode_results(res)
+    for b0 in range(0, n_pix, sub):
+        o = off[b0:b0 + sub + 1]
+        Ub = np.concatenate(recs[b0:b0 + sub])
+        rb, _ = afm.invert_batch_polished(prob, torch.from_numpy(Ub).cuda(),
+                                          torch.from_numpy(o - o[0]).cuda(), cfg, polish_k=Kc,
+                                          polish_steps=steps, n_cand=J, pixel0=b0, method="lm")
+        torch.cuda.synchronize()
+        for i, r in enumerate(afm.decode_results(rb)):
+            f = full[b0 + i]
+            assert r["status"] == 0 and f["status"] == 0
+            assert r["winner"] == f["winner"] and r["S"] == f["S"]
+            np.testing.assert_array_equal(r["x"], f["x"])
