@@ -342,8 +342,11 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
  * NULL or 0 selects the autotuner, which on the first call for a new (modes,
  * force, P, D, steps per cycle) times one evaluation of the first wave of
  * pixels per candidate (synchronous: make that call before any capture of
- * `stream`) and caches the fastest in the context.  The choice used is
- * written back to *particles_per_thread if non-NULL.
+ * `stream`), scales it by the waves the batch needs at that candidate's
+ * occupancy and caches the fastest in the context.  With 2 or 4 particles
+ * per thread, DMT swarms step two particles per paired FP32 instruction
+ * (bit-identical to one per thread).  The choice used is written back to
+ * *particles_per_thread if non-NULL.
  * workspace: device, >= afm_invert_batch_workspace_size(prob, n_pix),
  * 256-aligned (the queue, and the FP64 re-evaluation of every pixel's winner
  * by multiple shooting: ~250 bytes per 32-step segment of the longest record
