@@ -9,8 +9,9 @@
 // particle's result is bit-identical to integrate_multi / rk4_step (the one
 // expression of the scalar step that nvcc contracts, in the DMT law, is
 // written here in its contracted form; tests compare the two bit for bit).
-// Laws without rate dependence whose scalar form is written out operation by
-// operation (DMT); up to 4 modes (the add_rn force term of accel).
+// The DMT law only (the laws of the batched workloads; each other law would
+// need its own check of the compiler's contractions), up to 4 modes (the
+// add_rn force term of accel).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
