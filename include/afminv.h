@@ -204,7 +204,12 @@ typedef enum {
     AFM_LANES_MODES3 = 5
 } afm_lanes;
 afm_status afm_set_lanes(afm_ctx* ctx, int lanes);
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on the calling host thread ("" if none).
+ * The message is thread-local, not per context: every entry point clears it
+ * on entry and sets it when it returns a status other than AFM_OK, so a
+ * thread that drives several contexts reads the message of its own most
+ * recent call, whichever context that call used; other threads' calls never
+ * change it.  The pointer stays valid until the thread's next library call. */
 const char* afm_last_error(void);
 const char* afm_status_string(int status);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
@@ -427,7 +432,9 @@ afm_status afm_invert_image(afm_ctx* ctx, const afm_problem* prob, const float* 
  * cannot allocate device memory at all, such as a real-time AFM feedback
  * loop that forbids allocator calls once scanning has started, or a plug-in
  * whose host application owns the whole device-memory budget.  It runs the
- * same fused inversion as afm_invert, but its swarm state lives in a
+ * same fused inversion as afm_invert (with the context's afm_set_lanes
+ * choice; its iteration launches are timed by afm_profile_* like
+ * afm_invert's), but its swarm state lives in a
  * fixed array of AFM_NOALLOC_SCRATCH_BYTES inside the library's device data
  * (held by every GPU that loads the library until the process exits)
  * instead of a caller workspace; the caller still passes U, result and
@@ -451,9 +458,15 @@ afm_status afm_invert_noalloc(afm_ctx* ctx, const afm_problem* prob, const float
 
 /* ---- synthetic records (Sec. 4.1: data made by a different integration) --
  * For each of n_pix pixels, the truth x* (normalised, [D][n_pix] device
- * double) is integrated in FP64 at 1/sub of the solver step and sampled
- * every `sub` fine steps; then Gaussian noise of std sigma_m is added
- * (Box-Muller on Philox counter (n/2, 0, pixel0 + i, 4<<16), words 0/1).
+ * double; mapped to force coefficients in FP64) is integrated in FP32 with
+ * the compensated RK4 step of the solver (the same arithmetic as
+ * afm_forward_batch) at 1/sub of the solver step, and sampled every `sub`
+ * fine steps; then Gaussian noise of std sigma_m is added (Box-Muller in
+ * FP32 on Philox counter (n/2, 0, pixel0 + i, 4<<16), words 0/1: the cosine
+ * branch for even n, the sine branch for odd n).  The finer step is the
+ * paper's guard against the inverse crime (Sec. 4.1); records that need an
+ * FP64 truth come from afm_forward_batch_f64 on a problem with the finer
+ * step instead.
  * Records are concatenated: pixel i has n_i = off[i+1] - off[i] samples at
  * U_cat[off[i] ..] (device; off is a device int64 array [n_pix + 1]). */
 afm_status afm_synth_records(afm_ctx* ctx, const afm_problem* prob, const double* x_truth,

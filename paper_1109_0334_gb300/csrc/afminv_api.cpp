@@ -795,6 +795,19 @@ namespace detail {
 
 afm_status set_error(afm_status st, const char* msg) { return fail(st, "%s", msg); }
 
+void clear_error() { g_err[0] = 0; }
+
+cudaError_t invert_iter_timed(afm_ctx* ctx, const KConst<float>& K, const PsoConst& pc,
+                              const SwarmPtrs& sw, const float* U, float* history, int it,
+                              cudaStream_t s) {
+    return timed_launch(ctx, s, [&] {
+        return afm::launch_invert_iter(K, pc, sw, U, history, it, s, ctx->lanes);
+    });
+}
+
+void trace_push(const char* name) { nvtxRangePushA(name); }
+void trace_pop() { nvtxRangePop(); }
+
 afm_status prepare_invert(afm_ctx* ctx, const afm_problem* prob, const afm_pso_cfg* cfg,
                           KConst<float>* Kf, KConst<double>* Kd, PsoConst* pc,
                           size_t* scratch_bytes, size_t* reeval_bytes, int* device) {
@@ -865,6 +878,7 @@ afm_status afm_ctx_create(int device, afm_ctx** out) {
 }
 
 afm_status afm_ctx_destroy(afm_ctx* ctx) {
+    g_err[0] = 0;
     if (ctx) {
         for (auto& pr : ctx->ev_pending) {
             cudaEventDestroy(pr.first);

@@ -17,6 +17,14 @@ afm_status prepare_invert(afm_ctx* ctx, const afm_problem* prob, const afm_pso_c
                           KConst<float>* Kf, KConst<double>* Kd, PsoConst* pc,
                           size_t* scratch_bytes, size_t* reeval_bytes, int* device);
 void carve_swarm(void* base, int P, int D, SwarmPtrs* sw);
+void clear_error();
+// one fused iteration launch with the context's lanes-per-particle choice,
+// bracketed by the profiling events when afm_profile_enable is on
+cudaError_t invert_iter_timed(afm_ctx* ctx, const KConst<float>& K, const PsoConst& pc,
+                              const SwarmPtrs& sw, const float* U, float* history, int it,
+                              cudaStream_t s);
+void trace_push(const char* name);
+void trace_pop();
 }  // namespace detail
 }  // namespace afm
 
@@ -52,11 +60,21 @@ afm_status scratch_address(int device, void** out) {
     return AFM_OK;
 }
 
+// NVTX range over the call, as every other compute entry point has.
+struct Trace {
+    Trace() { afm::detail::trace_push("afm_invert_noalloc"); }
+    ~Trace() { afm::detail::trace_pop(); }
+    Trace(const Trace&) = delete;
+    Trace& operator=(const Trace&) = delete;
+};
+
 }  // namespace
 
 extern "C" afm_status afm_invert_noalloc(afm_ctx* ctx, const afm_problem* prob, const float* U,
                                          const afm_pso_cfg* cfg, afm_result* result,
                                          float* history, void* stream) {
+    Trace trace;
+    afm::detail::clear_error();
     afm::KConst<float> Kf;
     afm::KConst<double> Kd;
     afm::PsoConst pc;
@@ -78,7 +96,7 @@ extern "C" afm_status afm_invert_noalloc(afm_ctx* ctx, const afm_problem* prob, 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = afm::launch_pso_init(pc, sw, s);
     for (int it = 0; e == cudaSuccess && it <= pc.iters; ++it)
-        e = afm::launch_invert_iter(Kf, pc, sw, U, history, it, s);
+        e = afm::detail::invert_iter_timed(ctx, Kf, pc, sw, U, history, it, s);
     // the winner's FP64 re-evaluation by multiple shooting where the rest of
     // the scratch holds its segments, else one sequential FP64 pass
     const size_t at = (need + 255) & ~size_t(255);

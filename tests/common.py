@@ -92,29 +92,124 @@ def log_jacobian(spec, x):
     return J
 
 
+def _gauss_newton_ok(spec) -> bool:
+    """The oracle's complex-step residual sensitivities cover the force-law
+    slots of the steady drive on tip records."""
+    return (spec.get("drive") is None and not spec.get("points")
+            and all(f[0] < 5 for f in spec["free"]))
+
+
+def rho_eigen(orc, spec, U_m, x_ref, rel_param=0.005):
+    """Eigen-decomposition of the misfit Hessian in the relative coordinates
+    rho (log-parameters; a dimension with a fixed relative scale s: theta /
+    s) at x_ref: eigenvalues, eigenvectors (columns) and their one-sigma
+    statistical half-widths sqrt(2 sigma^2 / lambda) for noise sigma.  The
+    Hessian is the Gauss-Newton matrix 2 sum_n a_n a_n^T of the oracle's
+    complex-step residual sensitivities where it has them (exact to
+    rounding, so a direction the misfit does not see has a zero eigenvalue),
+    else central differences of the misfit."""
+    c, pm = oracle_case(orc, spec)
+    x_ref = np.asarray(x_ref, dtype=np.float64)
+    if _gauss_newton_ok(spec):
+        _S, Hgn, _b = orc.normal_eq(c, pm, x_ref.reshape(-1, 1).copy(), U_m)
+        H = 2.0 * np.asarray(Hgn)
+    else:
+        H = hessian_x(orc, c, pm, U_m, x_ref)
+    J = log_jacobian(spec, x_ref)
+    Hr = H / np.outer(J, J)
+    lam, V = np.linalg.eigh(Hr)
+    widths = np.sqrt(2 * spec["sigma"] ** 2 / np.maximum(lam, 1e-300))
+    return lam, V, widths
+
+
+def _drho(orc, spec, x_ref, x_test):
+    pm = orc.make_pmap(spec)
+    th_ref = orc.map_x(pm, np.asarray(x_ref, dtype=np.float64))
+    th_t = orc.map_x(pm, np.asarray(x_test, dtype=np.float64))
+    return np.array([(th_t[s] - th_ref[s]) / _rel_scale(spec, d) if _rel_scale(spec, d) is not None
+                     else math.log(th_t[s] / th_ref[s]) for d, (s, *_r) in enumerate(spec["free"])])
+
+
 def identifiable_check(orc, spec, U_m, x_ref, S_ref, x_test, rel_param=0.005):
     """Parameters are compared where the record determines them: the
-    eigen-directions of the misfit Hessian (in log-parameter coordinates, at
-    the reference optimum) whose one-sigma statistical half-width (noise
-    sigma) is below `rel_param`.  Returns (max projected relative error over
-    those directions, number of identifiable directions, S_oracle(x_test))."""
+    eigen-directions of the misfit Hessian (rho_eigen, at the reference
+    optimum) whose one-sigma statistical half-width (noise sigma) is below
+    `rel_param`.  Returns (max projected relative error over those
+    directions, number of identifiable directions, S_oracle(x_test),
+    widths)."""
     c, pm = oracle_case(orc, spec)
-    H = hessian_x(orc, c, pm, U_m, x_ref)
-    J = log_jacobian(spec, x_ref)
-    Jinv = np.diag(1.0 / J)
-    Hr = Jinv @ H @ Jinv
-    lam, V = np.linalg.eigh(Hr)
-    sig2 = spec["sigma"] ** 2
-    widths = np.sqrt(2 * sig2 / np.maximum(lam, 1e-300))
+    lam, V, widths = rho_eigen(orc, spec, U_m, x_ref)
     ident = widths <= rel_param
-    th_ref = orc.map_x(pm, x_ref)
-    th_t = orc.map_x(pm, x_test)
-    drho = np.array([(th_t[s] - th_ref[s]) / _rel_scale(spec, d) if _rel_scale(spec, d) is not None
-                     else math.log(th_t[s] / th_ref[s]) for d, (s, *_r) in enumerate(spec["free"])])
-    proj = np.abs(V.T @ drho)
+    proj = np.abs(V.T @ _drho(orc, spec, x_ref, x_test))
     err = float(proj[ident].max()) if ident.any() else 0.0
     S_t = orc.misfit_batch(c, pm, np.asarray(x_test, dtype=np.float64).reshape(-1, 1), U_m)[0]
     return err, int(ident.sum()), float(S_t), widths
+
+
+def named_combinations(spec):
+    """The parameter combinations the force law depends on, each as
+    (name, {slot: exponent}): a DMT-family law sees H and R only through
+    H R (van der Waals -H R / (6 d^2)), E* and R only through E* sqrt(R)
+    (Hertz), and, with contact damping, eta only through eta sqrt(R); a0
+    enters alone.  Combinations whose slots are all fixed are left out.
+    Other laws (Hooke, spring-damper, base motion): the free parameters
+    themselves."""
+    free_slots = [f[0] for f in spec["free"]]
+    if spec["force"] in ("dmt", "dmt_kv"):
+        cands = [("H R", {1: 1.0, 2: 1.0}), ("E* sqrt(R)", {0: 1.0, 2: 0.5}), ("a0", {3: 1.0})]
+        if spec["force"] == "dmt_kv":
+            cands.append(("eta sqrt(R)", {4: 1.0, 2: 0.5}))
+        return [(n, e) for n, e in cands if any(sl in free_slots for sl in e)]
+    names = {0: "k", 1: "h", 2: "zeta_s", 5: "a", 6: "f", 7: "g"}
+    return [(names.get(sl, f"slot {sl}"), {sl: 1.0}) for sl in free_slots]
+
+
+def named_check(orc, spec, U_m, x_ref, x_test, rel_param=0.005):
+    """The named combinations (named_combinations) against the determined
+    subspace (the span of the Hessian eigen-directions of rho_eigen whose
+    half-width is <= rel_param): for combination k with gradient g_k in rho
+    (log c_k = sum_s e_s rho_s), the fraction |P g_k|^2 / |g_k|^2 of it that
+    lies in that subspace (1: fully determined; the rest of it runs along
+    directions the record resolves worse than rel_param), and the relative
+    difference of c_k between x_test and x_ref.  Returns (n_id, {name:
+    (fraction, relative difference)})."""
+    lam, V, widths = rho_eigen(orc, spec, U_m, x_ref)
+    ident = V[:, widths <= rel_param]
+    d_of = {slot: d for d, (slot, *_r) in enumerate(spec["free"])}
+    drho = _drho(orc, spec, x_ref, x_test)
+    out = {}
+    for name, expo in named_combinations(spec):
+        g = np.zeros(len(spec["free"]))
+        for sl, e in expo.items():
+            if sl in d_of:
+                g[d_of[sl]] = e
+        pg = ident @ (ident.T @ g)
+        frac = float(pg @ pg / (g @ g))
+        lr = float(g @ drho)
+        sl0 = next(iter(expo))
+        err = abs(lr) if (len(expo) == 1 and _rel_scale(spec, d_of[sl0]) is not None) \
+            else abs(math.expm1(lr))
+        out[name] = (frac, err)
+    return int(ident.shape[1]), out
+
+
+def inside(named, min_frac=0.9):
+    """Names of the combinations that lie (to min_frac of their squared
+    length, i.e. within ~18 degrees) in the determined subspace."""
+    return sorted(n for n, (f, _e) in named.items() if f >= min_frac)
+
+
+def assert_determined(orc, spec, U_m, x_ref, x_test, n_id, names, rel_param=0.005):
+    """The inversion-parity statement made explicit: the record determines
+    exactly n_id eigen-directions to rel_param; the named combinations
+    `names` (and no others) lie in their span; x_test agrees with x_ref on
+    each of those combinations within rel_param."""
+    n, named = named_check(orc, spec, U_m, x_ref, x_test, rel_param)
+    assert n == n_id, (n, named)
+    assert inside(named) == sorted(names), named
+    for k in names:
+        assert named[k][1] <= rel_param, (k, named[k])
+    return named
 
 
 def law_combinations(orc, spec, x):

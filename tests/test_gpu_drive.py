@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_1109_0334_gb300 import workloads as W
-from common import NM, identifiable_check, oracle_defl_nm, rel_l2
+from common import NM, assert_determined, identifiable_check, oracle_defl_nm, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -39,8 +39,9 @@ def test_drive_forward_parity(orc, afm, name, modes):
     assert rel_l2(d64.cpu().numpy(), ref, axis=0).max() <= 1e-9
 
 
-@pytest.mark.parametrize("name", ["f3_amp", "f3_amp_freq", "f3_chirp"])
-def test_drive_inversion(orc, afm, name):
+@pytest.mark.parametrize("name,named", [("f3_amp", ["a"]), ("f3_amp_freq", ["a", "f"]),
+                                        ("f3_chirp", ["a", "f", "g"])])
+def test_drive_inversion(orc, afm, name, named):
     spec = W.get(name)
     c, pm = orc.make_case(spec), orc.make_pmap(spec)
     n = W.n_steps(spec)
@@ -56,8 +57,9 @@ def test_drive_inversion(orc, afm, name):
     r = afm.decode_result(res)
     D = pm.D
     err, n_id, S_g, widths = identifiable_check(orc, spec, U_m, x_o, S_o, r["x"][:D])
-    assert r["status"] == 0 and n_id >= 1
+    assert r["status"] == 0 and n_id == len(named)
     assert err <= 0.005, (err, widths)
+    assert_determined(orc, spec, U_m, x_o, r["x"][:D], len(named), named)
     assert S_g <= S_o * (1 + 1e-4)
     assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2
     assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 from paper_1109_0334_gb300 import workloads as W
-from common import NM, identifiable_check, oracle_record
+from common import NM, assert_determined, identifiable_check, oracle_record
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -94,13 +94,15 @@ def _gpu_invert(afm, spec, U32):
     return afm.decode_result(res), hist.cpu().numpy()
 
 
-def _check_inversion(orc, spec, U_m, r, x_o, S_o_m, hist):
+def _check_inversion(orc, spec, U_m, r, x_o, S_o_m, hist, n_id_expected, names):
     D = len(spec["free"])
     x_g = r["x"][:D]
     err, n_id, S_g_orc, widths = identifiable_check(orc, spec, U_m, x_o, S_o_m, x_g)
     S_o = S_o_m / NM ** 2
-    assert n_id >= 1
+    assert n_id == n_id_expected, widths
     assert err <= 0.005, (err, widths)
+    # the named combinations the record determines, compared by name
+    assert_determined(orc, spec, U_m, x_o, x_g, n_id_expected, names)
     # the GPU's optimum is as good as the oracle's
     assert S_g_orc / NM ** 2 <= S_o * (1 + 1e-4)
     # FP32 misfit of the winner and its FP64 re-evaluation on the GPU
@@ -118,7 +120,7 @@ def test_invert_c1_parity(orc, afm):
     r, hist = _gpu_invert(afm, spec, U32)
     x_o, S_o, _ = orc.invert(orc.make_case(spec), orc.make_pmap(spec), U_m, spec["P"],
                              spec["iters"], spec["w"], spec["c1"], spec["c2"], spec["seed"])
-    _check_inversion(orc, spec, U_m, r, x_o, S_o, hist)
+    _check_inversion(orc, spec, U_m, r, x_o, S_o, hist, 1, ["E* sqrt(R)"])
     assert r["iters"] == spec["iters"] and len(hist) == spec["iters"] + 1
 
 
@@ -132,7 +134,8 @@ def test_invert_c2_full_size_parity(orc, afm):
     U32, U_m, xt = oracle_record(orc, spec)
     assert abs(float(np.sum(U_m ** 2)) / gold["sumU2_m2"] - 1) < 1e-9
     r, hist = _gpu_invert(afm, spec, U32)
-    _check_inversion(orc, spec, U_m, r, np.array(gold["x"]), gold["S_m2"], hist)
+    _check_inversion(orc, spec, U_m, r, np.array(gold["x"]), gold["S_m2"], hist, 2,
+                     ["E* sqrt(R)", "a0"])
 
 
 @pytest.mark.parametrize("lanes", ["auto", "one", "stages", "modes2", "modes3", "modes4"])

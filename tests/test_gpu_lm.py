@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_1109_0334_gb300 import workloads as W
-from common import NM, identifiable_check, oracle_record
+from common import NM, assert_determined, identifiable_check, oracle_record
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -128,6 +128,7 @@ def test_invert_polished_lm_reaches_the_oracle_optimum(orc, afm):
     err, n_id, S_g, widths = identifiable_check(orc, spec, U_m, np.array(gold["x"]), gold["S_m2"],
                                                 r["x"][:pm.D])
     assert r["status"] == 0
-    assert n_id >= 1 and err <= 0.005, (err, widths)
+    assert n_id == 2 and err <= 0.005, (err, widths)
+    assert_determined(orc, spec, U_m, np.array(gold["x"]), r["x"][:pm.D], 2, ["E* sqrt(R)", "a0"])
     assert S_g - gold["S_m2"] <= spec["sigma"] ** 2
     assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_1109_0334_gb300 import workloads as W
-from common import NM, identifiable_check
+from common import NM, assert_determined, identifiable_check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -22,8 +22,9 @@ def afm():
     return afminv
 
 
-@pytest.mark.parametrize("name", ["f2_hooke", "f2_spring_damper"])
-def test_paper_force_law_inversion(orc, afm, name):
+@pytest.mark.parametrize("name,n_id_expected,named", [("f2_hooke", 2, ["h", "k"]),
+                                                      ("f2_spring_damper", 1, ["k"])])
+def test_paper_force_law_inversion(orc, afm, name, n_id_expected, named):
     spec = W.get(name)
     c, pm = orc.make_case(spec), orc.make_pmap(spec)
     n = W.n_steps(spec)
@@ -39,8 +40,10 @@ def test_paper_force_law_inversion(orc, afm, name):
     r = afm.decode_result(res)
     D = pm.D
     err, n_id, S_g, widths = identifiable_check(orc, spec, U_m, x_o, S_o, r["x"][:D])
-    assert r["status"] == 0 and n_id >= 1
+    assert r["status"] == 0 and n_id == n_id_expected
     assert err <= 0.005, (err, widths)
+    # (the spring-damper record resolves zeta_s only to ~2 %: not compared by name)
+    assert_determined(orc, spec, U_m, x_o, r["x"][:D], n_id_expected, named)
     assert S_g <= S_o * (1 + 1e-4)
     assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2
     assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2

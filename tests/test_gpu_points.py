@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_1109_0334_gb300 import workloads as W
-from common import NM, identifiable_check, oracle_defl_nm, oracle_record, rel_l2
+from common import NM, assert_determined, identifiable_check, oracle_defl_nm, oracle_record, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -65,8 +65,9 @@ def test_points_inversion(orc, afm):
     torch.cuda.synchronize()
     r = afm.decode_result(res)
     err, n_id, S_g, widths = identifiable_check(orc, spec, U_m, x_o, S_o, r["x"][:pm.D])
-    assert r["status"] == 0 and n_id >= 1
+    assert r["status"] == 0 and n_id == 1
     assert err <= 0.005, (err, widths)
+    assert_determined(orc, spec, U_m, x_o, r["x"][:pm.D], 1, ["E* sqrt(R)"])
     assert S_g <= S_o * (1 + 1e-4)
     assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2
     assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_1109_0334_gb300 import workloads as W
-from common import NM, identifiable_check, oracle_record
+from common import NM, assert_determined, identifiable_check, oracle_record
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -63,7 +63,8 @@ def test_invert_polished_matches_oracle(orc, afm):
     xo, So = orc.polish(c, pm, U_m, x_pso.reshape(-1, 1), steps=spec["polish_steps"], n_cand=16)
     D = pm.D
     err, n_id, S_g, widths = identifiable_check(orc, spec, U_m, xo[:, 0], So[0], r["x"][:D])
-    assert r["status"] == 0
+    assert r["status"] == 0 and n_id == 2
+    assert_determined(orc, spec, U_m, xo[:, 0], r["x"][:D], 2, ["eta sqrt(R)"])
     assert S_g <= So[0] * (1 + 1e-4)
     assert err <= 0.005, (err, widths)
     assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2

@@ -67,6 +67,66 @@ def test_invert_noalloc_matches_invert_twice(afm, name, iters):
         np.testing.assert_allclose(hist.cpu().numpy(), hist_ref.cpu().numpy(), rtol=1e-4)
 
 
+def test_invert_noalloc_sequential_fallback(afm):
+    """A swarm that fills most of the scratch (58 000 particles x 4
+    parameters: 3.9 of 4 MiB) leaves no room for the ~0.35 MB of
+    multiple-shooting segments of a 25 600-step record: the winner is
+    re-evaluated by the one-thread sequential FP64 pass instead (segments =
+    0), which agrees with afm_invert's multiple-shooting value to rounding."""
+    spec = W.get("c2", P=58000, iters=1)
+    D = len(spec["free"])
+    prob, U = _record(afm, spec)
+    cfg = afm.make_pso(spec)
+    res_ref, _ = afm.invert(prob, U, cfg)
+    torch.cuda.synchronize()
+    ref = afm.decode_result(res_ref)
+    assert ref["segments"] > 0
+    for _ in range(2):
+        res = torch.zeros(afm.result_dtype_size(), dtype=torch.uint8, device="cuda")
+        afm.invert_noalloc(prob, U, cfg, res)
+        torch.cuda.synchronize()
+        r = afm.decode_result(res)
+        assert r["status"] == 0 and r["nonfinite"] == 0
+        assert r["segments"] == 0
+        assert r["winner"] == ref["winner"] and r["S"] == ref["S"]
+        assert np.array_equal(r["x"][:D], ref["x"][:D])
+        assert np.array_equal(r["theta"], ref["theta"])
+        assert abs(r["S_f64"] - ref["S_f64"]) <= 1e-9 * ref["S_f64"]
+
+
+def test_invert_noalloc_lanes_profile_and_error(afm):
+    """The entry point honours the context's lanes choice (every variant is
+    bit-identical), its iteration launches are seen by the profiling
+    counters (iters + 1 per call), and a successful call clears the message
+    an earlier failed call left behind."""
+    spec = W.get("c2", iters=4)
+    prob, U = _record(afm, spec)
+    cfg = afm.make_pso(spec)
+    bad = afm.make_pso(W.get("c2", P=300000, iters=1))
+    out = {}
+    try:
+        for lanes in ("one", "modes3", "auto"):
+            afm.set_lanes(lanes)
+            afm.profile_enable(True)
+            afm.profile_read()
+            res = torch.zeros(afm.result_dtype_size(), dtype=torch.uint8, device="cuda")
+            with pytest.raises(afm.AfmError):     # leaves a message behind
+                afm.invert_noalloc(prob, U, bad, res)
+            assert afm.lib().afm_last_error() != b""
+            afm.invert_noalloc(prob, U, cfg, res)
+            assert afm.lib().afm_last_error() == b""
+            torch.cuda.synchronize()
+            ms, n = afm.profile_read()
+            assert n == spec["iters"] + 1 and ms > 0
+            out[lanes] = afm.decode_result(res)
+    finally:
+        afm.profile_enable(False)
+        afm.set_lanes("auto")
+    for lanes in ("one", "modes3"):
+        assert out[lanes]["S"] == out["auto"]["S"]
+        assert np.array_equal(out[lanes]["x"], out["auto"]["x"])
+
+
 def test_invert_noalloc_rejects_oversized_swarm(afm):
     spec = W.get("c2", P=300000, iters=1)
     prob, U = _record(afm, W.get("c2"))
