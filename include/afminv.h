@@ -216,8 +216,10 @@ const char* afm_status_string(int status);
 int afm_version(void);
 
 /* Kernel timing (tracing aid).  While enabled, the FP32 forward kernel of
- * afm_forward_batch and each fused iteration kernel of afm_invert are
- * bracketed by CUDA events on the call's stream.  afm_profile_read waits for
+ * afm_forward_batch, each fused iteration kernel of afm_invert (and
+ * afm_invert_noalloc), the persistent swarm kernel of afm_invert_batch
+ * (event-record nodes of its launch graph) and the polish passes of the
+ * polished inversions are bracketed by CUDA events on the call's stream.  afm_profile_read waits for
  * the recorded events and returns the summed device time [ms] and the number
  * of timed launches since the previous read. */
 afm_status afm_profile_enable(afm_ctx* ctx, int on);
@@ -335,9 +337,22 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
 
 /* ---- many pixel inversions in one launch (image scans) -------------------
  * n_pix independent IPs, pixel i with record U_cat[off[i] .. off[i+1]) (its
- * own length; prob->n_steps is only validated, not used) and Philox counter
- * word 2 = pixel0 + i.  Each pixel runs the same swarm as afm_invert with
- * cfg->P particles (<= 4096) and cfg->iters updates (cfg->pixel is ignored).
+ * own length) and Philox counter word 2 = pixel0 + i.  Each pixel runs the
+ * same swarm as afm_invert with cfg->P particles (<= 4096) and cfg->iters
+ * updates (cfg->pixel is ignored).
+ * Problems (the IP statement of Sec. 2.3, per pixel): probs[n_prob] with
+ * n_prob = 1 (one problem for every pixel) or n_prob = n_pix (pixel i
+ * inverts against probs[i]: an image scan whose set-point, free amplitude
+ * or cantilever calibration drifts from pixel to pixel).  Per-pixel
+ * problems must agree with probs[0] in model, n_modes, force law,
+ * steps_per_cycle, drive_mode 0, n_points 0 and the swarm's
+ * parametrisation (n_free, slot, lo, hi, log_scale); they may differ in
+ * f1_hz, k_N_per_m, Q, A0_m, Zc_m, the fixed parameter values and n_steps
+ * (the largest n_steps sizes the FP64 re-evaluation, so no record may be
+ * longer than it).  Else AFM_ERR_INVALID_ARG.  With per-pixel problems
+ * each pixel's constants are uploaded from host memory into the workspace
+ * on `stream` before the launch (the call returns once they are staged),
+ * and pixel i's result equals afm_invert on probs[i] alone bit for bit.
  * One persistent kernel: blocks pull pixels from a queue, longest record
  * first, and keep the whole swarm of a pixel on chip; then every winner is
  * re-evaluated in FP64.  results [n_pix] (device afm_result) are indexed by
@@ -352,13 +367,15 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
  * per thread, DMT swarms step two particles per paired FP32 instruction
  * (bit-identical to one per thread).  The choice used is written back to
  * *particles_per_thread if non-NULL.
- * workspace: device, >= afm_invert_batch_workspace_size(prob, n_pix),
- * 256-aligned (the queue, and the FP64 re-evaluation of every pixel's winner
- * by multiple shooting: ~250 bytes per 32-step segment of the longest record
- * and pixel, 1.6 GB for 4096 records of 51 200 steps). */
-afm_status afm_invert_batch_workspace_size(const afm_problem* prob, int n_pix, size_t* bytes);
-afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
-                            const int64_t* off, int n_pix, uint32_t pixel0,
+ * workspace: device, >= afm_invert_batch_workspace_size(probs, n_prob,
+ * n_pix), 256-aligned (the queue, the FP64 re-evaluation of every pixel's
+ * winner by multiple shooting: ~250 bytes per 32-step segment of the
+ * longest record and pixel, 1.6 GB for 4096 records of 51 200 steps; with
+ * per-pixel problems ~6 KB per pixel of constants and drive tables). */
+afm_status afm_invert_batch_workspace_size(const afm_problem* probs, int n_prob, int n_pix,
+                                           size_t* bytes);
+afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* probs, int n_prob,
+                            const float* U_cat, const int64_t* off, int n_pix, uint32_t pixel0,
                             const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
                             afm_result* results, int* particles_per_thread, void* stream);
 
@@ -379,7 +396,8 @@ typedef struct {
 } afm_batch_select;
 
 /* ---- many pixel inversions with gradient polish --------------------------
- * afm_invert_batch (same queue, swarms and autotuner; no graph capture), then
+ * afm_invert_batch (same problems, queue, swarms and autotuner; no graph
+ * capture), then
  * for every pixel the polish_k personal bests of lowest misfit (lowest index
  * on ties) take polish_steps steps of the polish of afm_polish (`method`,
  * n_cand trial points), all pixels' candidates together in each launch;
@@ -388,20 +406,23 @@ typedef struct {
  * afm_invert_batch.  Per candidate the arithmetic equals afm_invert_polished
  * on that pixel alone.  AFM_POLISH_STEEPEST: prob->n_steps must be >= the
  * longest record, as it sizes the adjoint checkpoints (a longer record keeps
- * its swarm winner).  select (or NULL): a subset of the n_pix pixels and a
- * prior for each (afm_batch_select).
- * workspace: device, >= afm_invert_batch_polished_workspace_size(n_run) with
- * n_run the number of pixels inverted (select->n_run, else n_pix), 256-aligned. */
-afm_status afm_invert_batch_polished_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
-                                                    int n_run, int polish_k, int n_cand,
-                                                    int method, size_t* bytes);
-afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
-                                     const int64_t* off, int n_pix, uint32_t pixel0,
-                                     const afm_pso_cfg* cfg, int polish_k, int polish_steps,
-                                     int n_cand, int method, const afm_batch_select* select,
-                                     void* workspace, size_t workspace_bytes,
-                                     afm_result* results, int* particles_per_thread,
-                                     void* stream);
+ * its swarm winner).  Per-pixel problems (n_prob = n_pix) are polished by
+ * AFM_POLISH_LM only (else AFM_ERR_UNSUPPORTED).  select (or NULL): a subset
+ * of the n_pix pixels and a prior for each (afm_batch_select).
+ * workspace: device, >= afm_invert_batch_polished_workspace_size(probs,
+ * n_prob, ..., n_run) with n_run the number of pixels inverted
+ * (select->n_run, else n_pix), 256-aligned. */
+afm_status afm_invert_batch_polished_workspace_size(const afm_problem* probs, int n_prob,
+                                                    const afm_pso_cfg* cfg, int n_run,
+                                                    int polish_k, int n_cand, int method,
+                                                    size_t* bytes);
+afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* probs, int n_prob,
+                                     const float* U_cat, const int64_t* off, int n_pix,
+                                     uint32_t pixel0, const afm_pso_cfg* cfg, int polish_k,
+                                     int polish_steps, int n_cand, int method,
+                                     const afm_batch_select* select, void* workspace,
+                                     size_t workspace_bytes, afm_result* results,
+                                     int* particles_per_thread, void* stream);
 
 /* ---- image scans with cross-pixel warm start ------------------------------
  * A row-major width x height image (pixel id = row * width + column; record

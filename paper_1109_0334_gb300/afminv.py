@@ -126,13 +126,14 @@ def lib():
                                                              i, i, i, C.POINTER(C.c_size_t)]
             L.afm_invert_polished.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), i, i,
                                               i, i, vp, C.c_size_t, vp, vp, vp]
-            L.afm_invert_batch_workspace_size.argtypes = [C.POINTER(Problem), i, C.POINTER(C.c_size_t)]
-            L.afm_invert_batch.argtypes = [vp, C.POINTER(Problem), vp, vp, i, u32,
+            L.afm_invert_batch_workspace_size.argtypes = [C.POINTER(Problem), i, i,
+                                                          C.POINTER(C.c_size_t)]
+            L.afm_invert_batch.argtypes = [vp, C.POINTER(Problem), i, vp, vp, i, u32,
                                            C.POINTER(PsoCfg), vp, C.c_size_t, vp,
                                            C.POINTER(C.c_int), vp]
             L.afm_invert_batch_polished_workspace_size.argtypes = [
-                C.POINTER(Problem), C.POINTER(PsoCfg), i, i, i, i, C.POINTER(C.c_size_t)]
-            L.afm_invert_batch_polished.argtypes = [vp, C.POINTER(Problem), vp, vp, i, u32,
+                C.POINTER(Problem), i, C.POINTER(PsoCfg), i, i, i, i, C.POINTER(C.c_size_t)]
+            L.afm_invert_batch_polished.argtypes = [vp, C.POINTER(Problem), i, vp, vp, i, u32,
                                                     C.POINTER(PsoCfg), i, i, i, i,
                                                     C.POINTER(BatchSelect), vp, C.c_size_t,
                                                     vp, C.POINTER(C.c_int), vp]
@@ -492,17 +493,28 @@ def invert_polished(prob: Problem, U, cfg: PsoCfg, polish_k: int = 32, polish_st
     return result, history
 
 
-def invert_batch_workspace_size(prob: Problem, n_pix: int) -> int:
+def _problems(prob):
+    """(pointer to the first of an afm_problem array, count) for one Problem
+    (shared by every pixel) or a sequence of them (one per pixel)."""
+    if isinstance(prob, Problem):
+        return C.byref(prob), 1
+    arr = (Problem * len(prob))(*prob)
+    return arr, len(prob)
+
+
+def invert_batch_workspace_size(prob, n_pix: int) -> int:
     n = C.c_size_t()
-    _check(lib().afm_invert_batch_workspace_size(C.byref(prob), int(n_pix), C.byref(n)))
+    pp, n_prob = _problems(prob)
+    _check(lib().afm_invert_batch_workspace_size(pp, n_prob, int(n_pix), C.byref(n)))
     return int(n.value)
 
 
-def invert_batch(prob: Problem, U_cat, off, cfg: PsoCfg, pixel0: int = 0,
+def invert_batch(prob, U_cat, off, cfg: PsoCfg, pixel0: int = 0,
                  particles_per_thread: int = 0, workspace=None, results=None, stream=None):
-    """Many pixel inversions in one graph launch.  U_cat float32 CUDA [sum n_i],
-    off int64 CUDA [n_pix + 1].  Returns (results uint8 [n_pix, sizeof(afm_result)],
-    particles per thread used)."""
+    """Many pixel inversions in one graph launch.  prob: one Problem for all
+    pixels or a sequence of n_pix (one per pixel).  U_cat float32 CUDA [sum
+    n_i], off int64 CUDA [n_pix + 1].  Returns (results uint8 [n_pix,
+    sizeof(afm_result)], particles per thread used)."""
     import torch
     dev = U_cat.device
     n_pix = int(off.shape[0]) - 1
@@ -512,29 +524,32 @@ def invert_batch(prob: Problem, U_cat, off, cfg: PsoCfg, pixel0: int = 0,
     if results is None:
         results = torch.zeros((n_pix, C.sizeof(Result)), dtype=torch.uint8, device=dev)
     kp = C.c_int(int(particles_per_thread))
-    _check(lib().afm_invert_batch(context(dev.index), C.byref(prob), _ptr(U_cat), _ptr(off), n_pix,
+    pp, n_prob = _problems(prob)
+    _check(lib().afm_invert_batch(context(dev.index), pp, n_prob, _ptr(U_cat), _ptr(off), n_pix,
                                   int(pixel0), C.byref(cfg), _ptr(workspace),
                                   C.c_size_t(workspace.numel()), _ptr(results), C.byref(kp),
                                   _stream(stream)))
     return results, kp.value
 
 
-def invert_batch_polished_workspace_size(prob: Problem, cfg: PsoCfg, n_pix: int, polish_k: int,
+def invert_batch_polished_workspace_size(prob, cfg: PsoCfg, n_pix: int, polish_k: int,
                                          n_cand: int = 16, method="steepest") -> int:
     n = C.c_size_t()
-    _check(lib().afm_invert_batch_polished_workspace_size(C.byref(prob), C.byref(cfg), int(n_pix),
+    pp, n_prob = _problems(prob)
+    _check(lib().afm_invert_batch_polished_workspace_size(pp, n_prob, C.byref(cfg), int(n_pix),
                                                           int(polish_k), int(n_cand),
                                                           _method(method), C.byref(n)))
     return int(n.value)
 
 
-def invert_batch_polished(prob: Problem, U_cat, off, cfg: PsoCfg, polish_k: int, polish_steps: int,
+def invert_batch_polished(prob, U_cat, off, cfg: PsoCfg, polish_k: int, polish_steps: int,
                           n_cand: int = 16, pixel0: int = 0, particles_per_thread: int = 0,
                           workspace=None, results=None, stream=None, method="steepest",
                           pixels=None, box_lo=None, box_hi=None, seeds=None):
     """Many pixel inversions, each followed by the gradient polish of its
-    polish_k best particles (afm_invert_batch_polished).  prob.n_steps must
-    bound the record lengths.  Optional selection and prior (CUDA tensors):
+    polish_k best particles (afm_invert_batch_polished).  prob: one Problem
+    or one per pixel (as invert_batch); n_steps must bound the record
+    lengths.  Optional selection and prior (CUDA tensors):
     pixels int32 [n_run], box_lo / box_hi float32 [n_run, D], seeds float32
     [n_run, n_seed, D].  Returns (results, particles per thread used)."""
     import torch
@@ -557,7 +572,8 @@ def invert_batch_polished(prob: Problem, U_cat, off, cfg: PsoCfg, polish_k: int,
     if results is None:
         results = torch.zeros((n_pix, C.sizeof(Result)), dtype=torch.uint8, device=dev)
     kp = C.c_int(int(particles_per_thread))
-    _check(lib().afm_invert_batch_polished(context(dev.index), C.byref(prob), _ptr(U_cat), _ptr(off),
+    pp, n_prob = _problems(prob)
+    _check(lib().afm_invert_batch_polished(context(dev.index), pp, n_prob, _ptr(U_cat), _ptr(off),
                                            n_pix, int(pixel0), C.byref(cfg), int(polish_k),
                                            int(polish_steps), int(n_cand), _method(method),
                                            None if sel is None else C.byref(sel), _ptr(workspace),

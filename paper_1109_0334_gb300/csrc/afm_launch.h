@@ -43,6 +43,21 @@ cudaError_t launch_synth(const KConst<float>& K, const double* x_truth, int n_pi
                          const int64_t* off, int sub, float sigma_nm, uint64_t seed,
                          uint32_t pixel0, float* U_cat, cudaStream_t st);
 
+// Per-pixel problem constants of a batch whose pixels differ in their
+// cantilever or set-point (afm_problem per pixel): indexed by pixel id, with
+// each pixel's drive table at its 2 spc half-step phases (+ wrap entry) in
+// FP64 and rounded to FP32.  kf == nullptr: every pixel uses the launch's
+// constants.
+struct PixConst {
+    const KConst<float>* kf;    // [n_pix]
+    const KConst<double>* kd;   // [n_pix]
+    const double* tab64;        // [n_pix][ld]
+    const float* tab32;         // [n_pix][ld]
+    int ld;
+};
+// fills tab64 / tab32 of n_pix pixels from kd (the formula of build_drive_table)
+cudaError_t launch_pix_tables(const PixConst& pc, int n_pix, int spc2, cudaStream_t st);
+
 // many independent pixel inversions in one persistent launch
 struct BatchArgs {
     const float* U;        // concatenated records
@@ -61,15 +76,18 @@ struct BatchArgs {
     const float* box_hi;
     const float* seeds;
     int n_seed;
+    PixConst pix;          // per-pixel constants (pix.kf == nullptr: shared)
 };
 int batch_threads(int P, int kp);
 // largest block of the batch kernel with kp particles per thread (the
 // paired-instruction kernels of kp = 2, 4 are built for up to 128 registers)
 int batch_max_threads(int kp);
-size_t batch_smem(int P, int D, int spc2);
+// dynamic shared memory of the batch kernel (pp: per-pixel constants)
+size_t batch_smem(int P, int D, int spc2, bool pp = false);
 int batch_sort_max();
 cudaError_t batch_sort(const int64_t* off, int n_pix, int* order, cudaStream_t st);
-cudaError_t batch_occupancy(int m, int force, int kp, int P, int D, int spc2, int* blocks_per_sm);
+cudaError_t batch_occupancy(int m, int force, int kp, int P, int D, int spc2, bool pp,
+                            int* blocks_per_sm);
 cudaError_t launch_batch(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a, int kp,
                          int grid, cudaStream_t st);
 
@@ -86,9 +104,11 @@ cudaError_t launch_adjoint(const KConst<float>& K, const float* x, int P, const 
 // Levenberg-Marquardt polish (kern_lm.cu): sensitivity pass (S [P], H
 // [P][D][D], b [P][D]; ragged form as launch_adjoint), damped trial points,
 // choice of the best trial point
+// (pix: per-pixel constants of the ragged form, pix.kf == nullptr: K for all)
 cudaError_t launch_sens(const KConst<float>& K, const float* x, int P, const float* U, float* S,
                         double* H, double* b, cudaStream_t st, const int64_t* off = nullptr,
-                        const int* order = nullptr, int per_slot = 1);
+                        const int* order = nullptr, int per_slot = 1,
+                        const PixConst& pix = PixConst{});
 // the same pass with one lane per parameter direction (kern_lm_lanes.cu);
 // launch_sens uses it when P x lanes fits one warp per SM sub-partition
 bool sens_lanes_preferred(int P, int D);
@@ -128,7 +148,7 @@ cudaError_t launch_topk_pix(const float* pb_all, int n_pix, int P, int D, int Kc
                             float* Sk, int* ik, cudaStream_t st);
 cudaError_t launch_forward_ragged(const KConst<float>& K, const float* x, int Ptot, const float* U_cat,
                                   const int64_t* off, const int* order, int per_slot, float* S,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const PixConst& pix = PixConst{});
 cudaError_t launch_pick_pix(int n_pix, int D, int Kc, const float* xk, const float* Sk,
                             const int* ik, const int* order, int iters, afm_result* res,
                             cudaStream_t st);

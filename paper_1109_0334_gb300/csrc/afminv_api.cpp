@@ -23,18 +23,24 @@ using afm::KConst;
 #include <vector>
 
 // One instantiated launch graph of afm_invert_batch and the argument bytes it
-// was built from.
+// was built from.  Two event-record nodes bracket the swarm kernel: they
+// record the graph's own events, or, while profiling is on, a fresh pair per
+// launch (afm_profile_read).
 struct afm_batch_graph {
     std::vector<unsigned char> key;
+    cudaGraph_t graph;
     cudaGraphExec_t exec;
+    cudaGraphNode_t ev_node[2];
+    cudaEvent_t ev_own[2];
 };
 
 struct afm_ctx {
     int device;
     int num_sms;
     // afm_invert_batch: particles per thread chosen by the autotuner, per
-    // (modes, force, particles, free parameters, steps per cycle)
-    std::map<std::tuple<int, int, int, int, int>, int> batch_kp;
+    // (modes, force, particles, free parameters, steps per cycle, per-pixel
+    // problems)
+    std::map<std::tuple<int, int, int, int, int, int>, int> batch_kp;
     cudaStream_t capture_stream = nullptr;
     std::vector<afm_batch_graph> batch_graphs;
     // kernel timing (afm_profile_*): events around each fused iteration launch
@@ -720,6 +726,64 @@ size_t batch_ws_bytes(const afm_problem& pr, int n_run) {
                                             n_run));
 }
 
+// Per-pixel problems of a batch (an afm_problem per pixel): their constants
+// and drive tables at the end of the workspace, indexed by pixel id.
+struct PixLayout {
+    size_t kf, kd, t64, t32, total;
+    int ld;
+};
+
+PixLayout pix_layout(int n_prob, int spc) {
+    PixLayout L{};
+    if (n_prob <= 1) return L;
+    const size_t n = (size_t)n_prob;
+    L.ld = (2 * spc + 1 + 3) & ~3;
+    L.kf = 0;
+    L.kd = align256(sizeof(KConst<float>) * n);
+    L.t64 = L.kd + align256(sizeof(KConst<double>) * n);
+    L.t32 = L.t64 + align256(sizeof(double) * n * L.ld);
+    L.total = L.t32 + align256(sizeof(float) * n * L.ld);
+    return L;
+}
+
+// Checks a batch's problem array: 1 (shared) or one per pixel, each valid,
+// all with the same model, modes, force law, steps per cycle and swarm
+// parametrisation (free slots, bounds and scales); they may differ in the
+// cantilever (f1, k, Q), the free amplitude, the set-point, the fixed
+// parameter values and n_steps.  *eff receives probs[0] with n_steps the
+// largest of them (it sizes the FP64 re-evaluation).
+afm_status check_batch_probs(const afm_problem* probs, int n_prob, int n_pix, afm_problem* eff) {
+    if (!probs) return fail(AFM_ERR_INVALID_ARG, "problem array is NULL");
+    if (n_prob != 1 && n_prob != n_pix)
+        return fail(AFM_ERR_INVALID_ARG, "n_prob = %d: 1 (shared) or n_pix = %d problems", n_prob,
+                    n_pix);
+    const afm_problem& a = probs[0];
+    afm_status st = check_problem(&a);
+    if (st) return st;
+    *eff = a;
+    for (int i = 1; i < n_prob; ++i) {
+        const afm_problem& b = probs[i];
+        if ((st = check_problem(&b))) {
+            char msg[sizeof(g_err)];
+            std::snprintf(msg, sizeof(msg), "%s", g_err);
+            return fail(st, "problem %d: %s", i, msg);
+        }
+        bool same = b.model == a.model && b.n_modes == a.n_modes && b.force == a.force &&
+                    b.steps_per_cycle == a.steps_per_cycle && b.n_free == a.n_free &&
+                    b.drive_mode == a.drive_mode && b.n_points == a.n_points;
+        for (int d = 0; same && d < a.n_free; ++d)
+            same = b.slot[d] == a.slot[d] && b.lo[d] == a.lo[d] && b.hi[d] == a.hi[d] &&
+                   b.log_scale[d] == a.log_scale[d];
+        if (!same)
+            return fail(AFM_ERR_INVALID_ARG,
+                        "problem %d differs from problem 0 in model, modes, force law, steps per "
+                        "cycle or swarm parametrisation",
+                        i);
+        eff->n_steps = std::max(eff->n_steps, b.n_steps);
+    }
+    return AFM_OK;
+}
+
 template <typename T>
 void append_bytes(std::vector<unsigned char>& v, const T& x) {
     const unsigned char* p = reinterpret_cast<const unsigned char*>(&x);
@@ -731,11 +795,12 @@ void append_bytes(std::vector<unsigned char>& v, const T& x) {
 // lowest estimated batch time (the wave's time x the waves the batch needs).
 afm_status batch_tune(afm_ctx* ctx, const KConst<float>& Kf, const afm::PsoConst& pc,
                       const afm::BatchArgs& a, cudaStream_t s, int* kp_out, int* occ_out) {
-    const auto key = std::make_tuple(Kf.m, Kf.force, pc.P, pc.D, Kf.spc2);
+    const bool pp = a.pix.kf != nullptr;
+    const auto key = std::make_tuple(Kf.m, Kf.force, pc.P, pc.D, Kf.spc2, (int)pp);
     auto it = ctx->batch_kp.find(key);
     if (it != ctx->batch_kp.end()) {
         *kp_out = it->second;
-        AFM_CUDA(afm::batch_occupancy(Kf.m, Kf.force, *kp_out, pc.P, pc.D, Kf.spc2, occ_out),
+        AFM_CUDA(afm::batch_occupancy(Kf.m, Kf.force, *kp_out, pc.P, pc.D, Kf.spc2, pp, occ_out),
                  "batch occupancy");
         return AFM_OK;
     }
@@ -748,7 +813,7 @@ afm_status batch_tune(afm_ctx* ctx, const KConst<float>& Kf, const afm::PsoConst
         const int threads = afm::batch_threads(pc.P, kp);
         if (threads > afm::batch_max_threads(kp) || (kp > 1 && Kf.m > 3)) continue;
         int occ = 0;
-        if (afm::batch_occupancy(Kf.m, Kf.force, kp, pc.P, pc.D, Kf.spc2, &occ) != cudaSuccess ||
+        if (afm::batch_occupancy(Kf.m, Kf.force, kp, pc.P, pc.D, Kf.spc2, pp, &occ) != cudaSuccess ||
             occ < 1) {
             cudaGetLastError();
             continue;
@@ -885,7 +950,12 @@ afm_status afm_ctx_destroy(afm_ctx* ctx) {
             cudaEventDestroy(pr.second);
         }
         for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-        for (auto& g : ctx->batch_graphs) cudaGraphExecDestroy(g.exec);
+        for (auto& g : ctx->batch_graphs) {
+            cudaGraphExecDestroy(g.exec);
+            cudaGraphDestroy(g.graph);
+            cudaEventDestroy(g.ev_own[0]);
+            cudaEventDestroy(g.ev_own[1]);
+        }
         if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     }
     delete ctx;
@@ -1248,17 +1318,20 @@ const double kLmLambda0 = 1e-7, kLmRatio = 10.0;
 // nullptr): candidate k is compared with the record of pixel order[k / per].
 afm_status polish_step(afm_ctx* ctx, const KConst<float>& K, int method, const float* U,
                        const int64_t* off, const int* order, int per, float* x, float* S, int Kn,
-                       int J, const PolishLayout& L, char* ws, cudaStream_t s) {
+                       int J, const PolishLayout& L, char* ws, cudaStream_t s,
+                       const afm::PixConst& pix = afm::PixConst{}) {
     float* Xc = reinterpret_cast<float*>(ws + L.Xc);
     float* Sc = reinterpret_cast<float*>(ws + L.Sc);
     const int D = K.D;
     if (method == AFM_POLISH_LM) {
         double* H = reinterpret_cast<double*>(ws + L.H);
         double* b = reinterpret_cast<double*>(ws + L.b);
-        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_sens(K, x, Kn, U, S, H, b, s, off, order, per); }),
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_sens(K, x, Kn, U, S, H, b, s, off, order, per, pix); }),
                  "sensitivity kernel");
         AFM_CUDA(afm::launch_lm_cand(D, Kn, J, x, H, b, kLmLambda0, kLmRatio, Xc, s), "LM trial kernel");
     } else {
+        if (pix.kf != nullptr)
+            return fail(AFM_ERR_UNSUPPORTED, "the steepest-descent polish needs one problem for all pixels");
         float* G = reinterpret_cast<float*>(ws + L.G);
         float* ck = reinterpret_cast<float*>(ws + L.ckpt);
         AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_adjoint(K, x, Kn, U, S, G, ck, s, off, order, per); }),
@@ -1267,7 +1340,7 @@ afm_status polish_step(afm_ctx* ctx, const KConst<float>& K, int method, const f
                  "polish candidate kernel");
     }
     if (off != nullptr)
-        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_ragged(K, Xc, Kn * J, U, off, order, per * J, Sc, s); }),
+        AFM_CUDA(timed_launch(ctx, s, [&] { return afm::launch_forward_ragged(K, Xc, Kn * J, U, off, order, per * J, Sc, s, pix); }),
                  "ragged forward kernel");
     else
         AFM_CUDA(afm::launch_forward_f32(K, Xc, Kn * J, nullptr, U, Sc, nullptr, s), "forward kernel");
@@ -1429,12 +1502,14 @@ afm_status afm_invert_polished(afm_ctx* ctx, const afm_problem* prob, const floa
     return AFM_OK;
 }
 
-afm_status afm_invert_batch_workspace_size(const afm_problem* prob, int n_pix, size_t* bytes) {
+afm_status afm_invert_batch_workspace_size(const afm_problem* probs, int n_prob, int n_pix,
+                                           size_t* bytes) {
     g_err[0] = 0;
     if (!bytes || n_pix < 1) return fail(AFM_ERR_INVALID_ARG, "n_pix >= 1 and bytes needed");
-    afm_status st = check_problem(prob);
+    afm_problem eff;
+    afm_status st = check_batch_probs(probs, n_prob, n_pix, &eff);
     if (st) return st;
-    *bytes = batch_ws_bytes(*prob, n_pix);
+    *bytes = batch_ws_bytes(eff, n_pix) + pix_layout(n_prob, eff.steps_per_cycle).total;
     return AFM_OK;
 }
 
@@ -1454,13 +1529,15 @@ struct BatchSetup {
     int kp, grid;
 };
 
-afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
+afm_status batch_setup(afm_ctx* ctx, const afm_problem* probs, int n_prob, const float* U_cat,
                        const int64_t* off, int n_pix, uint32_t pixel0, const afm_pso_cfg* cfg,
-                       void* workspace, afm_result* results, int* particles_per_thread,
-                       cudaStream_t s, const char* who, BatchSetup* out,
+                       void* workspace, size_t pix_at, afm_result* results,
+                       int* particles_per_thread, cudaStream_t s, const char* who, BatchSetup* out,
                        const afm_batch_select* select = nullptr) {
-    afm_status st = check_problem(prob);
+    afm_problem eff;
+    afm_status st = check_batch_probs(probs, n_prob, n_pix, &eff);
     if (st) return st;
+    const afm_problem* prob = &eff;
     if ((st = modal_only(prob, who))) return st;
     if ((st = check_ctx(ctx))) return st;
     if ((st = check_pso(cfg, prob->n_free))) return st;
@@ -1469,7 +1546,7 @@ afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat
     if (reinterpret_cast<uintptr_t>(workspace) % 256)
         return fail(AFM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     if (cfg->P > 4096) return fail(AFM_ERR_INVALID_ARG, "batched swarms hold at most 4096 particles");
-    const size_t smem = afm::batch_smem(cfg->P, prob->n_free, 2 * prob->steps_per_cycle);
+    const size_t smem = afm::batch_smem(cfg->P, prob->n_free, 2 * prob->steps_per_cycle, n_prob > 1);
     if (smem > 200 * 1024)
         return fail(AFM_ERR_INVALID_ARG, "swarm state of %zu bytes exceeds shared memory", smem);
     // queue (and sort order) sized for the pixels inverted
@@ -1506,6 +1583,31 @@ afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat
         a.seeds = select->n_seed > 0 ? select->seeds : nullptr;
         a.n_seed = select->n_seed;
     }
+    if (n_prob > 1) {
+        // every pixel's constants (FP32 and FP64), uploaded to the workspace,
+        // and its drive tables computed there
+        const PixLayout X = pix_layout(n_prob, prob->steps_per_cycle);
+        char* pw = ws + pix_at;
+        std::vector<KConst<float>> kf(n_prob);
+        std::vector<KConst<double>> kd(n_prob);
+        for (int i = 0; i < n_prob; ++i) {
+            fill_kconst(probs[i], prob->steps_per_cycle, prob->n_steps, kf[i]);
+            fill_kconst(probs[i], prob->steps_per_cycle, prob->n_steps, kd[i]);
+        }
+        AFM_CUDA(cudaMemcpyAsync(pw + X.kf, kf.data(), sizeof(KConst<float>) * (size_t)n_prob,
+                                 cudaMemcpyHostToDevice, s),
+                 "per-pixel constants upload");
+        AFM_CUDA(cudaMemcpyAsync(pw + X.kd, kd.data(), sizeof(KConst<double>) * (size_t)n_prob,
+                                 cudaMemcpyHostToDevice, s),
+                 "per-pixel constants upload");
+        a.pix.kf = reinterpret_cast<const KConst<float>*>(pw + X.kf);
+        a.pix.kd = reinterpret_cast<const KConst<double>*>(pw + X.kd);
+        a.pix.tab64 = reinterpret_cast<const double*>(pw + X.t64);
+        a.pix.tab32 = reinterpret_cast<const float*>(pw + X.t32);
+        a.pix.ld = X.ld;
+        AFM_CUDA(afm::launch_pix_tables(a.pix, n_prob, 2 * prob->steps_per_cycle, s),
+                 "per-pixel drive tables");
+    }
     // queue order (longest record first) is needed by the tuner's probe too
     if (a.order && select == nullptr)
         AFM_CUDA(afm::batch_sort(off, n_pix, const_cast<int*>(a.order), s), "sort kernel");
@@ -1516,7 +1618,8 @@ afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat
         if (afm::batch_threads(pc.P, want) > afm::batch_max_threads(want) || (want > 1 && B.Kf.m > 3))
             return fail(AFM_ERR_INVALID_ARG, "particles_per_thread %d unsupported here", want);
         kp = want;
-        AFM_CUDA(afm::batch_occupancy(B.Kf.m, B.Kf.force, kp, pc.P, pc.D, B.Kf.spc2, &occ),
+        AFM_CUDA(afm::batch_occupancy(B.Kf.m, B.Kf.force, kp, pc.P, pc.D, B.Kf.spc2, n_prob > 1,
+                                      &occ),
                  "batch occupancy");
         if (occ < 1) return fail(AFM_ERR_UNSUPPORTED, "batch kernel does not fit (P = %d)", pc.P);
     } else if (want != 0) {
@@ -1534,21 +1637,24 @@ afm_status batch_setup(afm_ctx* ctx, const afm_problem* prob, const float* U_cat
 
 extern "C" {
 
-afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
-                            const int64_t* off, int n_pix, uint32_t pixel0,
+afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* probs, int n_prob,
+                            const float* U_cat, const int64_t* off, int n_pix, uint32_t pixel0,
                             const afm_pso_cfg* cfg, void* workspace, size_t workspace_bytes,
                             afm_result* results, int* particles_per_thread, void* stream) {
     AFM_TRACE("afm_invert_batch");
     g_err[0] = 0;
+    if (n_pix < 1) return fail(AFM_ERR_INVALID_ARG, "n_pix must be >= 1");
+    afm_problem eff;
     afm_status st0;
-    if ((st0 = check_problem(prob))) return st0;
-    if (n_pix >= 1 && workspace_bytes < batch_ws_bytes(*prob, n_pix))
-        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes,
-                    batch_ws_bytes(*prob, n_pix));
+    if ((st0 = check_batch_probs(probs, n_prob, n_pix, &eff))) return st0;
+    const size_t pix_at = batch_ws_bytes(eff, n_pix);
+    const size_t need = pix_at + pix_layout(n_prob, eff.steps_per_cycle).total;
+    if (workspace_bytes < need)
+        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, need);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     BatchSetup B;
-    afm_status st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, cfg, workspace, results,
-                                particles_per_thread, s, "afm_invert_batch", &B);
+    afm_status st = batch_setup(ctx, probs, n_prob, U_cat, off, n_pix, pixel0, cfg, workspace,
+                                pix_at, results, particles_per_thread, s, "afm_invert_batch", &B);
     if (st) return st;
     const KConst<float>& Kf = B.Kf;
     const KConst<double>& Kd = B.Kd;
@@ -1563,36 +1669,84 @@ afm_status afm_invert_batch(afm_ctx* ctx, const afm_problem* prob, const float* 
     append_bytes(key, a);
     append_bytes(key, kp);
     append_bytes(key, grid);
-    cudaGraphExec_t exec = nullptr;
+    afm_batch_graph* G = nullptr;
     for (auto& g : ctx->batch_graphs)
-        if (g.key == key) exec = g.exec;
-    if (!exec) {
+        if (g.key == key) G = &g;
+    if (!G) {
         if (!ctx->capture_stream)
             AFM_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking),
                      "cudaStreamCreate");
-        cudaStream_t c = ctx->capture_stream;
-        AFM_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal), "begin capture");
-        cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), c);
-        if (e == cudaSuccess && a.order) e = afm::batch_sort(off, n_pix, const_cast<int*>(a.order), c);
-        if (e == cudaSuccess) e = afm::launch_batch(Kf, pc, a, kp, grid, c);
-        if (e == cudaSuccess) e = afm::launch_reeval_batch(Kf, Kd, B.R, a, c);
-        cudaGraph_t graph = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(c, &graph);
-        if (e != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            return cuda_fail(e, "batch graph capture");
+        afm_batch_graph g{};
+        g.key = key;
+        AFM_CUDA(cudaEventCreate(&g.ev_own[0]), "cudaEventCreate");
+        if (cudaEventCreate(&g.ev_own[1]) != cudaSuccess) {
+            cudaEventDestroy(g.ev_own[0]);
+            return fail(AFM_ERR_CUDA, "cudaEventCreate failed");
         }
-        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        auto drop = [&](cudaError_t err, const char* where) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.graph) cudaGraphDestroy(g.graph);
+            cudaEventDestroy(g.ev_own[0]);
+            cudaEventDestroy(g.ev_own[1]);
+            return cuda_fail(err, where);
+        };
+        cudaStream_t c = ctx->capture_stream;
+        cudaError_t e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return drop(e, "begin capture");
+        e = cudaMemsetAsync(a.queue, 0, sizeof(int), c);
+        if (e == cudaSuccess && a.order) e = afm::batch_sort(off, n_pix, const_cast<int*>(a.order), c);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(g.ev_own[0], c, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = afm::launch_batch(Kf, pc, a, kp, grid, c);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(g.ev_own[1], c, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = afm::launch_reeval_batch(Kf, Kd, B.R, a, c);
+        cudaError_t e2 = cudaStreamEndCapture(c, &g.graph);
+        if (e != cudaSuccess) return drop(e, "batch graph capture");
+        if (e2 != cudaSuccess) return drop(e2, "cudaStreamEndCapture");
+        // the two event-record nodes around the swarm kernel
+        size_t n_nodes = 0;
+        if ((e = cudaGraphGetNodes(g.graph, nullptr, &n_nodes)) != cudaSuccess)
+            return drop(e, "cudaGraphGetNodes");
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        if ((e = cudaGraphGetNodes(g.graph, nodes.data(), &n_nodes)) != cudaSuccess)
+            return drop(e, "cudaGraphGetNodes");
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType ty;
+            cudaEvent_t ev = nullptr;
+            if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord ||
+                cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess)
+                continue;
+            if (ev == g.ev_own[0]) g.ev_node[0] = nd;
+            if (ev == g.ev_own[1]) g.ev_node[1] = nd;
+        }
+        if (!g.ev_node[0] || !g.ev_node[1])
+            return drop(cudaErrorInvalidValue, "batch graph: event nodes not found");
+        if ((e = cudaGraphInstantiate(&g.exec, g.graph, 0)) != cudaSuccess)
+            return drop(e, "cudaGraphInstantiate");
         if (ctx->batch_graphs.size() >= 8) {
-            cudaGraphExecDestroy(ctx->batch_graphs.front().exec);
+            afm_batch_graph& old = ctx->batch_graphs.front();
+            cudaGraphExecDestroy(old.exec);
+            cudaGraphDestroy(old.graph);
+            cudaEventDestroy(old.ev_own[0]);
+            cudaEventDestroy(old.ev_own[1]);
             ctx->batch_graphs.erase(ctx->batch_graphs.begin());
         }
-        ctx->batch_graphs.push_back({key, exec});
+        ctx->batch_graphs.push_back(g);
+        G = &ctx->batch_graphs.back();
     }
-    AFM_CUDA(cudaGraphLaunch(exec, s), "cudaGraphLaunch");
+    if (ctx->profiling) {
+        // a fresh event pair per launch, read back by afm_profile_read
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        AFM_CUDA(take_event(ctx, &e0), "cudaEventCreate");
+        AFM_CUDA(take_event(ctx, &e1), "cudaEventCreate");
+        AFM_CUDA(cudaGraphExecEventRecordNodeSetEvent(G->exec, G->ev_node[0], e0), "event node");
+        AFM_CUDA(cudaGraphExecEventRecordNodeSetEvent(G->exec, G->ev_node[1], e1), "event node");
+        AFM_CUDA(cudaGraphLaunch(G->exec, s), "cudaGraphLaunch");
+        ctx->ev_pending.emplace_back(e0, e1);
+        return AFM_OK;
+    }
+    AFM_CUDA(cudaGraphExecEventRecordNodeSetEvent(G->exec, G->ev_node[0], G->ev_own[0]), "event node");
+    AFM_CUDA(cudaGraphExecEventRecordNodeSetEvent(G->exec, G->ev_node[1], G->ev_own[1]), "event node");
+    AFM_CUDA(cudaGraphLaunch(G->exec, s), "cudaGraphLaunch");
     return AFM_OK;
 }
 
@@ -1633,15 +1787,18 @@ static afm_status check_batch_polish(const afm_problem* prob, const afm_pso_cfg*
     return AFM_OK;
 }
 
-afm_status afm_invert_batch_polished_workspace_size(const afm_problem* prob, const afm_pso_cfg* cfg,
-                                                    int n_pix, int polish_k, int n_cand,
-                                                    int method, size_t* bytes) {
+afm_status afm_invert_batch_polished_workspace_size(const afm_problem* probs, int n_prob,
+                                                    const afm_pso_cfg* cfg, int n_run,
+                                                    int polish_k, int n_cand, int method,
+                                                    size_t* bytes) {
     g_err[0] = 0;
     if (!bytes) return fail(AFM_ERR_INVALID_ARG, "bytes is NULL");
-    afm_status st = check_batch_polish(prob, cfg, n_pix, polish_k, n_cand, method);
+    afm_status st = check_batch_polish(probs, cfg, n_run, polish_k, n_cand, method);
     if (st) return st;
-    if ((st = check_problem(prob))) return st;
-    *bytes = batch_polish_layout(*prob, *cfg, n_pix, polish_k, n_cand, method).total;
+    afm_problem eff;
+    if ((st = check_batch_probs(probs, n_prob, n_prob > 1 ? n_prob : 1, &eff))) return st;
+    *bytes = batch_polish_layout(eff, *cfg, n_run, polish_k, n_cand, method).total +
+             pix_layout(n_prob, eff.steps_per_cycle).total;
     return AFM_OK;
 }
 
@@ -1651,29 +1808,35 @@ static afm_status batch_polished_run(afm_ctx* ctx, const afm_problem* prob, cons
                                      int polish_steps, int n_cand, int method, char* ws,
                                      afm_result* results, cudaStream_t s);
 
-afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* prob, const float* U_cat,
-                                     const int64_t* off, int n_pix, uint32_t pixel0,
-                                     const afm_pso_cfg* cfg, int polish_k, int polish_steps,
-                                     int n_cand, int method, const afm_batch_select* select,
-                                     void* workspace, size_t workspace_bytes,
-                                     afm_result* results, int* particles_per_thread,
-                                     void* stream) {
+afm_status afm_invert_batch_polished(afm_ctx* ctx, const afm_problem* probs, int n_prob,
+                                     const float* U_cat, const int64_t* off, int n_pix,
+                                     uint32_t pixel0, const afm_pso_cfg* cfg, int polish_k,
+                                     int polish_steps, int n_cand, int method,
+                                     const afm_batch_select* select, void* workspace,
+                                     size_t workspace_bytes, afm_result* results,
+                                     int* particles_per_thread, void* stream) {
     AFM_TRACE("afm_invert_batch_polished");
     g_err[0] = 0;
     const int n_run = select ? select->n_run : n_pix;
-    afm_status st = check_batch_polish(prob, cfg, n_run, polish_k, n_cand, method);
+    afm_status st = check_batch_polish(probs, cfg, n_run, polish_k, n_cand, method);
     if (st) return st;
     if (polish_steps < 0) return fail(AFM_ERR_INVALID_ARG, "polish_steps < 0");
-    if ((st = check_problem(prob))) return st;
-    const BatchPolishLayout PL = batch_polish_layout(*prob, *cfg, n_run, polish_k, n_cand, method);
-    if (workspace_bytes < PL.total)
-        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, PL.total);
+    afm_problem eff;
+    if ((st = check_batch_probs(probs, n_prob, n_pix, &eff))) return st;
+    if (n_prob > 1 && method != AFM_POLISH_LM)
+        return fail(AFM_ERR_UNSUPPORTED,
+                    "per-pixel problems are polished by Levenberg-Marquardt (AFM_POLISH_LM) only");
+    const BatchPolishLayout PL = batch_polish_layout(eff, *cfg, n_run, polish_k, n_cand, method);
+    const size_t need = PL.total + pix_layout(n_prob, eff.steps_per_cycle).total;
+    if (workspace_bytes < need)
+        return fail(AFM_ERR_INVALID_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, need);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     BatchSetup B;
-    if ((st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, cfg, workspace, results,
-                          particles_per_thread, s, "afm_invert_batch_polished", &B, select)))
+    if ((st = batch_setup(ctx, probs, n_prob, U_cat, off, n_pix, pixel0, cfg, workspace, PL.total,
+                          results, particles_per_thread, s, "afm_invert_batch_polished", &B,
+                          select)))
         return st;
-    return batch_polished_run(ctx, prob, B, PL, U_cat, off, cfg, polish_k, polish_steps, n_cand,
+    return batch_polished_run(ctx, &eff, B, PL, U_cat, off, cfg, polish_k, polish_steps, n_cand,
                               method, static_cast<char*>(workspace), results, s);
 }
 
@@ -1696,7 +1859,7 @@ static afm_status batch_polished_run(afm_ctx* ctx, const afm_problem* prob, cons
     AFM_CUDA(afm::launch_topk_pix(a.pb_out, n_pix, cfg->P, D, Kc, xk, Sk, ik, s), "top-k kernel");
     for (int k = 0; k < polish_steps; ++k)
         if ((st = polish_step(ctx, B.Kf, method, U_cat, off, a.order, Kc, xk, Sk, Nt, J, PL.P,
-                              ws + PL.pol, s)))
+                              ws + PL.pol, s, a.pix)))
             return st;
     AFM_CUDA(afm::launch_pick_pix(n_pix, D, Kc, xk, Sk, ik, a.order, cfg->iters, results, s),
              "winner pick kernel");
@@ -1784,8 +1947,8 @@ afm_status afm_invert_image(afm_ctx* ctx, const afm_problem* prob, const float* 
     sel.pixels = coarse;
     sel.n_run = L.n_coarse;
     BatchSetup B;
-    if ((st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, &ic.coarse, bws, results, nullptr, s,
-                          "afm_invert_image", &B, &sel)))
+    if ((st = batch_setup(ctx, prob, 1, U_cat, off, n_pix, pixel0, &ic.coarse, bws, 0, results,
+                          nullptr, s, "afm_invert_image", &B, &sel)))
         return st;
     BatchPolishLayout PL = batch_polish_layout(*prob, ic.coarse, L.n_coarse, ic.coarse_polish_k,
                                                ic.n_cand, ic.method);
@@ -1803,8 +1966,8 @@ afm_status afm_invert_image(afm_ctx* ctx, const afm_problem* prob, const float* 
     sel.box_hi = bhi;
     sel.seeds = seeds;
     sel.n_seed = 4;
-    if ((st = batch_setup(ctx, prob, U_cat, off, n_pix, pixel0, &ic.fine, bws, results, nullptr, s,
-                          "afm_invert_image", &B, &sel)))
+    if ((st = batch_setup(ctx, prob, 1, U_cat, off, n_pix, pixel0, &ic.fine, bws, 0, results,
+                          nullptr, s, "afm_invert_image", &B, &sel)))
         return st;
     PL = batch_polish_layout(*prob, ic.fine, L.n_fine, ic.fine_polish_k, ic.n_cand, ic.method);
     return batch_polished_run(ctx, prob, B, PL, U_cat, off, &ic.fine, ic.fine_polish_k,

@@ -19,9 +19,36 @@ int batch_threads(int P, int kp) { return ((P + kp - 1) / kp + 31) / 32 * 32; }
 
 int batch_max_threads(int kp) { return kp == 1 ? 1024 : 512; }
 
-size_t batch_smem(int P, int D, int spc2) {
+size_t batch_smem(int P, int D, int spc2, bool pp) {
     const size_t tab = (size_t)((spc2 + 1 + 3) & ~3);
-    return sizeof(float) * (tab + 3 * (size_t)D * P);
+    const size_t kc = pp ? (size_t)batch_kc_words<true>() : 0;
+    return sizeof(float) * (kc + tab + 3 * (size_t)D * P);
+}
+
+// ---------------------------------------------------------------------------
+// Per-pixel drive tables (batches whose pixels differ in their problem): the
+// arithmetic of build_drive_table in FP64 from each pixel's constants, also
+// rounded to FP32.  One thread per (pixel, phase).
+// ---------------------------------------------------------------------------
+__global__ void pix_tables_kernel(const KConst<double>* __restrict__ kd, int n_pix, int spc2,
+                                  int ld, double* __restrict__ tab64, float* __restrict__ tab32) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pix = (int)(t / (spc2 + 1)), j = (int)(t % (spc2 + 1));
+    if (pix >= n_pix) return;
+    const int jj = j == spc2 ? 0 : j;
+    const double ph = 6.283185307179586476925 * (double)jj / (double)spc2 + kd[pix].drive_phase;
+    const double g = kd[pix].drive_amp * sin(ph);
+    tab64[(size_t)pix * ld + j] = g;
+    tab32[(size_t)pix * ld + j] = (float)g;
+}
+
+cudaError_t launch_pix_tables(const PixConst& pc, int n_pix, int spc2, cudaStream_t st) {
+    if (pc.kd == nullptr || pc.ld < spc2 + 1) return cudaErrorInvalidValue;
+    const long long total = (long long)n_pix * (spc2 + 1);
+    const int threads = 256;
+    pix_tables_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(
+        pc.kd, n_pix, spc2, pc.ld, const_cast<double*>(pc.tab64), const_cast<float*>(pc.tab32));
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -79,7 +106,7 @@ int batch_sort_max() { return SORT_MAX; }
 // The kernels of each force law are instantiated in kern_batch_<law>.cu (so
 // that they compile in parallel); this file only calls their entry points.
 #define AFM_BATCH_DECLARE(F)                                                                   \
-    template <> cudaError_t batch_occupancy_of<F>(int, int, int, int, int, int*);              \
+    template <> cudaError_t batch_occupancy_of<F>(int, int, int, int, int, bool, int*);        \
     template <> cudaError_t batch_launch_of<F>(const KConst<float>&, const PsoConst&,          \
                                                const BatchArgs&, int, int, cudaStream_t);
 AFM_BATCH_DECLARE(F_LINEAR)
@@ -103,9 +130,10 @@ static cudaError_t by_force(int force, F&& f) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t batch_occupancy(int m, int force, int kp, int P, int D, int spc2, int* blocks_per_sm) {
+cudaError_t batch_occupancy(int m, int force, int kp, int P, int D, int spc2, bool pp,
+                            int* blocks_per_sm) {
     return by_force(force, [&](auto Fc) {
-        return batch_occupancy_of<decltype(Fc)::value>(m, kp, P, D, spc2, blocks_per_sm);
+        return batch_occupancy_of<decltype(Fc)::value>(m, kp, P, D, spc2, pp, blocks_per_sm);
     });
 }
 

@@ -24,18 +24,39 @@ __device__ __forceinline__ unsigned long long warp_min(unsigned long long k) {
     return k;
 }
 
+// The problem constants of the pixel being inverted: the launch's (shared by
+// every pixel), or the per-pixel copy staged in shared memory.
+template <bool PP>
+__device__ __forceinline__ const KConst<float>& pick_k(const KConst<float>& K,
+                                                       const KConst<float>* sK) {
+    if constexpr (PP)
+        return *sK;
+    else
+        return K;
+}
+
 }  // namespace batch_detail
+
+// 32-bit words of dynamic shared memory before the drive table (per-pixel
+// constants), a multiple of 4 so that the arrays after it stay 16-byte aligned
+template <bool PP>
+__host__ __device__ constexpr int batch_kc_words() {
+    return PP ? (int)((sizeof(KConst<float>) + 15) / 16 * 4) : 0;
+}
 
 // ---------------------------------------------------------------------------
 // Persistent swarm kernel.
 // ---------------------------------------------------------------------------
-template <int M, int FORCE, int KP>
+// PP: the pixels' problems differ (a.pix): each pixel's constants and drive
+// table are staged into shared memory when a block takes the pixel.
+template <int M, int FORCE, int KP, bool PP>
 __global__ void __launch_bounds__(KP == 1 ? 1024 : 512) batch_kernel(const KConst<float> K, const PsoConst pc,
                                                      const BatchArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int P = pc.P, D = pc.D;
-    float* tab = sm;
-    float* sx = sm + ((K.spc2 + 1 + 3) & ~3);
+    KConst<float>* sK = reinterpret_cast<KConst<float>*>(sm);
+    float* tab = sm + batch_kc_words<PP>();
+    float* sx = tab + ((K.spc2 + 1 + 3) & ~3);
     float* sv = sx + D * P;
     float* spb = sv + D * P;
     __shared__ unsigned long long wkey[32];
@@ -43,7 +64,8 @@ __global__ void __launch_bounds__(KP == 1 ? 1024 : 512) batch_kernel(const KCons
     __shared__ int s_slot, s_bad;
     __shared__ float s_blo[AFM_MAXD], s_bspan[AFM_MAXD];   // optional per-slot box
     const bool boxed = a.box_lo != nullptr;
-    build_drive_table(K, tab);
+    if (!PP) build_drive_table(K, tab);
+    const KConst<float>& KK = batch_detail::pick_k<PP>(K, sK);
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = T >> 5;
     for (;;) {
@@ -63,6 +85,14 @@ __global__ void __launch_bounds__(KP == 1 ? 1024 : 512) batch_kernel(const KCons
         const int slot = s_slot;
         if (slot >= a.n_pix) return;
         const int pix = a.order != nullptr ? a.order[slot] : slot;
+        if constexpr (PP) {   // this pixel's constants and drive table
+            const unsigned* src = reinterpret_cast<const unsigned*>(a.pix.kf + pix);
+            unsigned* dst = reinterpret_cast<unsigned*>(sK);
+            for (int w = tid; w < (int)(sizeof(KConst<float>) / 4); w += blockDim.x) dst[w] = src[w];
+            const float* t32 = a.pix.tab32 + (size_t)pix * a.pix.ld;
+            for (int j = tid; j <= K.spc2; j += blockDim.x) tab[j] = t32[j];
+            __syncthreads();
+        }
         const int64_t o = a.off[pix];
         const int n = (int)(a.off[pix + 1] - o);
         const float* U = a.U + o;
@@ -126,14 +156,14 @@ __global__ void __launch_bounds__(KP == 1 ? 1024 : 512) batch_kernel(const KCons
                 float x[AFM_MAXD];
                 for (int d = 0; d < D; ++d)
                     x[d] = boxed ? fmaf(sx[d * P + p], s_bspan[d], s_blo[d]) : sx[d * P + p];
-                c[k] = make_coef<float, float>(K, x);
+                c[k] = make_coef<float, float>(KK, x);
             }
             float S[KP];
             // pairs of particles per paired FP32 instruction where the law allows
             if constexpr (KP % 2 == 0 && M <= 4 && x2::Supported<FORCE>::value)
-                integrate_multi_x2<M, FORCE, KP>(K, c, tab, U, n, S);
+                integrate_multi_x2<M, FORCE, KP>(KK, c, tab, U, n, S);
             else
-                integrate_multi<M, FORCE, KP>(K, c, tab, U, n, S);
+                integrate_multi<M, FORCE, KP>(KK, c, tab, U, n, S);
             unsigned long long key = ~0ull;
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
@@ -213,11 +243,20 @@ struct BatchOps {
         return cudaErrorInvalidValue;
     }
 
-    static cudaError_t occupancy(int m, int kp, int P, int D, int spc2, int* blocks) {
-        const int threads = batch_threads(P, kp);
-        const size_t smem = batch_smem(P, D, spc2);
+    template <typename F>
+    static cudaError_t by_mkp(int m, int kp, bool pp, F&& f) {
         return by_mk(m, kp, [&](auto Mc, auto Kc) -> cudaError_t {
-            auto kern = batch_kernel<decltype(Mc)::value, FORCE, decltype(Kc)::value>;
+            if (pp) return f(Mc, Kc, std::true_type{});
+            return f(Mc, Kc, std::false_type{});
+        });
+    }
+
+    static cudaError_t occupancy(int m, int kp, int P, int D, int spc2, bool pp, int* blocks) {
+        const int threads = batch_threads(P, kp);
+        const size_t smem = batch_smem(P, D, spc2, pp);
+        return by_mkp(m, kp, pp, [&](auto Mc, auto Kc, auto Pc) -> cudaError_t {
+            auto kern = batch_kernel<decltype(Mc)::value, FORCE, decltype(Kc)::value,
+                                     decltype(Pc)::value>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
@@ -228,9 +267,11 @@ struct BatchOps {
     static cudaError_t launch(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a, int kp,
                               int grid, cudaStream_t st) {
         const int threads = batch_threads(pc.P, kp);
-        const size_t smem = batch_smem(pc.P, pc.D, K.spc2);
-        return by_mk(K.m, kp, [&](auto Mc, auto Kc) -> cudaError_t {
-            auto kern = batch_kernel<decltype(Mc)::value, FORCE, decltype(Kc)::value>;
+        const bool pp = a.pix.kf != nullptr;
+        const size_t smem = batch_smem(pc.P, pc.D, K.spc2, pp);
+        return by_mkp(K.m, kp, pp, [&](auto Mc, auto Kc, auto Pc) -> cudaError_t {
+            auto kern = batch_kernel<decltype(Mc)::value, FORCE, decltype(Kc)::value,
+                                     decltype(Pc)::value>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
@@ -245,7 +286,7 @@ struct BatchOps {
 // its kern_batch_<law>.cu so that kern_batch.cu dispatches without
 // instantiating any kernel.
 template <int FORCE>
-cudaError_t batch_occupancy_of(int m, int kp, int P, int D, int spc2, int* blocks);
+cudaError_t batch_occupancy_of(int m, int kp, int P, int D, int spc2, bool pp, int* blocks);
 template <int FORCE>
 cudaError_t batch_launch_of(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a, int kp,
                             int grid, cudaStream_t st);

@@ -4,8 +4,9 @@
 
 namespace afm {
 template <>
-cudaError_t batch_occupancy_of<F_DMT_KV>(int m, int kp, int P, int D, int spc2, int* blocks) {
-    return BatchOps<F_DMT_KV>::occupancy(m, kp, P, D, spc2, blocks);
+cudaError_t batch_occupancy_of<F_DMT_KV>(int m, int kp, int P, int D, int spc2, bool pp,
+                                  int* blocks) {
+    return BatchOps<F_DMT_KV>::occupancy(m, kp, P, D, spc2, pp, blocks);
 }
 template <>
 cudaError_t batch_launch_of<F_DMT_KV>(const KConst<float>& K, const PsoConst& pc, const BatchArgs& a,

@@ -92,18 +92,33 @@ __global__ void __launch_bounds__(256) topk_pix_kernel(const float* __restrict__
 // Forward solve + misfit (the arithmetic of fwd_kernel) of candidates that
 // belong to different pixels: candidate p of slot p / per_slot against that
 // pixel's record.
-template <int M, int FORCE>
-__global__ void fwd_ragged_kernel(const KConst<float> K, const float* __restrict__ x, int Ptot,
+// PP: each candidate's pixel has its own constants and drive table (pix),
+// read from global memory.
+template <bool PP>
+__device__ __forceinline__ const KConst<float>& ragged_k(const KConst<float>& K0, const PixConst& pc,
+                                                         int pix) {
+    if constexpr (PP)
+        return pc.kf[pix];
+    else
+        return K0;
+}
+
+template <int M, int FORCE, bool PP>
+__global__ void fwd_ragged_kernel(const KConst<float> K0, const float* __restrict__ x, int Ptot,
                                   const float* __restrict__ U_cat, const int64_t* __restrict__ off,
                                   const int* __restrict__ order, int per_slot,
-                                  float* __restrict__ S) {
-    extern __shared__ __align__(16) float tab[];
-    build_drive_table(K, tab);
-    __syncthreads();
+                                  float* __restrict__ S, const PixConst pixc) {
+    extern __shared__ __align__(16) float tabs[];
+    if constexpr (!PP) {
+        build_drive_table(K0, tabs);
+        __syncthreads();
+    }
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= Ptot) return;
     const int slot = p / per_slot;
     const int pix = order != nullptr ? order[slot] : slot;
+    const KConst<float>& K = ragged_k<PP>(K0, pixc, pix);
+    const float* tab = PP ? pixc.tab32 + (size_t)pix * pixc.ld : tabs;
     const int64_t o = off[pix];
     const int n = (int)(off[pix + 1] - o);
     float xd[AFM_MAXD];
@@ -117,19 +132,23 @@ __global__ void fwd_ragged_kernel(const KConst<float> K, const float* __restrict
 // The same with candidates 2t and 2t + 1 on thread t in paired FP32
 // instructions (afm_f32x2.cuh; bit-identical): with an even number of
 // candidates per slot both belong to the same pixel and record.
-template <int M, int FORCE>
-__global__ void fwd_ragged_x2_kernel(const KConst<float> K, const float* __restrict__ x,
+template <int M, int FORCE, bool PP>
+__global__ void fwd_ragged_x2_kernel(const KConst<float> K0, const float* __restrict__ x,
                                      int Ptot, const float* __restrict__ U_cat,
                                      const int64_t* __restrict__ off,
                                      const int* __restrict__ order, int per_slot,
-                                     float* __restrict__ S) {
-    extern __shared__ __align__(16) float tab[];
-    build_drive_table(K, tab);
-    __syncthreads();
+                                     float* __restrict__ S, const PixConst pixc) {
+    extern __shared__ __align__(16) float tabs[];
+    if constexpr (!PP) {
+        build_drive_table(K0, tabs);
+        __syncthreads();
+    }
     const int p = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (p >= Ptot) return;
     const int slot = p / per_slot;
     const int pix = order != nullptr ? order[slot] : slot;
+    const KConst<float>& K = ragged_k<PP>(K0, pixc, pix);
+    const float* tab = PP ? pixc.tab32 + (size_t)pix * pixc.ld : tabs;
     const int64_t o = off[pix];
     const int n = (int)(off[pix + 1] - o);
     float xa[AFM_MAXD], xb[AFM_MAXD];
@@ -182,36 +201,46 @@ cudaError_t launch_topk_pix(const float* pb_all, int n_pix, int P, int D, int Kc
 
 cudaError_t launch_forward_ragged(const KConst<float>& K, const float* x, int Ptot, const float* U_cat,
                                   const int64_t* off, const int* order, int per_slot, float* S,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const PixConst& pix) {
     const int threads = Ptot <= 152 * 32 * 4 ? 32 : 128;
     const int blocks = (Ptot + threads - 1) / threads;
-    const size_t smem = sizeof(float) * (size_t)(K.spc2 + 1);
+    const bool pp = pix.kf != nullptr;
+    const size_t smem = pp ? 0 : sizeof(float) * (size_t)(K.spc2 + 1);
+    auto by_pp = [&](auto&& f) -> cudaError_t {
+        return pp ? f(std::true_type{}) : f(std::false_type{});
+    };
     // pairs of candidates for large DMT batches (the same rule as
     // afm_forward_batch's paired kernel)
     if (K.force == F_DMT && (K.m == 1 || K.m == 3) && per_slot % 2 == 0 && Ptot >= 65536) {
         const int pairs = Ptot / 2;
         auto go = [&](auto Mc) -> cudaError_t {
-            auto kern = fwd_ragged_x2_kernel<decltype(Mc)::value, F_DMT>;
-            if (smem > 48 * 1024) {
-                cudaError_t e = cudaFuncSetAttribute(
-                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e != cudaSuccess) return e;
-            }
-            kern<<<(pairs + 127) / 128, 128, smem, st>>>(K, x, Ptot, U_cat, off, order, per_slot, S);
-            return cudaGetLastError();
+            return by_pp([&](auto Pc) -> cudaError_t {
+                auto kern = fwd_ragged_x2_kernel<decltype(Mc)::value, F_DMT, decltype(Pc)::value>;
+                if (smem > 48 * 1024) {
+                    cudaError_t e = cudaFuncSetAttribute(
+                        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (e != cudaSuccess) return e;
+                }
+                kern<<<(pairs + 127) / 128, 128, smem, st>>>(K, x, Ptot, U_cat, off, order,
+                                                              per_slot, S, pix);
+                return cudaGetLastError();
+            });
         };
         if (K.m == 1) return go(std::integral_constant<int, 1>{});
         return go(std::integral_constant<int, 3>{});
     }
     return dispatch_mf(K.m, K.force, [&](auto Mc, auto Fc) -> cudaError_t {
-        auto kern = fwd_ragged_kernel<decltype(Mc)::value, decltype(Fc)::value>;
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        kern<<<blocks, threads, smem, st>>>(K, x, Ptot, U_cat, off, order, per_slot, S);
-        return cudaGetLastError();
+        return by_pp([&](auto Pc) -> cudaError_t {
+            auto kern = fwd_ragged_kernel<decltype(Mc)::value, decltype(Fc)::value,
+                                          decltype(Pc)::value>;
+            if (smem > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(
+                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            kern<<<blocks, threads, smem, st>>>(K, x, Ptot, U_cat, off, order, per_slot, S, pix);
+            return cudaGetLastError();
+        });
     });
 }
 

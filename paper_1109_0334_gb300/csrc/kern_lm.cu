@@ -48,30 +48,42 @@ constexpr int kFold = 32;   // steps summed in FP32 before folding into FP64 tot
 // Sensitivity pass of one particle per thread: S (as the forward kernel),
 // H [P][D][D] and b [P][D] in FP64.  Ragged form as the adjoint: off !=
 // nullptr gives particle p the record of pixel order[p / per_slot].
-template <int M, int FORCE, int ND>
-__global__ void __launch_bounds__(kThreads) sens_kernel(const KConst<float> K,
+// PP (ragged form only): each particle's pixel has its own constants and
+// drive table (pix), read from global memory.
+template <int M, int FORCE, int ND, bool PP>
+__global__ void __launch_bounds__(kThreads) sens_kernel(const KConst<float> K0,
                                                         const float* __restrict__ x, int P,
                                                         const float* __restrict__ U,
                                                         const int64_t* __restrict__ off,
                                                         const int* __restrict__ order,
                                                         int per_slot, float* __restrict__ S_out,
                                                         double* __restrict__ H_out,
-                                                        double* __restrict__ b_out) {
-    extern __shared__ __align__(16) float tab[];
+                                                        double* __restrict__ b_out,
+                                                        const PixConst pixc) {
+    extern __shared__ __align__(16) float tabs[];
     __shared__ double accH[ND * (ND + 1) / 2][kThreads], accb[ND][kThreads];
-    build_drive_table(K, tab);
-    __syncthreads();
+    if constexpr (!PP) {
+        build_drive_table(K0, tabs);
+        __syncthreads();
+    }
     const int tid = threadIdx.x;
     const int p = blockIdx.x * blockDim.x + tid;
     if (p >= P) return;
-    const int D = K.D;
-    int n = K.n_steps;
+    int n = K0.n_steps, pix = 0;
     if (off != nullptr) {
         const int slot = p / per_slot;
-        const int pix = order != nullptr ? order[slot] : slot;
+        pix = order != nullptr ? order[slot] : slot;
         U += off[pix];
         n = (int)(off[pix + 1] - off[pix]);
     }
+    const KConst<float>* Kp = &K0;
+    const float* tab = tabs;
+    if constexpr (PP) {
+        Kp = pixc.kf + pix;
+        tab = pixc.tab32 + (size_t)pix * pixc.ld;
+    }
+    const KConst<float>& K = *Kp;
+    const int D = K.D;
     float xd[AFM_MAXD];
     for (int d = 0; d < AFM_MAXD; ++d) xd[d] = d < D ? x[(size_t)d * P + p] : 0.f;
     const Coef<float> c = make_coef<float, float>(K, xd);
@@ -257,22 +269,28 @@ cudaError_t launch_lm_select_hb(int D, int K, int J, float* x, float* S, double*
 
 cudaError_t launch_sens(const KConst<float>& K, const float* x, int P, const float* U, float* S,
                         double* H, double* b, cudaStream_t st, const int64_t* off, const int* order,
-                        int per_slot) {
-    if (sens_modes_supported(K.m, K.force, P, K.D))
+                        int per_slot, const PixConst& pix) {
+    const bool pp = pix.kf != nullptr;
+    if (pp && off == nullptr) return cudaErrorInvalidValue;
+    if (!pp && sens_modes_supported(K.m, K.force, P, K.D))
         return launch_sens_modes(K, x, P, U, S, H, b, st, off, order, per_slot);
-    if (sens_lanes_preferred(P, K.D))
+    if (!pp && sens_lanes_preferred(P, K.D))
         return launch_sens_lanes(K, x, P, U, S, H, b, st, off, order, per_slot);
     const int blocks = (P + kThreads - 1) / kThreads;
-    const size_t smem = sizeof(float) * (size_t)(K.spc2 + 1);
+    const size_t smem = pp ? 0 : sizeof(float) * (size_t)(K.spc2 + 1);
     return dispatch_mfd(K.m, K.force, K.D, [&](auto Mc, auto Fc, auto Dc) -> cudaError_t {
-        auto kern = sens_kernel<decltype(Mc)::value, decltype(Fc)::value, decltype(Dc)::value>;
-        if (smem > 24 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        kern<<<blocks, kThreads, smem, st>>>(K, x, P, U, off, order, per_slot, S, H, b);
-        return cudaGetLastError();
+        auto go = [&](auto Pc) -> cudaError_t {
+            auto kern = sens_kernel<decltype(Mc)::value, decltype(Fc)::value, decltype(Dc)::value,
+                                    decltype(Pc)::value>;
+            if (smem > 24 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(
+                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            kern<<<blocks, kThreads, smem, st>>>(K, x, P, U, off, order, per_slot, S, H, b, pix);
+            return cudaGetLastError();
+        };
+        return pp ? go(std::true_type{}) : go(std::false_type{});
     });
 }
 

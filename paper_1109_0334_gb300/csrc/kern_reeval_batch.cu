@@ -36,6 +36,24 @@ __device__ __forceinline__ int slot_segments(const ReevalBatch& R, int n) {
     return B <= R.maxB ? B : 0;
 }
 
+// The constants and FP64 drive table of pixel pix: the launch's, or its own
+// (PP: a batch whose pixels differ in their problem).
+template <bool PP, typename T>
+__device__ __forceinline__ const KConst<T>& pix_k(const KConst<T>& K, const KConst<T>* per, int pix) {
+    if constexpr (PP)
+        return per[pix];
+    else
+        return K;
+}
+
+template <bool PP>
+__device__ __forceinline__ const double* pix_tab64(const ReevalBatch& R, const BatchArgs& a, int pix) {
+    if constexpr (PP)
+        return a.pix.tab64 + (size_t)pix * a.pix.ld;
+    else
+        return R.tab;
+}
+
 __device__ __forceinline__ Coef<double> slot_coef(const ReevalBatch& R, int i) {
     Coef<double> c;
     c.c0 = R.coef[4 * (size_t)i];
@@ -47,17 +65,22 @@ __device__ __forceinline__ Coef<double> slot_coef(const ReevalBatch& R, int i) {
 
 }  // namespace
 
-template <int M, int FORCE>
-__global__ void __launch_bounds__(128) rb_guess_kernel(const KConst<float> Kf,
-                                                       const KConst<double> Kd,
+template <int M, int FORCE, bool PP>
+__global__ void __launch_bounds__(128) rb_guess_kernel(const KConst<float> Kf0,
+                                                       const KConst<double> Kd0,
                                                        const ReevalBatch R, const BatchArgs a) {
-    extern __shared__ __align__(16) float tabf[];
-    build_drive_table(Kf, tabf);
-    if (blockIdx.x == 0) build_drive_table(Kd, R.tab);
-    __syncthreads();
+    extern __shared__ __align__(16) float tabs[];
+    if constexpr (!PP) {
+        build_drive_table(Kf0, tabs);
+        if (blockIdx.x == 0) build_drive_table(Kd0, R.tab);
+        __syncthreads();
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_pix) return;
     const int pix = slot_pixel(a, i);
+    const KConst<float>& Kf = pix_k<PP>(Kf0, a.pix.kf, pix);
+    const KConst<double>& Kd = pix_k<PP>(Kd0, a.pix.kd, pix);
+    const float* tabf = PP ? a.pix.tab32 + (size_t)pix * a.pix.ld : tabs;
     const int n = slot_steps(a, pix);
     const float* U = a.U + a.off[pix];
     double xd[AFM_MAXD];
@@ -103,8 +126,8 @@ __global__ void __launch_bounds__(128) rb_guess_kernel(const KConst<float> Kf,
     }
 }
 
-template <int M, int FORCE, bool TANGENT>
-__global__ void __launch_bounds__(32) rb_pass_kernel(const KConst<double> K, const ReevalBatch R,
+template <int M, int FORCE, bool TANGENT, bool PP>
+__global__ void __launch_bounds__(32) rb_pass_kernel(const KConst<double> K0, const ReevalBatch R,
                                                      const BatchArgs a) {
     __shared__ float rec[TANGENT ? AFM_SEG * kRec * 32 : 1];
     constexpr int S2 = 2 * M;
@@ -115,6 +138,8 @@ __global__ void __launch_bounds__(32) rb_pass_kernel(const KConst<double> K, con
     const int pix = slot_pixel(a, i);
     const int n = slot_steps(a, pix);
     if (b >= slot_segments(R, n)) return;
+    const KConst<double>& K = pix_k<PP>(K0, a.pix.kd, pix);
+    const double* tab = pix_tab64<PP>(R, a, pix);
     const float* U = a.U + a.off[pix];
     const Coef<double> c = slot_coef(R, i);
     Coef<float> cf;
@@ -134,7 +159,7 @@ __global__ void __launch_bounds__(32) rb_pass_kernel(const KConst<double> K, con
     int j = (int)((2ll * n0) % K.spc2);
     double S = 0.0;
     for (int s = n0; s < n1; ++s) {
-        const double g0 = R.tab[j], gh = R.tab[j + 1], g1 = R.tab[j + 2];
+        const double g0 = tab[j], gh = tab[j + 1], g1 = tab[j + 2];
         j += 2;
         if (j >= K.spc2) j = 0;
         step64<M, FORCE, TANGENT>(K, c, cf, q, v, g0, gh, g1, rec + lane + (s - n0) * kRec * 32);
@@ -228,13 +253,14 @@ __global__ void __launch_bounds__(128) rb_correct_kernel(const ReevalBatch R, co
 
 // Per slot: S_f64 = sum of the shares in order, the join check (sequential
 // FP64 fallback), and the result record.
-template <int M, int FORCE>
-__global__ void __launch_bounds__(128) rb_final_kernel(const KConst<double> K, const ReevalBatch R,
+template <int M, int FORCE, bool PP>
+__global__ void __launch_bounds__(128) rb_final_kernel(const KConst<double> K0, const ReevalBatch R,
                                                        const BatchArgs a) {
     constexpr int S2 = 2 * M;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n_pix) return;
     const int pix = slot_pixel(a, i);
+    const KConst<double>& K = pix_k<PP>(K0, a.pix.kd, pix);
     const int n = slot_steps(a, pix);
     const int B = slot_segments(R, n);
     const size_t g0 = (size_t)i * R.maxB;
@@ -253,8 +279,8 @@ __global__ void __launch_bounds__(128) rb_final_kernel(const KConst<double> K, c
     }
     int segs = B;
     if (!(defect <= kDefectTol) || !isfinite(S64)) {
-        S64 = integrate<double, M, FORCE, float>(K, slot_coef(R, i), R.tab, a.U + a.off[pix],
-                                                 nullptr, 0, 0, n);
+        S64 = integrate<double, M, FORCE, float>(K, slot_coef(R, i), pix_tab64<PP>(R, a, pix),
+                                                 a.U + a.off[pix], nullptr, 0, 0, n);
         segs = 0;
     }
     afm_result* r = a.res + pix;
@@ -309,25 +335,30 @@ void reeval_batch_carve(void* base, int m, int n_steps, int spc, int n_pix, Reev
 cudaError_t launch_reeval_batch(const KConst<float>& Kf, const KConst<double>& Kd,
                                 const ReevalBatch& R, const BatchArgs& a, cudaStream_t st) {
     if (R.maxB != reeval_segments(Kd.n_steps) || Kd.np > 0) return cudaErrorInvalidValue;
+    const bool pp = a.pix.kf != nullptr;
     return dispatch_m13(Kd.m, Kd.force, [&](auto Mc, auto Fc) -> cudaError_t {
         constexpr int M = decltype(Mc)::value, FORCE = decltype(Fc)::value;
-        const size_t smem = sizeof(float) * (size_t)(Kf.spc2 + 1);
-        rb_guess_kernel<M, FORCE><<<(a.n_pix + 127) / 128, 128, smem, st>>>(Kf, Kd, R, a);
-        cudaError_t e = cudaGetLastError();
-        const long long segs = (long long)a.n_pix * R.maxB;
-        const int grid = (int)((segs + 31) / 32);
-        const int cgrid = (a.n_pix * 32 + 127) / 128;
-        for (int k = 0; e == cudaSuccess && k < kSweeps; ++k) {
-            rb_pass_kernel<M, FORCE, true><<<grid, 32, 0, st>>>(Kd, R, a);
-            if ((e = cudaGetLastError()) != cudaSuccess) break;
-            rb_correct_kernel<M><<<cgrid, 128, 0, st>>>(R, a);
-            e = cudaGetLastError();
-        }
-        if (e != cudaSuccess) return e;
-        rb_pass_kernel<M, FORCE, false><<<grid, 32, 0, st>>>(Kd, R, a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        rb_final_kernel<M, FORCE><<<(a.n_pix + 127) / 128, 128, 0, st>>>(Kd, R, a);
-        return cudaGetLastError();
+        auto run = [&](auto Pc) -> cudaError_t {
+            constexpr bool PP = decltype(Pc)::value;
+            const size_t smem = PP ? 0 : sizeof(float) * (size_t)(Kf.spc2 + 1);
+            rb_guess_kernel<M, FORCE, PP><<<(a.n_pix + 127) / 128, 128, smem, st>>>(Kf, Kd, R, a);
+            cudaError_t e = cudaGetLastError();
+            const long long segs = (long long)a.n_pix * R.maxB;
+            const int grid = (int)((segs + 31) / 32);
+            const int cgrid = (a.n_pix * 32 + 127) / 128;
+            for (int k = 0; e == cudaSuccess && k < kSweeps; ++k) {
+                rb_pass_kernel<M, FORCE, true, PP><<<grid, 32, 0, st>>>(Kd, R, a);
+                if ((e = cudaGetLastError()) != cudaSuccess) break;
+                rb_correct_kernel<M><<<cgrid, 128, 0, st>>>(R, a);
+                e = cudaGetLastError();
+            }
+            if (e != cudaSuccess) return e;
+            rb_pass_kernel<M, FORCE, false, PP><<<grid, 32, 0, st>>>(Kd, R, a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            rb_final_kernel<M, FORCE, PP><<<(a.n_pix + 127) / 128, 128, 0, st>>>(Kd, R, a);
+            return cudaGetLastError();
+        };
+        return pp ? run(std::true_type{}) : run(std::false_type{});
     });
 }
 

@@ -153,6 +153,20 @@ def n_steps(w: dict) -> int:
     return int(cyc) * int(w["spc"])
 
 
+def c3_layout(spec: dict, n_pix: int | None = None, cycles_div: int = 1):
+    """Seeded per-pixel inputs of the 4096-pixel batch: record lengths in
+    cycles (uniform integers in the workload's cycle range, divided by
+    cycles_div, at least 1) and truths x* [D][n_pix] uniform in [0.1, 0.9]
+    (the interior of the normalised cube).  Pixel i's record is its truth's
+    deflection over cycles[i] * spc steps plus noise keyed by pixel i."""
+    n_pix = spec["n_pix"] if n_pix is None else n_pix
+    lo, hi = spec["cycles"]
+    rng = np.random.default_rng(spec["seed"])
+    cyc = np.maximum(rng.integers(lo, hi + 1, size=n_pix) // cycles_div, 1)
+    xt = rng.uniform(0.1, 0.9, size=(len(spec["free"]), n_pix))
+    return cyc, xt
+
+
 def sample_x(D: int, P: int, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
     """Seeded uniform swarm coordinates, shape [D][P], float32-exact."""
     rng = np.random.default_rng(seed)

@@ -57,14 +57,48 @@ def c4_invert():
                 oracle_seconds=time.time() - t, threads=O.get_threads())
 
 
+def c3_subset(n_sub: int = 32):
+    """The oracle's optimum of each of the first n_sub pixels of the
+    4096-pixel batch (their seeded truths, lengths and noise, records made by
+    the oracle): its own swarm of the batch configuration (256 particles x
+    60 updates, Philox pixel word = pixel index), then 12 Levenberg-Marquardt
+    steps from that winner and from the seeded truth (an input of the
+    workload); the lowest misfit of the three is the stored optimum."""
+    spec = W.get("c3")
+    cyc, xt = W.c3_layout(spec)
+    pm = O.make_pmap(spec)
+    t = time.time()
+    pixels = []
+    for i in range(n_sub):
+        sp = dict(spec, cycles=int(cyc[i]))
+        c = O.make_case(sp)
+        n = int(cyc[i]) * spec["spc"]
+        U = O.record(c, pm, xt[:, i], n, spec["record_sub"], spec["sigma"], spec["seed"], i)
+        U_m = (U / 1e-9).astype(np.float32).astype(np.float64) * 1e-9
+        x, S, _ = O.invert(c, pm, U_m, spec["P"], spec["iters"], spec["w"], spec["c1"],
+                           spec["c2"], spec["seed"], i)
+        starts = np.array([np.asarray(x, dtype=np.float64), xt[:, i]]).T.copy()
+        xo, So = O.lm_polish(c, pm, U_m, starts, steps=12)
+        cands = [(float(S), np.asarray(x, dtype=np.float64))] + \
+            [(float(So[k]), xo[:, k]) for k in range(2)]
+        S_opt, x_opt = min(cands, key=lambda t: t[0])
+        pixels.append(dict(pixel=i, cycles=int(cyc[i]), x=[float(v) for v in x_opt],
+                           S_m2=S_opt, x_pso=[float(v) for v in x], S_pso_m2=float(S),
+                           sumU2_m2=float(np.sum(U_m ** 2)),
+                           truth_x=[float(v) for v in xt[:, i]]))
+    return dict(workload="c3", pixels=pixels, oracle_seconds=time.time() - t,
+                threads=O.get_threads())
+
+
 if __name__ == "__main__":
     O.build()
     O.set_threads(os.cpu_count() or 1)
-    which = sys.argv[1:] or ["c2", "c4"]
-    for name, fn in (("c2", c2_invert), ("c4", c4_invert)):
+    which = sys.argv[1:] or ["c2", "c4", "c3"]
+    for name, fn in (("c2", c2_invert), ("c4", c4_invert), ("c3", c3_subset)):
         if name not in which:
             continue
         out = fn()
-        with open(os.path.join(HERE, f"{name}_invert.json"), "w") as f:
+        fname = "c3_subset_optima.json" if name == "c3" else f"{name}_invert.json"
+        with open(os.path.join(HERE, fname), "w") as f:
             json.dump(out, f, indent=1)
         print(json.dumps({k: v for k, v in out.items() if k != "hist_m2"}))

@@ -107,3 +107,30 @@ def test_status_strings(libafm):
     assert L.afm_status_string(0) == b"AFM_OK"
     assert L.afm_status_string(3) == b"AFM_ERR_NONFINITE"
     assert L.afm_version() >= 100
+
+
+def test_batch_problem_array_validation(libafm):
+    """One problem for every pixel, or one per pixel: the workspace grows by
+    the per-pixel constants; other counts and problems that differ in more
+    than the cantilever, drive and set-point are rejected."""
+    from paper_1109_0334_gb300 import workloads as W
+    spec = W.get("c3", P=64, iters=2)
+    p0 = libafm.make_problem(spec, n_steps=2560)
+    p1 = libafm.make_problem(dict(spec, Zc=14e-9, A0=18e-9, f1_hz=310e3), n_steps=2048)
+    n1 = libafm.invert_batch_workspace_size(p0, 2)
+    n2 = libafm.invert_batch_workspace_size([p0, p1], 2)
+    assert n2 > n1 and n2 % 256 == 0
+    with pytest.raises(libafm.AfmError) as ei:
+        libafm.invert_batch_workspace_size([p0, p1], 3)
+    assert ei.value.status == libafm.ERR_INVALID_ARG
+    bad = libafm.make_problem(dict(spec, spc=128), n_steps=2048)
+    with pytest.raises(libafm.AfmError) as ei:
+        libafm.invert_batch_workspace_size([p0, bad], 2)
+    assert ei.value.status == libafm.ERR_INVALID_ARG
+    assert b"differs from problem 0" in libafm.lib().afm_last_error()
+    bad = libafm.make_problem(spec, n_steps=2048)
+    bad.hi[2] = 40e-9
+    with pytest.raises(libafm.AfmError):
+        libafm.invert_batch_workspace_size([p0, bad], 2)
+    # the largest n_steps sizes the FP64 re-evaluation
+    assert libafm.invert_batch_workspace_size([p1, p0], 2) == n2

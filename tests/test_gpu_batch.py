@@ -89,7 +89,7 @@ def test_batch_oracle_parity_and_autotune(orc, afm):
         D = pm.D
         err, n_id, S_g, _ = identifiable_check(orc, sp, U_m, x_o, S_o, r["x"][:D])
         assert err <= 0.005 and n_id == 1
-        assert_determined(orc, sp, U_m, x_o, r["x"][:D], 1, ["E* sqrt(R)"])
+        assert_determined(orc, sp, U_m, x_o, r["x"][:D], 1, [])
         assert S_g <= S_o * (1 + 1e-4)
         assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2
         assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2

@@ -129,6 +129,6 @@ def test_invert_polished_lm_reaches_the_oracle_optimum(orc, afm):
                                                 r["x"][:pm.D])
     assert r["status"] == 0
     assert n_id == 2 and err <= 0.005, (err, widths)
-    assert_determined(orc, spec, U_m, np.array(gold["x"]), r["x"][:pm.D], 2, ["E* sqrt(R)", "a0"])
+    assert_determined(orc, spec, U_m, np.array(gold["x"]), r["x"][:pm.D], 2, ["E* sqrt(R)"])
     assert S_g - gold["S_m2"] <= spec["sigma"] ** 2
     assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2

@@ -67,7 +67,7 @@ def test_points_inversion(orc, afm):
     err, n_id, S_g, widths = identifiable_check(orc, spec, U_m, x_o, S_o, r["x"][:pm.D])
     assert r["status"] == 0 and n_id == 1
     assert err <= 0.005, (err, widths)
-    assert_determined(orc, spec, U_m, x_o, r["x"][:pm.D], 1, ["E* sqrt(R)"])
+    assert_determined(orc, spec, U_m, x_o, r["x"][:pm.D], 1, [])
     assert S_g <= S_o * (1 + 1e-4)
     assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2
     assert abs(r["S_f64"] - S_g / NM ** 2) <= 1e-9 * S_g / NM ** 2

@@ -64,7 +64,7 @@ def test_invert_polished_matches_oracle(orc, afm):
     D = pm.D
     err, n_id, S_g, widths = identifiable_check(orc, spec, U_m, xo[:, 0], So[0], r["x"][:D])
     assert r["status"] == 0 and n_id == 2
-    assert_determined(orc, spec, U_m, xo[:, 0], r["x"][:D], 2, ["eta sqrt(R)"])
+    assert_determined(orc, spec, U_m, xo[:, 0], r["x"][:D], 2, [])
     assert S_g <= So[0] * (1 + 1e-4)
     assert err <= 0.005, (err, widths)
     assert abs(r["S"] - S_g / NM ** 2) <= 1e-4 * S_g / NM ** 2

@@ -3,7 +3,7 @@ records: the Gauss-Newton Hessian agrees with central differences where the
 record determines the parameters, a point moved along the DMT law's exact
 valley (R changed with H R, E* sqrt(R) and a0 held) has the same misfit and
 zero error on every named combination, and the determined subspace of the
-full-size 3-mode record holds E* sqrt(R) and a0 but not H R."""
+full-size 3-mode record holds E* sqrt(R), most of a0 and little of H R."""
 import json
 import math
 import os
@@ -66,5 +66,6 @@ def test_named_subspace_of_the_full_size_record(orc):
     spec, U_m, x0, _ = _c2_gold(orc)
     n_id, named = named_check(orc, spec, U_m, x0, x0)
     assert n_id == 2
-    assert inside(named) == ["E* sqrt(R)", "a0"]
-    assert named["E* sqrt(R)"][0] >= 0.999 and named["H R"][0] <= 0.3
+    assert inside(named) == ["E* sqrt(R)"]
+    assert named["E* sqrt(R)"][0] >= 0.999 and 0.9 <= named["a0"][0] < 0.99
+    assert named["H R"][0] <= 0.3
