@@ -266,6 +266,34 @@ afm_status afm_pso_init(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw, voi
 afm_status afm_pso_step(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw,
                         const float* S_new, uint32_t iter, void* stream);
 
+/* ---- one swarm split across processes (Sec. 3.4, Eq. 8) ------------------
+ * The synchronous swarm of cfg->P particles in contiguous slices, one per
+ * process (GPU): a process holds particles p0 .. p0 + sw->P - 1 in its own
+ * afm_swarm (arrays of sw->P columns) and evaluates their misfits itself
+ * (e.g. afm_forward_batch).  Per generation iter = 0 .. cfg->iters:
+ *   afm_pso_best_slice   personal bests of the slice from its misfits S_new
+ *                        [sw->P] (as afm_pso_step's part 1), and *sw->gbest
+ *                        = the slice's best key: (float bits of the misfit)
+ *                        << 32 | swarm-wide particle index;
+ *   the processes then reduce their keys to the minimum (the swarm's global
+ *   best: lowest misfit, lowest index on ties; the paper's synchronous
+ *   global best) and the process owning that particle sends its personal
+ *   best position, a column of its pbest_x, to the others (D floats);
+ *   afm_pso_move_slice   unless iter == cfg->iters: the Eq. 8 move of the
+ *                        slice for generation iter + 1 with that global-best
+ *                        position gbest_x [D] (device).
+ * afm_pso_init_slice starts the slice as afm_pso_init.  The Philox counters
+ * carry the swarm-wide index p0 + p, so slices covering 0 .. P - 1 give the
+ * swarm of afm_pso_step (and afm_invert) bit for bit.  Errors:
+ * AFM_ERR_INVALID_ARG for a slice outside the swarm, a NULL array, or (move)
+ * iter >= cfg->iters. */
+afm_status afm_pso_init_slice(afm_ctx* ctx, const afm_pso_cfg* cfg, int p0, afm_swarm* sw,
+                              void* stream);
+afm_status afm_pso_best_slice(afm_ctx* ctx, const afm_pso_cfg* cfg, int p0, afm_swarm* sw,
+                              const float* S_new, uint32_t iter, void* stream);
+afm_status afm_pso_move_slice(afm_ctx* ctx, const afm_pso_cfg* cfg, int p0, afm_swarm* sw,
+                              const float* gbest_x, uint32_t iter, void* stream);
+
 /* ---- inverse problem IP (Sec. 2.3) --------------------------------------
  * One fused inversion: initial swarm, (iters + 1) fused evaluations (PSO
  * move + RK4 forward + misfit + personal/global best), then the winner is

@@ -406,30 +406,39 @@ int orc_misfit_batch(const orc_case* c, const orc_pmap* pm, const double* x,
 /* Counter words: (particle, iteration, pixel, tag<<16 | block);            */
 /* tags 0 = initial x, 1 = initial v, 2 = r1/r2.                            */
 /* ======================================================================== */
-void orc_pso_init(int P, int D, uint64_t seed, uint32_t pixel, double* x, double* v)
+/* Particles p0 .. p0 + P - 1 of a swarm (a slice of it; the counters carry
+ * the swarm-wide index), stored as columns 0 .. P - 1. */
+void orc_pso_init_slice(int P, int p0, int D, uint64_t seed, uint32_t pixel, double* x, double* v)
 {
     for (int p = 0; p < P; ++p)
         for (int d = 0; d < D; ++d) {
-            double u0 = orc_draw(seed, (uint32_t)p, 0, pixel, 0, (uint32_t)(d / 4), d % 4);
-            double u1 = orc_draw(seed, (uint32_t)p, 0, pixel, 1, (uint32_t)(d / 4), d % 4);
+            const uint32_t id = (uint32_t)(p0 + p);
+            double u0 = orc_draw(seed, id, 0, pixel, 0, (uint32_t)(d / 4), d % 4);
+            double u1 = orc_draw(seed, id, 0, pixel, 1, (uint32_t)(d / 4), d % 4);
             x[(size_t)d * P + p] = u0;
             v[(size_t)d * P + p] = (u1 - u0) / 2.0;
         }
 }
 
+void orc_pso_init(int P, int D, uint64_t seed, uint32_t pixel, double* x, double* v)
+{
+    orc_pso_init_slice(P, 0, D, seed, pixel, x, v);
+}
+
 /* Eq. 8: v <- w v + c1 r1 (b_l - x) + c2 r2 (b_g - x); x <- x + v; a
  * coordinate that leaves [0, 1] is put on the bound and its velocity zeroed.
  * r1, r2 per particle and dimension: words 2d and 2d+1 of the tag-2 stream. */
-void orc_pso_update(int P, int D, uint32_t it, uint64_t seed, uint32_t pixel,
-                    double w, double c1, double c2, double* x, double* v,
-                    const double* pbest_x, const double* gbest_x)
+void orc_pso_update_slice(int P, int p0, int D, uint32_t it, uint64_t seed, uint32_t pixel,
+                          double w, double c1, double c2, double* x, double* v,
+                          const double* pbest_x, const double* gbest_x)
 {
     for (int p = 0; p < P; ++p)
         for (int d = 0; d < D; ++d) {
             size_t q = (size_t)d * P + p;
             uint32_t blk = (uint32_t)((2 * d) / 4);
-            double r1 = orc_draw(seed, (uint32_t)p, it, pixel, 2, blk, (2 * d) % 4);
-            double r2 = orc_draw(seed, (uint32_t)p, it, pixel, 2, blk, (2 * d + 1) % 4);
+            const uint32_t id = (uint32_t)(p0 + p);
+            double r1 = orc_draw(seed, id, it, pixel, 2, blk, (2 * d) % 4);
+            double r2 = orc_draw(seed, id, it, pixel, 2, blk, (2 * d + 1) % 4);
             double vn = w * v[q] + c1 * r1 * (pbest_x[q] - x[q]) + c2 * r2 * (gbest_x[d] - x[q]);
             double xn = x[q] + vn;
             if (xn < 0.0) { xn = 0.0; vn = 0.0; }
@@ -437,6 +446,13 @@ void orc_pso_update(int P, int D, uint32_t it, uint64_t seed, uint32_t pixel,
             x[q] = xn;
             v[q] = vn;
         }
+}
+
+void orc_pso_update(int P, int D, uint32_t it, uint64_t seed, uint32_t pixel,
+                    double w, double c1, double c2, double* x, double* v,
+                    const double* pbest_x, const double* gbest_x)
+{
+    orc_pso_update_slice(P, 0, D, it, seed, pixel, w, c1, c2, x, v, pbest_x, gbest_x);
 }
 
 static int argmin_first(const double* S, int P)

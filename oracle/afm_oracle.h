@@ -155,6 +155,11 @@ int orc_misfit_batch(const orc_case* c, const orc_pmap* pm, const double* x,
 
 /* ---- particle swarm (Sec. 3.4, Eq. 8) ------------------------------------ */
 void orc_pso_init(int P, int D, uint64_t seed, uint32_t pixel, double* x, double* v);
+/* the same for particles p0 .. p0 + P - 1 of a larger swarm (columns 0 .. P - 1) */
+void orc_pso_init_slice(int P, int p0, int D, uint64_t seed, uint32_t pixel, double* x, double* v);
+void orc_pso_update_slice(int P, int p0, int D, uint32_t it, uint64_t seed, uint32_t pixel,
+                          double w, double c1, double c2, double* x, double* v,
+                          const double* pbest_x, const double* gbest_x);
 void orc_pso_update(int P, int D, uint32_t it, uint64_t seed, uint32_t pixel,
                     double w, double c1, double c2, double* x, double* v,
                     const double* pbest_x, const double* gbest_x);

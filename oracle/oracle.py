@@ -106,6 +106,11 @@ def lib():
             L.orc_misfit_batch.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int,
                                            _dp, C.c_int, _dp]
             L.orc_pso_init.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32, _dp, _dp]
+            L.orc_pso_init_slice.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
+                                             _dp, _dp]
+            L.orc_pso_update_slice.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint32, C.c_uint64,
+                                               C.c_uint32, C.c_double, C.c_double, C.c_double,
+                                               _dp, _dp, _dp, _dp]
             L.orc_pso_update.argtypes = [C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint32,
                                          C.c_double, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
             L.orc_invert.argtypes = [C.POINTER(Case), C.POINTER(Pmap), _dp, C.c_int,
@@ -281,21 +286,23 @@ def misfit_batch(case: Case, pm: Pmap, x_dp, U) -> np.ndarray:
     return S
 
 
-def pso_init(P: int, D: int, seed: int, pixel: int = 0):
+def pso_init(P: int, D: int, seed: int, pixel: int = 0, p0: int = 0):
+    """Initial positions and velocities [D][P] of particles p0 .. p0 + P - 1."""
     x = np.zeros((D, P))
     v = np.zeros((D, P))
-    lib().orc_pso_init(P, D, seed, pixel, x, v)
+    lib().orc_pso_init_slice(P, p0, D, seed, pixel, x, v)
     return x, v
 
 
 def pso_update(it: int, seed: int, pixel: int, w: float, c1: float, c2: float,
-               x, v, pbest_x, gbest_x):
+               x, v, pbest_x, gbest_x, p0: int = 0):
+    """Eq. 8 move of particles p0 .. p0 + P - 1 (columns of x, v [D][P])."""
     x = np.array(x, dtype=np.float64, order="C")
     v = np.array(v, dtype=np.float64, order="C")
     D, P = x.shape
-    lib().orc_pso_update(P, D, it, seed, pixel, w, c1, c2, x, v,
-                         np.ascontiguousarray(pbest_x, dtype=np.float64),
-                         np.ascontiguousarray(gbest_x, dtype=np.float64))
+    lib().orc_pso_update_slice(P, p0, D, it, seed, pixel, w, c1, c2, x, v,
+                               np.ascontiguousarray(pbest_x, dtype=np.float64),
+                               np.ascontiguousarray(gbest_x, dtype=np.float64))
     return x, v
 
 

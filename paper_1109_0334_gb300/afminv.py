@@ -111,6 +111,11 @@ def lib():
             L.afm_misfit.argtypes = [vp, vp, vp, i, i, vp, vp]
             L.afm_pso_init.argtypes = [vp, C.POINTER(PsoCfg), C.POINTER(Swarm), vp]
             L.afm_pso_step.argtypes = [vp, C.POINTER(PsoCfg), C.POINTER(Swarm), vp, u32, vp]
+            L.afm_pso_init_slice.argtypes = [vp, C.POINTER(PsoCfg), i, C.POINTER(Swarm), vp]
+            L.afm_pso_best_slice.argtypes = [vp, C.POINTER(PsoCfg), i, C.POINTER(Swarm), vp, u32,
+                                             vp]
+            L.afm_pso_move_slice.argtypes = [vp, C.POINTER(PsoCfg), i, C.POINTER(Swarm), vp, u32,
+                                             vp]
             L.afm_invert_workspace_size.argtypes = [C.POINTER(Problem), C.POINTER(PsoCfg),
                                                     C.POINTER(C.c_size_t)]
             L.afm_invert.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(PsoCfg), vp,
@@ -329,6 +334,37 @@ def pso_step(cfg: PsoCfg, sw: SwarmState, S_new, it: int, stream=None) -> None:
     cs = sw.c_struct()
     _check(lib().afm_pso_step(context(sw.x.device.index), C.byref(cfg), C.byref(cs),
                               _ptr(S_new), int(it), _stream(stream)))
+
+
+def pso_init_slice(cfg: PsoCfg, p0: int, n: int, D: int, device=None, stream=None) -> SwarmState:
+    """Particles p0 .. p0 + n - 1 of a swarm of cfg.P split across processes
+    (afm_pso_init_slice)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    sw = SwarmState(x=torch.empty((D, n), dtype=torch.float32, device=dev),
+                    v=torch.empty((D, n), dtype=torch.float32, device=dev),
+                    pbest_x=torch.empty((D, n), dtype=torch.float32, device=dev),
+                    pbest_S=torch.empty(n, dtype=torch.float32, device=dev),
+                    gbest=torch.empty(1, dtype=torch.int64, device=dev))
+    cs = sw.c_struct()
+    _check(lib().afm_pso_init_slice(context(dev.index), C.byref(cfg), int(p0), C.byref(cs),
+                                    _stream(stream)))
+    return sw
+
+
+def pso_best_slice(cfg: PsoCfg, p0: int, sw: SwarmState, S_new, it: int, stream=None) -> None:
+    """Personal bests of the slice and its best key in sw.gbest."""
+    cs = sw.c_struct()
+    _check(lib().afm_pso_best_slice(context(sw.x.device.index), C.byref(cfg), int(p0), C.byref(cs),
+                                    _ptr(S_new), int(it), _stream(stream)))
+
+
+def pso_move_slice(cfg: PsoCfg, p0: int, sw: SwarmState, gbest_x, it: int, stream=None) -> None:
+    """Eq. 8 move of the slice for generation it + 1 with the swarm's global
+    best position gbest_x (float32 CUDA [D])."""
+    cs = sw.c_struct()
+    _check(lib().afm_pso_move_slice(context(sw.x.device.index), C.byref(cfg), int(p0), C.byref(cs),
+                                    _ptr(gbest_x), int(it), _stream(stream)))
 
 
 def invert_workspace_size(prob: Problem, cfg: PsoCfg) -> int:

@@ -24,6 +24,7 @@ struct PsoConst {
     float w, c1, c2;
     uint64_t seed;
     uint32_t pixel;
+    uint32_t p0;   // swarm-wide index of particle 0 (a slice of a split swarm; else 0)
 };
 
 // forward + optional misfit; lanes (afm_lanes): AFM_LANES_ONE keeps one
@@ -179,6 +180,9 @@ cudaError_t launch_pso_init(const PsoConst& pc, const SwarmPtrs& sw, cudaStream_
 cudaError_t launch_pso_best(const PsoConst& pc, const SwarmPtrs& sw, const float* S, int it,
                             cudaStream_t st);
 cudaError_t launch_pso_move(const PsoConst& pc, const SwarmPtrs& sw, int it, cudaStream_t st);
+// the move with a given global-best position gb [D] (a slice of a split swarm)
+cudaError_t launch_pso_move_given(const PsoConst& pc, const SwarmPtrs& sw, const float* gb, int it,
+                                  cudaStream_t st);
 // fused inversion iteration (it = 0: initial evaluation); `lanes` picks the
 // lanes-per-particle variant (afm_lanes of afminv.h; all are bit-identical,
 // a variant the problem does not support runs the automatic choice)

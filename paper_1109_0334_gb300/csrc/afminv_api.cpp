@@ -647,6 +647,7 @@ afm::PsoConst pso_const(const afm_pso_cfg& c, int D) {
     pc.c2 = (float)c.c2;
     pc.seed = c.seed;
     pc.pixel = c.pixel;
+    pc.p0 = 0;
     return pc;
 }
 
@@ -1128,6 +1129,67 @@ afm_status afm_pso_step(afm_ctx* ctx, const afm_pso_cfg* cfg, afm_swarm* sw, con
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     AFM_CUDA(afm::launch_pso_best(pc, p, S_new, (int)iter, s), "pso best kernel");
     if ((int)iter < cfg->iters) AFM_CUDA(afm::launch_pso_move(pc, p, (int)iter + 1, s), "pso move kernel");
+    return AFM_OK;
+}
+
+// A slice of a split swarm: particles p0 .. p0 + sw->P - 1 of cfg->P.
+static afm_status slice_setup(afm_ctx* ctx, const afm_pso_cfg* cfg, int p0, afm_swarm* sw,
+                              afm::SwarmPtrs& p, afm::PsoConst& pc) {
+    afm_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!sw) return fail(AFM_ERR_INVALID_ARG, "swarm is NULL");
+    if ((st = check_pso(cfg, sw->D))) return st;
+    if (sw->P < 1 || sw->D > AFM_MAX_PARAMS || p0 < 0 || (long long)p0 + sw->P > cfg->P)
+        return fail(AFM_ERR_INVALID_ARG, "slice p0 %d of %d particles outside the swarm of %d",
+                    p0, sw->P, cfg->P);
+    if ((st = swarm_ptrs(sw, p))) return st;
+    pc = pso_const(*cfg, sw->D);
+    pc.P = sw->P;
+    pc.p0 = (uint32_t)p0;
+    return AFM_OK;
+}
+
+afm_status afm_pso_init_slice(afm_ctx* ctx, const afm_pso_cfg* cfg, int p0, afm_swarm* sw,
+                              void* stream) {
+    AFM_TRACE("afm_pso_init_slice");
+    g_err[0] = 0;
+    afm::SwarmPtrs p;
+    afm::PsoConst pc;
+    afm_status st = slice_setup(ctx, cfg, p0, sw, p, pc);
+    if (st) return st;
+    AFM_CUDA(afm::launch_pso_init(pc, p, reinterpret_cast<cudaStream_t>(stream)), "pso init kernel");
+    return AFM_OK;
+}
+
+afm_status afm_pso_best_slice(afm_ctx* ctx, const afm_pso_cfg* cfg, int p0, afm_swarm* sw,
+                              const float* S_new, uint32_t iter, void* stream) {
+    AFM_TRACE("afm_pso_best_slice");
+    g_err[0] = 0;
+    afm::SwarmPtrs p;
+    afm::PsoConst pc;
+    afm_status st = slice_setup(ctx, cfg, p0, sw, p, pc);
+    if (st) return st;
+    if (!S_new) return fail(AFM_ERR_INVALID_ARG, "S_new is NULL");
+    if ((int)iter > cfg->iters) return fail(AFM_ERR_INVALID_ARG, "iter %u > iters", iter);
+    AFM_CUDA(afm::launch_pso_best(pc, p, S_new, (int)iter, reinterpret_cast<cudaStream_t>(stream)),
+             "pso best kernel");
+    return AFM_OK;
+}
+
+afm_status afm_pso_move_slice(afm_ctx* ctx, const afm_pso_cfg* cfg, int p0, afm_swarm* sw,
+                              const float* gbest_x, uint32_t iter, void* stream) {
+    AFM_TRACE("afm_pso_move_slice");
+    g_err[0] = 0;
+    afm::SwarmPtrs p;
+    afm::PsoConst pc;
+    afm_status st = slice_setup(ctx, cfg, p0, sw, p, pc);
+    if (st) return st;
+    if (!gbest_x) return fail(AFM_ERR_INVALID_ARG, "gbest_x is NULL");
+    if ((int)iter >= cfg->iters)
+        return fail(AFM_ERR_INVALID_ARG, "iter %u: the last evaluation (iters) has no move", iter);
+    AFM_CUDA(afm::launch_pso_move_given(pc, p, gbest_x, (int)iter + 1,
+                                        reinterpret_cast<cudaStream_t>(stream)),
+             "pso move kernel");
     return AFM_OK;
 }
 

@@ -64,9 +64,10 @@ __global__ void pso_init_kernel(const PsoConst pc, SwarmPtrs sw) {
         if (sw.flags) sw.flags[0] = 0;
     }
     if (p >= pc.P) return;
+    const uint32_t id = pc.p0 + (uint32_t)p;   // swarm-wide particle index
     for (int b = 0; b * 4 < pc.D; ++b) {
-        uint4 w0 = philox_draw(pc.seed, (uint32_t)p, 0u, pc.pixel, 0u, (uint32_t)b);
-        uint4 w1 = philox_draw(pc.seed, (uint32_t)p, 0u, pc.pixel, 1u, (uint32_t)b);
+        uint4 w0 = philox_draw(pc.seed, id, 0u, pc.pixel, 0u, (uint32_t)b);
+        uint4 w1 = philox_draw(pc.seed, id, 0u, pc.pixel, 1u, (uint32_t)b);
         for (int k = 0; k < 4 && b * 4 + k < pc.D; ++k) {
             const int d = b * 4 + k;
             const float u0 = unif24(word_of(w0, k)), u1 = unif24(word_of(w1, k));
@@ -98,7 +99,7 @@ __global__ void pso_best_kernel(const PsoConst pc, SwarmPtrs sw, const float* __
             for (int d = 0; d < pc.D; ++d)
                 sw.pb[0][(size_t)d * pc.P + p] = sw.x[(size_t)d * pc.P + p];
         }
-        key = best_key(best, p);
+        key = best_key(best, (int)(pc.p0 + (uint32_t)p));
     }
     warp_min_atomic(key, sw.gkey[0]);
 }
@@ -122,6 +123,34 @@ __global__ void pso_move_kernel(const PsoConst pc, SwarmPtrs sw, int it) {
         sw.x[(size_t)d * pc.P + p] = x[d];
         sw.v[(size_t)d * pc.P + p] = v[d];
     }
+}
+
+// The same move with the global best position given (gb [D], device): the
+// particles of a slice of a swarm split across processes.
+__global__ void pso_move_given_kernel(const PsoConst pc, SwarmPtrs sw, const float* __restrict__ gbp,
+                                      int it) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= pc.P) return;
+    float x[AFM_MAXD], v[AFM_MAXD], pb[AFM_MAXD], gb[AFM_MAXD];
+    for (int d = 0; d < pc.D; ++d) {
+        const size_t q = (size_t)d * pc.P;
+        x[d] = sw.x[q + p];
+        v[d] = sw.v[q + p];
+        pb[d] = sw.pb[0][q + p];
+        gb[d] = gbp[d];
+    }
+    pso_move_dev(pc, x, v, pb, gb, (int)(pc.p0 + (uint32_t)p), it);
+    for (int d = 0; d < pc.D; ++d) {
+        sw.x[(size_t)d * pc.P + p] = x[d];
+        sw.v[(size_t)d * pc.P + p] = v[d];
+    }
+}
+
+cudaError_t launch_pso_move_given(const PsoConst& pc, const SwarmPtrs& sw, const float* gb, int it,
+                                  cudaStream_t st) {
+    const int threads = 128;
+    pso_move_given_kernel<<<(pc.P + threads - 1) / threads, threads, 0, st>>>(pc, sw, gb, it);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pso_best(const PsoConst& pc, const SwarmPtrs& sw, const float* S, int it,

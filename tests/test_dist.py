@@ -77,3 +77,95 @@ def test_reference_arm_other_ranks_exit_without_work():
                        env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def _split_rank_main(rank, world, port, q):
+    """One rank of a swarm split over gloo: its slice of a C1 swarm, misfits
+    from the oracle (rounded to FP32 nm^2, the library's key precision),
+    personal bests, the exchange of split.exchange_dist, the Eq. 8 move of
+    its slice by the oracle; plus its share of a sharded image."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import bench
+    import torch.distributed as dist
+    from paper_1109_0334_gb300 import split
+    r, w, _ = bench.dist_setup(backend="gloo")
+    keys, x_fin = _swarm_run(split, r, w, exchange=True)
+    lo, hi = bench.rank_slice(4096 * w, r, w)
+    spans = [None] * w
+    dist.all_gather_object(spans, (lo, hi))
+    dist.destroy_process_group()
+    q.put((r, keys, x_fin.tolist(), spans))
+
+
+def _swarm_run(split, rank, world, exchange):
+    """Keys after each generation and the final global-best position."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_1109_0334_gb300 import workloads as W
+    from common import oracle_record
+    O.build()
+    O.set_threads(1)
+    spec = W.get("c1", P=64, iters=8)
+    c, pm = O.make_case(spec), O.make_pmap(spec)
+    _, U_m, _ = oracle_record(O, spec)
+    P, D = spec["P"], pm.D
+    lo, hi = split.slice_of(P, rank, world) if exchange else (0, P)
+    x, v = O.pso_init(hi - lo, D, spec["seed"], 0, p0=lo)
+    pb, pbS = x.copy(), np.full(hi - lo, np.inf, dtype=np.float32)
+    keys = []
+    for it in range(spec["iters"] + 1):
+        S32 = (O.misfit_batch(c, pm, x, U_m) / 1e-18).astype(np.float32)
+        better = (S32 < pbS) | (it == 0)
+        pbS = np.where(better, np.minimum(S32, pbS), pbS).astype(np.float32)
+        pb[:, better] = x[:, better]
+        loc = [(int(np.float32(s).view(np.uint32)) << 32) | (lo + p) for p, s in enumerate(pbS)]
+        key = min(loc)
+        if exchange:
+            def owner(kmin):
+                g = split.key_index(kmin)
+                if lo <= g < hi:
+                    return True, torch.from_numpy(pb[:, g - lo].astype(np.float32))
+                return False, None
+            kmin, pos = split.exchange_dist(key, owner, D, torch.device("cpu"))
+            gb = pos.numpy().astype(np.float64)
+        else:
+            kmin = key
+            gb = pb[:, split.key_index(kmin)].astype(np.float32).astype(np.float64)
+        keys.append(kmin)
+        if it < spec["iters"]:
+            x, v = O.pso_update(it + 1, spec["seed"], 0, spec["w"], spec["c1"], spec["c2"], x, v,
+                                pb, gb, p0=lo)
+    return keys, gb
+
+
+def test_split_swarm_exchange_reproduces_one_rank():
+    """Two gloo ranks, each with half of the swarm, reproduce the one-rank
+    sequence of global-best keys bit for bit and end on the same position;
+    the image shards of the benchmark cover every pixel exactly once."""
+    import torch.multiprocessing as mp
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from paper_1109_0334_gb300 import split
+    ref_keys, ref_x = _swarm_run(split, 0, 1, exchange=False)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_split_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted([q.get(timeout=300) for _ in procs])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, keys, x_fin, spans in out:
+        assert keys == ref_keys
+        assert x_fin == ref_x.tolist()
+        covered = sorted(i for lo, hi in spans for i in range(lo, hi))
+        assert covered == list(range(2 * 4096))
+    # the winner moved between the slices at least once (the exchange matters)
+    owners = {split.key_index(k) >= 32 for k in ref_keys}
+    assert owners == {True, False}
