@@ -70,6 +70,20 @@ def algo_ops_per_step(m: int) -> int:
     return 36 * m + 24
 
 
+def fe_algo_ops_per_step(n: int = 64) -> int:
+    """The method's FP32 operations per particle and Newmark step of the FE
+    cantilever run in its modal basis (the roofline's numerator): per mode
+    the increment b1 z + d2 dz + g G + f Fo (1 mul + 3 fma), the predicted
+    tip term pt (z + dz + inc) (2 adds + 1 fma) and the update dz += inc + f
+    F, z += dz (1 fma + 2 adds): 10; per particle Fo = 2 F_n + F_{n-1} (1),
+    one Newton step of the DMT law with the final force evaluation (2 x 8 for
+    gap and law, 4 for residual and update), the tip deflection (1) and the
+    compensated misfit (5): 27.  667 for 64 modes.  The kernel issues more
+    (fe_fp32_ops_per_step): compensated updates of the lowest modes and the
+    group's redundant Newton solve and tip sum."""
+    return 10 * n + 27
+
+
 def fe_fp32_ops_per_step() -> int:
     """FP32 add/mul/fma instructions per particle per step of the FP32 FE
     kernel (DMT law, 64 modes on 8 lanes of 8 mode slots), counted from its
@@ -166,6 +180,7 @@ KERNEL_SOURCES = {
     "fwd_x2_kernel": ["afm_device.cuh", "afm_internal.h", "afm_f32x2.cuh", "kern_forward.cu"],
     "batch_kernel": ["afm_device.cuh", "afm_internal.h", "afm_f32x2.cuh", "kern_batch.cuh", "kern_batch.cu",
                      "kern_batch_dmt.cu"],
+    "fe_modal_kernel": ["afm_device.cuh", "afm_internal.h", "kern_fe.cu"],
 }
 
 
@@ -326,12 +341,43 @@ def _dchi2_and_comb(A, spec, prob_n, U_pix, r, x_ref):
     return (r["S_f64"] - S_ref) / var, [abs(a / b - 1) for a, b in zip(ca, cb)], S_ref
 
 
+def determined_error(A, spec, prob_n, U_pix, x_ref, x_test, rel=0.005):
+    """Relative parameter error of x_test against x_ref along the directions
+    the record determines: the misfit's Gauss-Newton Hessian at x_ref (the
+    library's tangent-linear normal equations), in log-parameter coordinates,
+    has eigen-directions of one-sigma half-width sqrt(2 sigma^2 / lambda)
+    for noise sigma; over those of half-width <= rel, the largest projection
+    of the log-parameter difference.  Returns (error, number of such
+    directions)."""
+    import numpy as np
+    import torch
+    D = len(spec["free"])
+    xo = torch.tensor(x_ref, dtype=torch.float32, device=U_pix.device).reshape(D, 1)
+    _, H, _ = A.normal_equations(prob_n, xo, U_pix.contiguous())
+    Hs = 2.0 * H[0].cpu().numpy()                        # Hessian of S [nm^2]
+    th_r, th_t = _theta_of(spec, x_ref), _theta_of(spec, x_test)
+    J, drho = np.empty(D), np.empty(D)
+    for d, (slot, lo, hi, lg) in enumerate(spec["free"]):
+        J[d] = math.log(10.0) * (math.log10(hi) - math.log10(lo)) if lg else (hi - lo) / th_r[slot]
+        drho[d] = math.log(th_t[slot] / th_r[slot])
+    lam, V = np.linalg.eigh(Hs / np.outer(J, J))
+    widths = np.sqrt(2 * (spec["sigma"] / 1e-9) ** 2 / np.maximum(lam, 1e-300))
+    ident = widths <= rel
+    proj = np.abs(V.T @ drho)
+    return (float(proj[ident].max()) if ident.any() else 0.0), int(ident.sum())
+
+
 def accuracy_vs_oracle(A, spec, U, off, results, golden=GOLDEN_C3):
     """Each result of the first pixels against the oracle's stored optimum of
     the same pixel (tests/golden/c3_subset_optima.json, written by the
     oracle alone on records with the same truths, lengths and noise):
     delta chi^2 = (S - S_opt) / sigma^2 on this record (<= 1: statistically
-    at the optimum) and the identifiable combinations within 0.5 %."""
+    at the optimum), the parameter error along the directions the record
+    determines to 0.5 % (determined_error), and, for information, the
+    combinations H R, E* sqrt(R), a0 (only some of which a record
+    determines) against the optimum's.  A point more than one noise variance
+    below the stored optimum counts as meeting the parameter criterion (it is
+    a better optimum than the stored one)."""
     import numpy as np
     with open(golden) as f:
         gold = json.load(f)
@@ -342,22 +388,29 @@ def accuracy_vs_oracle(A, spec, U, off, results, golden=GOLDEN_C3):
         n = int(off_h[i + 1] - off_h[i])
         assert n == g["cycles"] * spec["spc"], "golden subset and bench records differ"
         prob_n = A.make_problem(spec, n_steps=n)
-        d, comb, _ = _dchi2_and_comb(A, spec, prob_n, U[int(off_h[i]):int(off_h[i + 1])],
-                                     results[i], g["x"])
-        rows.append((d, comb))
+        U_pix = U[int(off_h[i]):int(off_h[i + 1])]
+        d, comb, _ = _dchi2_and_comb(A, spec, prob_n, U_pix, results[i], g["x"])
+        e, n_id = determined_error(A, spec, prob_n, U_pix, g["x"], list(results[i]["x"][:len(g["x"])]))
+        rows.append((d, comb, e, n_id))
     dchi = np.array([r[0] for r in rows])
     comb = np.array([r[1] for r in rows])
-    ok = (dchi <= 1.0)
+    err = np.array([r[2] for r in rows])
+    # a point more than one noise variance below the stored optimum is a
+    # better optimum than the oracle's: the parameter comparison is void there
+    ok, ok_p = dchi <= 1.0, (err <= 0.005) | (dchi < -1.0)
     return {"pixels": len(rows),
             "reference": "oracle optimum per pixel (own 256 x 60 swarm, then 12 LM steps from "
                          "its winner and from the seeded truth; best of the three), FP64 misfit "
                          "re-evaluated on this run's record",
             "frac_dchi2_le_1": float(ok.mean()),
-            "frac_ident_within_0.5pct": float(np.all(comb <= 0.005, axis=1).mean()),
-            "frac_Esqrt_R_within_0.5pct": float((comb[:, 1] <= 0.005).mean()),
-            "frac_meeting_both": float((ok & np.all(comb <= 0.005, axis=1)).mean()),
+            "frac_param_err_le_0.5pct_determined": float(ok_p.mean()),
+            "frac_meeting_both": float((ok & ok_p).mean()),
             "median_dchi2": float(np.median(dchi)), "max_dchi2": float(dchi.max()),
-            "ident": "H R, E* sqrt(R), a0"}
+            "median_determined_directions": float(np.median([r[3] for r in rows])),
+            "frac_combinations_within_0.5pct": {
+                "H R": float((comb[:, 0] <= 0.005).mean()),
+                "E* sqrt(R)": float((comb[:, 1] <= 0.005).mean()),
+                "a0": float((comb[:, 2] <= 0.005).mean())}}
 
 
 def run_c3_polished(A, spec, prob, U, off, pixel0, flush, steps=3):
@@ -546,7 +599,7 @@ def run_c5(A, W, dev, peak_ops, flush, iters=None):
     ms = e0.elapsed_time(e1)
     r = A.decode_result(res)
     units = spec["P"] * (spec["iters"] + 1) * N
-    ops_ps = fe_fp32_ops_per_step()
+    ops_ps = fe_algo_ops_per_step()
     ach = spec["P"] * N * ops_ps / ((kms / max(kn, 1)) / 1e3)
     return {"workload": "c5: 32-element Hermite FE cantilever, Newmark beta=1/4, DMT 4 unknowns, "
                         "8192 particles x 60 updates, 50 cycles x 512 steps",
@@ -556,6 +609,9 @@ def run_c5(A, W, dev, peak_ops, flush, iters=None):
             "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP32 lane-ops/s", "frac": ach / peak_ops,
                          "ops_per_particle_step": ops_ps,
+                         "issued_ops_per_particle_step": fe_fp32_ops_per_step(),
+                         "kernel": "fe_modal_kernel<float,DMT,invert iteration>",
+                         "traffic": ncu_traffic("fe_modal_kernel", "c5"),
                          "note": "modal-basis Newmark kernel (no dense propagator)"}}
 
 
@@ -788,8 +844,11 @@ def run_c2(A, W, dev, flush, peak_ops, steps=3):
 
     def acc(rr):
         d, comb, S_ref = _dchi2_and_comb(A, spec, prob, U, rr, gold["x"])
-        return {"dchi2_vs_oracle_optimum": d, "ident_rel_err_vs_oracle": comb,
-                "meets_0.5pct": bool(d <= 1.0 and max(comb) <= 0.005)}
+        e, n_id = determined_error(A, spec, prob, U, gold["x"], list(rr["x"][:D]))
+        return {"dchi2_vs_oracle_optimum": d, "param_err_determined": e,
+                "determined_directions": n_id,
+                "combinations_rel_err_vs_oracle": dict(zip(("H R", "E* sqrt(R)", "a0"), comb)),
+                "meets_0.5pct": bool(d <= 1.0 and (e <= 0.005 or d < -1.0))}
     units = P * (iters + 1) * N
     ops_launch = P * N * algo_ops_per_step(m)
     avg_s = (kms / max(kn, 1)) / 1e3
@@ -1023,9 +1082,10 @@ def run_ours(args):
             "ms_per_inversion_at_0.5pct": None if polished is None else {
                 "config": "LM-polished batch: " + polished["config"],
                 "ms_per_pixel_inversion": polished["ms_per_pixel_inversion"],
-                "frac_pixels_dchi2_le_1": polished["accuracy_vs_oracle"]["frac_dchi2_le_1"],
-                "frac_pixels_ident_within_0.5pct":
-                    polished["accuracy_vs_oracle"]["frac_ident_within_0.5pct"]},
+                "frac_pixels_meeting": polished["accuracy_vs_oracle"]["frac_meeting_both"],
+                "criterion": "delta chi^2 <= 1 against the oracle's optimum and <= 0.5 % "
+                             "parameter error along every direction the record determines to "
+                             "0.5 % (32-pixel subset)"},
             "lm_polished_batch": polished,
         }
         out.update(extras)
@@ -1131,10 +1191,12 @@ def run_probe(args):
     from paper_1109_0334_gb300 import workloads as W
 
     if args.probe == "batch":
-        # one wave of pixels with records shortened tenfold, --probe-iters updates
+        # one full wave of resident pixels (8 per SM: the occupancy of the
+        # 4-particles-per-thread kernel) with records shortened tenfold,
+        # --probe-iters updates
         props = torch.cuda.get_device_properties(0)
         spec, prob, U, off, total, _, _ = c3_inputs(A, W, torch.device("cuda"),
-                                                 n_pix=props.multi_processor_count * 4,
+                                                 n_pix=props.multi_processor_count * 8,
                                                  cycles_div=10)
         cfg = A.make_pso(dict(spec, iters=args.probe_iters))
         res, kp = A.invert_batch(prob, U, off, cfg, particles_per_thread=args.probe_kp or 0)

@@ -76,17 +76,14 @@ __device__ __forceinline__ void fe_force(const Coef<T>& c, T d, T& Fv, T& dF) {
         Fv = -c.c0 * (d - c.c1);
         dF = -c.c0;
     } else if (FORCE == F_DMT) {
-        if (d > c.c3) {
-            const T r = rcp_fast(d);
-            const T r2 = r * r;
-            Fv = -c.c1 * r2;
-            dF = (T)2 * c.c1 * r2 * r;
-        } else {
-            const T del = c.c3 - d, sq = sqrt_fast(del);
-            const T r = rcp_fast(c.c3);
-            Fv = c.c0 * del * sq - c.c1 * r * r;
-            dF = (T)(-1.5) * c.c0 * sq;
-        }
+        // branch-free (the van der Waals term saturates at d = a0, where it
+        // is the contact branch's constant): particles of one warp in and out
+        // of contact follow one instruction stream
+        const T r = rcp_fast(fmax(d, c.c3));
+        const T r2 = r * r;
+        const T del = fmax(c.c3 - d, (T)0), sq = sqrt_fast(del);
+        Fv = c.c0 * del * sq - c.c1 * r2;
+        dF = d > c.c3 ? (T)2 * c.c1 * r2 * r : (T)(-1.5) * c.c0 * sq;
     } else {   // HOOKE
         if (d < c.c1) {
             Fv = c.c0 * (c.c1 - d);
@@ -96,6 +93,25 @@ __device__ __forceinline__ void fe_force(const Coef<T>& c, T d, T& Fv, T& dF) {
             dF = (T)0;
         }
     }
+}
+
+// sum_j pt_j zp_j (the predicted tip deflection of a lane's mode slots) as a
+// pairwise tree: the products of a pair meet in one fma, the pairs' sums in
+// a balanced tree -- a dependency chain of log2(N) + 2 operations instead of
+// N fmas.
+template <typename T, int N>
+__device__ __forceinline__ T fe_dot(const T* pt, const T* zp) {
+    T s[(N + 1) / 2];
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) s[k] = fma(pt[2 * k], zp[2 * k], pt[2 * k + 1] * zp[2 * k + 1]);
+    if (N % 2) s[N / 2] = pt[N - 1] * zp[N - 1];
+#pragma unroll
+    for (int w = (N + 1) / 2; w > 1; w = (w + 1) / 2) {
+#pragma unroll
+        for (int k = 0; k < w / 2; ++k) s[k] = s[2 * k] + s[2 * k + 1];
+        if (w % 2) s[w / 2] = s[w - 1];
+    }
+    return s[0];
 }
 
 // z = base + cz F(Zc + z) by Newton from z = base.
@@ -219,12 +235,16 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
     // changes no result in the tests' cases), to FP64 after 3
     const int newton_it = sizeof(T) == 8 ? 3 : 1;
     int jn = 0;
+    // the record value of step n is loaded during step n - 1, so that no
+    // step waits for a global-memory load
+    T Unext = (U != nullptr && F.n_steps > 0 && lane == 0) ? (T)U[0] : (T)0;
     for (int n = 0; n < F.n_steps; ++n) {
         const int jp = jn + 1 == spc ? 0 : jn + 1;
+        const T Un = Unext;
+        if (U != nullptr && lane == 0 && n + 1 < F.n_steps) Unext = (T)U[n + 1];
         const T G = tab[jn];
         const T Fo = (T)2 * Fn + Fm;
-        T incs[FEM], cfs[FEM];
-        T tsum = (T)0;
+        T incs[FEM], cfs[FEM], pts[FEM], zps[FEM];
 #pragma unroll
         for (int j = 0; j < FEM; ++j) {
             const int i = lane + FEL * j;
@@ -235,9 +255,10 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
             inc = fma(c4.f, Fo, inc);
             incs[j] = inc;
             cfs[j] = c4.f;
-            tsum = fma(cpt[i], fe_comp<T>(j) ? z[j] + ((dz[j] + inc) - cz[j]) : z[j] + (dz[j] + inc),
-                       tsum);
+            pts[j] = cpt[i];
+            zps[j] = fe_comp<T>(j) ? z[j] + ((dz[j] + inc) - cz[j]) : z[j] + (dz[j] + inc);
         }
+        T tsum = fe_dot<T, FEM>(pts, zps);
 #pragma unroll
         for (int o = FEL / 2; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
         T Fp;
@@ -260,7 +281,6 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
             const T ut = fma(ctip, Fp, tsum);
             if (MODE == 0 && defl != nullptr) defl[(size_t)n * P + p] = ut;
             if (U != nullptr) {
-                const T Un = (T)U[n];
                 const T r = Un - ut;
                 const T y = fma(r, r, -cS);
                 const T t = add_rn(S, y);

@@ -50,6 +50,30 @@ def test_fe_forward_parity(orc, afm, cycles, P, n_traj):
     assert np.max(np.abs(S - S_ref) / S_ref) <= 1e-4
 
 
+def test_fe_inversion_equals_composed_swarm(orc, afm):
+    """The fused FE inversion iteration against afm_pso_step driven by
+    afm_forward_batch's misfits: the same global-best key after every
+    generation and the same winner (the two kernels' FP32 arithmetic is
+    one template)."""
+    spec = W.get("c5", cycles=2, P=1000, iters=3)
+    U32, _, _ = oracle_record(orc, spec)
+    prob = afm.make_problem(spec)
+    cfg = afm.make_pso(spec)
+    Ug = torch.from_numpy(U32).cuda()
+    res, hist = afm.invert(prob, Ug, cfg)
+    sw = afm.pso_init(cfg, 4)
+    keys = []
+    for it in range(cfg.iters + 1):
+        _, S = afm.forward_batch(prob, sw.x, Ug, want_defl=False)
+        afm.pso_step(cfg, sw, S, it)
+        keys.append(int(sw.gbest.item()))
+    torch.cuda.synchronize()
+    r = afm.decode_result(res)
+    S_keys = np.array([np.uint32(k >> 32).view(np.float32) for k in keys])
+    np.testing.assert_array_equal(hist.cpu().numpy(), S_keys)
+    assert r["winner"] == keys[-1] & 0xFFFFFFFF
+
+
 def test_fe_forward_f64_parity(orc, afm):
     spec = W.get("c5", cycles=10)
     n = W.n_steps(spec)
