@@ -72,33 +72,34 @@ def algo_ops_per_step(m: int) -> int:
 
 def fe_algo_ops_per_step(n: int = 64) -> int:
     """The method's FP32 operations per particle and Newmark step of the FE
-    cantilever run in its modal basis (the roofline's numerator): per mode
-    the increment b1 z + d2 dz + g G + f Fo (1 mul + 3 fma), the predicted
-    tip term pt (z + dz + inc) (2 adds + 1 fma) and the update dz += inc + f
-    F, z += dz (1 fma + 2 adds): 10; per particle Fo = 2 F_n + F_{n-1} (1),
-    one Newton step of the DMT law with the final force evaluation (2 x 8 for
-    gap and law, 4 for residual and update), the tip deflection (1) and the
-    compensated misfit (5): 27.  667 for 64 modes.  The kernel issues more
-    (fe_fp32_ops_per_step): compensated updates of the lowest modes and the
+    cantilever run in its modal basis (the roofline's numerator), with each
+    mode carried scaled by its tip displacement (w = phi(tip) z): per mode
+    delta + increment = (1 + d2) delta + b1 w + g G + f Fo (1 mul + 3 fma),
+    the predicted coordinate w + that sum and its term of the tip sum (2
+    adds), the update delta' = that sum + f F (1 fma) and w' = w + delta' (1
+    add): 8; per particle Fo = 2 F_n + F_{n-1} (1), one Newton step of the DMT
+    law with the final force evaluation (2 x 8 for gap and law, 4 for residual
+    and update), the tip deflection (1) and the compensated misfit (5): 27.
+    539 for 64 modes.  The kernel issues more (fe_fp32_ops_per_step): the
+    increment form with compensated updates for the lowest modes and the
     group's redundant Newton solve and tip sum."""
-    return 10 * n + 27
+    return 8 * n + 27
 
 
 def fe_fp32_ops_per_step() -> int:
     """FP32 add/mul/fma instructions per particle per step of the FP32 FE
     kernel (DMT law, 64 modes on 8 lanes of 8 mode slots), counted from its
-    source.  Per lane: the force history term 1; per mode slot the increment
-    4 (+1 for slot 0's low word), the predicted tip term 4 compensated / 3
-    plain, the update 1 + 8 compensated (two Kahan sums) / 1 + 2 plain, slot
-    0 compensated and slots 1-7 plain; the group sum of the tip deflection 3;
-    one Newton step 15 (gap 1 + law 4.5, residual 2, update 2, gap 1 + law
-    4.5; the law's constant products hoisted, contact and free branches 5
-    and 4).  Lane 0 alone: the tip deflection and the compensated misfit 6.
-    ncu's FFMA + FADD + FMUL thread-instruction counters on a 10-cycle swarm
-    give 846 per particle-step (365 + 367 + 114) against these 862."""
-    slot0 = 4 + 1 + 4 + 1 + 8
-    slot_plain = 4 + 3 + 1 + 2
-    per_lane = 1 + slot0 + 7 * slot_plain + 3 + 15
+    source.  Per lane: the force history term 1; slot 0 (compensated): the
+    increment 5 (drive and past-force terms 2, state terms 2, b1's low word
+    1), the predicted coordinate 3, the update 1 + 8 (two Kahan sums); slots
+    1-7: delta + increment 4, the predicted coordinate 1, the update 2; the
+    lane's tip tree 7 and the group's sum 3; one Newton step 15 (gap 1 + law
+    4.5, residual 2, update 2, gap 1 + law 4.5; the law's constant products
+    hoisted, contact and free branches 5 and 4).  Lane 0 alone: the tip
+    deflection and the compensated misfit 6."""
+    slot0 = 5 + 3 + 1 + 8
+    slot_plain = 4 + 1 + 2
+    per_lane = 1 + slot0 + 7 * slot_plain + 7 + 3 + 15
     return 8 * per_lane + 6
 
 

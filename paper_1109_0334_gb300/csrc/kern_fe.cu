@@ -13,8 +13,15 @@
 // 1e-3 errors of the resonant response.
 //
 // Layout: AFM_FE_LANES lanes per particle, each lane owns modes
-// lane, lane + 8, ...; the tip deflection is a group sum (3 shuffles), the
-// Newton solve for the tip force runs redundantly in the group's lanes.
+// lane, lane + 8, ... and holds their step coefficients in registers; the
+// tip deflection is a group sum (3 shuffles), the Newton solve for the tip
+// force runs redundantly in the group's lanes.
+//
+// The kernel carries each mode scaled by its tip displacement, w_i =
+// phi_i(tip) z_i.  The recursion is linear and homogeneous in (z_i, delta_i),
+// so w_i obeys it with g_i and f_i multiplied by phi_i(tip) and b1_i, d2_i
+// unchanged, and the tip deflection is the plain sum of the w_i: one add per
+// mode instead of a product, and no per-step fetch of phi_i(tip).
 #include <type_traits>
 
 #include "afm_device.cuh"
@@ -33,13 +40,6 @@ constexpr int FE_MIN_BLOCKS = 8;   // caps registers at 128 per thread
 template <typename T>
 struct FeLanes {
     static constexpr int value = sizeof(T) == 8 ? 32 : AFM_FE_LANES;
-};
-
-// Per-mode step coefficients, one 16-byte-aligned record per mode so that a
-// lane fetches them with one vector load.
-template <typename T>
-struct alignas(16) FeQ4 {
-    T b1, d2, g, f;
 };
 
 // Which mode slots of a lane take compensated updates.  FP64: all.  FP32:
@@ -95,18 +95,15 @@ __device__ __forceinline__ void fe_force(const Coef<T>& c, T d, T& Fv, T& dF) {
     }
 }
 
-// sum_j pt_j zp_j (the predicted tip deflection of a lane's mode slots) as a
-// pairwise tree: the products of a pair meet in one fma, the pairs' sums in
-// a balanced tree -- a dependency chain of log2(N) + 2 operations instead of
-// N fmas.
+// sum_j wp_j (the predicted tip deflection of a lane's mode slots) as a
+// pairwise tree: a dependency chain of log2(N) adds instead of N.
 template <typename T, int N>
-__device__ __forceinline__ T fe_dot(const T* pt, const T* zp) {
-    T s[(N + 1) / 2];
+__device__ __forceinline__ T fe_sum(const T* wp) {
+    T s[N];
 #pragma unroll
-    for (int k = 0; k < N / 2; ++k) s[k] = fma(pt[2 * k], zp[2 * k], pt[2 * k + 1] * zp[2 * k + 1]);
-    if (N % 2) s[N / 2] = pt[N - 1] * zp[N - 1];
+    for (int k = 0; k < N; ++k) s[k] = wp[k];
 #pragma unroll
-    for (int w = (N + 1) / 2; w > 1; w = (w + 1) / 2) {
+    for (int w = N; w > 1; w = (w + 1) / 2) {
 #pragma unroll
         for (int k = 0; k < w / 2; ++k) s[k] = s[2 * k] + s[2 * k + 1];
         if (w % 2) s[w / 2] = s[w - 1];
@@ -141,21 +138,8 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
     constexpr int FEM = FEN / FEL;               // modes per lane
     constexpr int FE_PPB = FE_THREADS / FEL;     // particles per block
     extern __shared__ __align__(16) unsigned char fe_smem[];
-    FeQ4<T>* cq = reinterpret_cast<FeQ4<T>*>(fe_smem);
-    T* cpt = reinterpret_cast<T*>(cq + FEN);
-    T* cb1lo = cpt + FEN;
-    T* tab = cb1lo + FEN;
+    T* tab = reinterpret_cast<T*>(fe_smem);
     const int tid = threadIdx.x, lane = tid & (FEL - 1), grp = tid / FEL;
-    for (int i = tid; i < FEN; i += blockDim.x) {
-        FeQ4<T> c4;
-        c4.b1 = (T)F.b1[i];
-        c4.d2 = (T)F.d2[i];
-        c4.g = (T)F.g[i];
-        c4.f = (T)F.f[i];
-        cq[i] = c4;
-        cpt[i] = (T)F.pt[i];
-        cb1lo[i] = (T)(F.b1[i] - (double)c4.b1);
-    }
     fe_table<T>(F, tab);
     const int D = F.pm.D;
     int p = blockIdx.x * FE_PPB + grp;
@@ -214,16 +198,26 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
     const Coef<T> cfc = make_coef<T, T>(pm, x);
     __syncthreads();
 
-    // ---- modal state of this lane
+    // ---- this lane's modes: coefficients and tip-scaled state
+    T b1[FEM], d2[FEM], gq[FEM], fq[FEM];
     T z[FEM], dz[FEM], cz[FEM], cdz[FEM];
 #pragma unroll
     for (int j = 0; j < FEM; ++j) {
         const int i = lane + FEL * j;
-        z[j] = (T)F.z0[i];
-        dz[j] = (T)F.dz0[i];
+        const double pt = F.pt[i];
+        b1[j] = (T)F.b1[i];
+        // the uncompensated slots take 1 + d2, see the step below
+        d2[j] = fe_comp<T>(j) ? (T)F.d2[i] : (T)(1.0 + F.d2[i]);
+        gq[j] = (T)(F.g[i] * pt);
+        fq[j] = (T)(F.f[i] * pt);
+        z[j] = (T)(F.z0[i] * pt);
+        dz[j] = (T)(F.dz0[i] * pt);
         cz[j] = (T)0;
         cdz[j] = (T)0;
     }
+    // the low word of the lowest mode's b1 (the resonant frequency must be
+    // represented to ~1e-12); zero in FP64
+    const T b1lo = (T)(F.b1[lane] - (double)b1[0]);
     const T Zc = (T)F.Zc, ctip = (T)F.ctip;
     T Fn, Fm, dF;
     fe_force<FORCE, T>(cfc, Zc + (T)F.utip0, Fn, dF);
@@ -244,21 +238,20 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
         if (U != nullptr && lane == 0 && n + 1 < F.n_steps) Unext = (T)U[n + 1];
         const T G = tab[jn];
         const T Fo = (T)2 * Fn + Fm;
-        T incs[FEM], cfs[FEM], pts[FEM], zps[FEM];
+        // the drive and past-force terms first: they wait on no state update
+        // of the previous step.  Compensated slots form the increment; the
+        // others form delta_n + increment in one sum, with (1 + d2) dz.
+        T incs[FEM], zps[FEM];
 #pragma unroll
         for (int j = 0; j < FEM; ++j) {
-            const int i = lane + FEL * j;
-            const FeQ4<T> c4 = cq[i];
-            T inc = fma(c4.b1, z[j], c4.d2 * dz[j]);
-            if (j == 0) inc = fma(cb1lo[i], z[j], inc);
-            inc = fma(c4.g, G, inc);
-            inc = fma(c4.f, Fo, inc);
+            T inc = fma(fq[j], Fo, gq[j] * G);
+            inc = fma(d2[j], dz[j], inc);
+            if (j == 0) inc = fma(b1lo, z[j], inc);
+            inc = fma(b1[j], z[j], inc);
             incs[j] = inc;
-            cfs[j] = c4.f;
-            pts[j] = cpt[i];
-            zps[j] = fe_comp<T>(j) ? z[j] + ((dz[j] + inc) - cz[j]) : z[j] + (dz[j] + inc);
+            zps[j] = fe_comp<T>(j) ? z[j] + ((dz[j] + inc) - cz[j]) : z[j] + inc;
         }
-        T tsum = fe_dot<T, FEM>(pts, zps);
+        T tsum = fe_sum<T, FEM>(zps);
 #pragma unroll
         for (int o = FEL / 2; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
         T Fp;
@@ -268,10 +261,10 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
 #pragma unroll
         for (int j = 0; j < FEM; ++j) {
             if (fe_comp<T>(j)) {
-                kahan_add(dz[j], cdz[j], fma(cfs[j], Fp, incs[j]));
+                kahan_add(dz[j], cdz[j], fma(fq[j], Fp, incs[j]));
                 kahan_add(z[j], cz[j], dz[j]);
             } else {
-                dz[j] = dz[j] + fma(cfs[j], Fp, incs[j]);
+                dz[j] = fma(fq[j], Fp, incs[j]);
                 z[j] = z[j] + dz[j];
             }
         }
@@ -363,7 +356,7 @@ cudaError_t fe_dispatch(int force, Fn&& f) {
 
 template <typename T>
 size_t fe_smem(const FeConst& F) {
-    return sizeof(FeQ4<T>) * (size_t)FEN + sizeof(T) * (2 * (size_t)FEN + (size_t)F.spc);
+    return sizeof(T) * (size_t)F.spc;
 }
 
 template <typename T, typename TU, int MODE, typename... Args>
