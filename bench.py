@@ -403,7 +403,8 @@ def accuracy_vs_oracle(A, spec, U, off, results, golden=GOLDEN_C3):
     ok, ok_p = dchi <= 1.0, (err <= 0.005) | (dchi < -1.0)
     return {"pixels": len(rows),
             "reference": "oracle optimum per pixel (own 256 x 60 swarm, then 12 LM steps from "
-                         "its winner and from the seeded truth; best of the three), FP64 misfit "
+                         "its winner and from the seeded truth; the best of the three refined "
+                         "to convergence in the box by Marquardt's method), FP64 misfit "
                          "re-evaluated on this run's record",
             "frac_dchi2_le_1": float(ok.mean()),
             "frac_param_err_le_0.5pct_determined": float(ok_p.mean()),
@@ -827,9 +828,10 @@ def run_paper_laws(A, W, dev, flush):
 # ---------------------------------------------------------------------------
 def run_c2(A, W, dev, flush, peak_ops, steps=3):
     """One 1024 x 100 inversion of the 3-mode cantilever on the record of
-    the oracle's stored optimum's truth (tests/golden/c2_invert.json; record
-    made on the GPU), its LM-polished counterpart, both against the stored
-    oracle optimum (delta chi^2 on this record), the 16-record comparison,
+    the stored truth (tests/golden/c2_invert.json; record made on the GPU),
+    its LM-polished counterpart, both against the oracle's converged optimum
+    of that record (x_opt; delta chi^2 on this record), the 16-record
+    comparison,
     the fused iteration kernel's roofline, and the wide forward + misfit
     launch (262 144 particles) of the same record."""
     import numpy as np
@@ -879,8 +881,8 @@ def run_c2(A, W, dev, flush, peak_ops, steps=3):
     r_lm = A.decode_result(r_lm[0])
 
     def acc(rr):
-        d, comb, S_ref = _dchi2_and_comb(A, spec, prob, U, rr, gold["x"])
-        e, n_id = determined_error(A, spec, prob, U, gold["x"], list(rr["x"][:D]))
+        d, comb, S_ref = _dchi2_and_comb(A, spec, prob, U, rr, gold["x_opt"])
+        e, n_id = determined_error(A, spec, prob, U, gold["x_opt"], list(rr["x"][:D]))
         return {"dchi2_vs_oracle_optimum": d, "param_err_determined": e,
                 "determined_directions": n_id,
                 "combinations_rel_err_vs_oracle": dict(zip(("H R", "E* sqrt(R)", "a0"), comb)),

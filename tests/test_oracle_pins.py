@@ -819,6 +819,61 @@ def test_lm_polish_descends_and_reaches_the_optimum(orc):
     assert np.all(Ss < 1e-10 * S0)
 
 
+def _coordinate_minimal(orc, c, pm, U, x, S, h=1e-4):
+    """No admissible coordinate step of size h lowers the misfit (the
+    first-order conditions of the box, checked on the misfit alone)."""
+    for d in range(len(x)):
+        for s in (1.0, -1.0):
+            xx = np.array(x, dtype=np.float64)
+            xx[d] += s * h
+            if not 0.0 <= xx[d] <= 1.0:
+                continue
+            Sd = orc.misfit_batch(c, pm, xx.reshape(-1, 1), U)[0]
+            assert Sd >= S * (1 - 1e-12), (d, s, Sd, S)
+
+
+def test_refine_optimum_vs_grid_and_first_order(orc, c1_problem):
+    """The converged optimum on C1's two parameters: at or below the best
+    point of a 201 x 201 brute-force grid of the misfit, no worse than the
+    Levenberg-Marquardt polish from the same start, at or below every point
+    of a fine local grid around it (the valley is curved and soft: the
+    coarse grid's minimiser lies elsewhere along it), and minimal along every
+    coordinate."""
+    w, c, pm, n, xt, U = c1_problem
+    G = 201
+    g1 = np.linspace(0, 1, G)
+    X = np.array(np.meshgrid(g1, g1, indexing="ij")).reshape(2, -1)
+    Sg = orc.misfit_batch(c, pm, X, U)
+    k = int(np.argmin(Sg))
+    x0 = np.array([0.5, 0.5])
+    x, S = orc.refine_optimum(c, pm, U, x0)
+    assert S <= Sg[k] * (1 + 1e-12)
+    _, Sl = orc.lm_polish(c, pm, U, x0.reshape(-1, 1), steps=12)
+    assert S <= Sl[0] * (1 + 1e-12)
+    assert S == pytest.approx(orc.misfit_batch(c, pm, x.reshape(-1, 1), U)[0], rel=1e-15)
+    loc = np.linspace(-0.01, 0.01, 41)
+    XL = np.clip((x[:, None, None] + np.array(np.meshgrid(loc, loc, indexing="ij")))
+                 .reshape(2, -1), 0.0, 1.0)
+    assert S <= orc.misfit_batch(c, pm, XL, U).min() * (1 + 1e-12)
+    _coordinate_minimal(orc, c, pm, U, x, S)
+
+
+def test_refine_optimum_ends_on_the_bound_beyond_the_truth(orc, c1_problem):
+    """With the stiffness truth placed beyond the box (E* twice its upper
+    bound), the constrained optimum lies on that bound: the coordinate ends
+    at exactly 1, the misfit rises into the box along it, and the other
+    coordinate is minimal.  (The refinement is local: it starts in the
+    basin of the bound, as the golden script starts it from swarm winners.)"""
+    w, c, pm, n, _, _ = c1_problem
+    xt = np.array([1.15, 0.5])
+    U = orc.record(c, pm, xt, n, w["record_sub"], w["sigma"], w["seed"])
+    x, S = orc.refine_optimum(c, pm, U, np.array([0.85, 0.5]))
+    assert x[0] == 1.0
+    _, _, b = orc.normal_eq(c, pm, x, U)
+    assert -2.0 * b[0] < 0.0          # the misfit falls outward, rises inward
+    _coordinate_minimal(orc, c, pm, U, x, S)
+
+
 # --------------------------------------------------------------------------
 # Finite-element cantilever (reading R13)
 # --------------------------------------------------------------------------
