@@ -48,12 +48,13 @@ def fp32_ops_per_step(m: int, force: str) -> int:
     """FP32 instructions (add/mul/fma/min/max) per particle per RK4 step of
     the fused forward + misfit kernel, counted from its source:
     accel(): tip sum (m-1), gap (1), force law, per mode 4 (+1 for mode 1's
-    low word); RK4 stage states and slope sums 12m; compensated update 8m;
+    low word); RK4 stage states and slope sums 12m; state update 8 for the
+    lowest mode (compensated) and 2 for each other mode (plain sums);
     tip deflection (m-1); compensated misfit 5."""
     force_ops = {"dmt": 7, "dmt_kv": 9 + (m - 1), "linear_spring": 2, "hooke": 3,
                  "spring_damper": 4 + (m - 1)}[force]
     accel = (m - 1) + 1 + force_ops + 4 * m + 1
-    return 4 * accel + 12 * m + 8 * m + (m - 1) + 5
+    return 4 * accel + 12 * m + 8 + 2 * (m - 1) + (m - 1) + 5
 
 
 def algo_ops_per_step(m: int) -> int:
@@ -63,10 +64,10 @@ def algo_ops_per_step(m: int) -> int:
     reciprocal square root, 4m for the modal accelerations of Eq. 2, 2m
     stage-state and 2m slope-accumulation FMAs] plus the misfit of Eq. 5
     with its compensated sum: 36m + 24 (132 for 3 modes, 60 for 1).  The
-    library issues more (fp32_ops_per_step: its compensated state update and
-    the resonant mode's low word are precision devices of this
-    implementation, not work of the method), so a fraction on this count is
-    the conservative one."""
+    library issues more (fp32_ops_per_step: the resonant mode's compensated
+    state update and low word are precision devices of this implementation,
+    not work of the method), so a fraction on this count is the
+    conservative one."""
     return 36 * m + 24
 
 

@@ -294,9 +294,25 @@ __device__ __forceinline__ void kahan_add(T& x, T& c, T inc) {
     x = t;
 }
 
+// The state update of mode i: compensated or plain by comp_mode.  The plain
+// sum is the compensated one entered with c == 0 (y = inc exactly), which is
+// how kernels holding one mode per lane run it: every lane the compensated
+// form, then c masked to zero (bitwise, by the run-time KConst::cmask) where
+// the lane's mode takes plain sums.  ALL: every mode compensated (the
+// adjoint, whose gradient is more sensitive to the trajectory's rounding
+// than the misfit is).
+template <typename T, bool ALL = false>
+__device__ __forceinline__ void state_add(int i, T& x, T& c, T inc) {
+    if (ALL || comp_mode<T>(i))
+        kahan_add(x, c, inc);
+    else
+        x = add_rn(x, inc);
+}
+
 // One classic RK4 step (h = 6, h/2 = 3, h/6 = 1 in scaled time) with
-// compensated state update.  g0, gh, g1: drive at t, t + h/2, t + h.
-template <typename T, int M, int FORCE>
+// compensated state update (state_add).  g0, gh, g1: drive at t, t + h/2,
+// t + h.
+template <typename T, int M, int FORCE, bool ALLC = false>
 __device__ __forceinline__ void rk4_step(const KConst<T>& K, const Coef<T>& c, T* q, T* v, T* cq,
                                          T* cv, T g0, T gh, T g1) {
     T a[M], qs[M], vs[M], Kq[M], Kv[M];
@@ -329,8 +345,8 @@ __device__ __forceinline__ void rk4_step(const KConst<T>& K, const Coef<T>& c, T
     for (int i = 0; i < M; ++i) {
         Kq[i] = Kq[i] + vs[i];
         Kv[i] = Kv[i] + a[i];
-        kahan_add(q[i], cq[i], Kq[i]);
-        kahan_add(v[i], cv[i], Kv[i]);
+        state_add<T, ALLC>(i, q[i], cq[i], Kq[i]);
+        state_add<T, ALLC>(i, v[i], cv[i], Kv[i]);
     }
 }
 
@@ -397,10 +413,20 @@ __device__ __forceinline__ T integrate_points(const KConst<T>& K, const Coef<T>&
     T S = (T)0, cS = (T)0;
     int j = 0;
     const int spc2 = K.spc2, np = K.np;
+    // the record values of step s are loaded during step s - 1, so that no
+    // step waits for a global-memory load
+    T Ucur[AFM_MAX_POINTS];
+#pragma unroll
+    for (int k = 0; k < AFM_MAX_POINTS; ++k)
+        Ucur[k] = (U != nullptr && n > 0 && k < np) ? (T)U[k] : (T)0;
     for (int s = 0; s < n; ++s) {
         const T g0 = tab[j], gh = tab[j + 1], g1 = tab[j + 2];
         j += 2;
         if (j >= spc2) j = 0;
+        T Unext[AFM_MAX_POINTS];
+#pragma unroll
+        for (int k = 0; k < AFM_MAX_POINTS; ++k)
+            Unext[k] = (U != nullptr && s + 1 < n && k < np) ? (T)U[(size_t)(s + 1) * np + k] : (T)0;
         rk4_step<T, M, FORCE>(K, c, q, v, cq, cv, g0, gh, g1);
         // unrolled to the largest point count (a uniform guard), so that the
         // point deflections schedule alongside the step's arithmetic
@@ -413,7 +439,7 @@ __device__ __forceinline__ T integrate_points(const KConst<T>& K, const Coef<T>&
                 const size_t idx = (size_t)s * np + k;
                 if (defl != nullptr) defl[idx * P + p] = uk;
                 if (U != nullptr) {
-                    const T r = (T)U[idx] - uk;
+                    const T r = Ucur[k] - uk;
                     const T y = fma(r, r, -cS);
                     const T t = add_rn(S, y);
                     cS = sub_rn(sub_rn(t, S), y);
@@ -421,6 +447,8 @@ __device__ __forceinline__ T integrate_points(const KConst<T>& K, const Coef<T>&
                 }
             }
         }
+#pragma unroll
+        for (int k = 0; k < AFM_MAX_POINTS; ++k) Ucur[k] = Unext[k];
     }
     return S;
 }

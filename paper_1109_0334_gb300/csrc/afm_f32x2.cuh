@@ -128,8 +128,13 @@ __device__ __forceinline__ void rk4_step(const ModeC<M>& C, const Coef2& c, floa
     for (int i = 0; i < M; ++i) {
         Kq[i] = add(Kq[i], vs[i]);
         Kv[i] = add(Kv[i], a[i]);
-        kahan_add(q[i], cq[i], Kq[i]);
-        kahan_add(v[i], cv[i], Kv[i]);
+        if (comp_mode<float>(i)) {   // as afm::state_add
+            kahan_add(q[i], cq[i], Kq[i]);
+            kahan_add(v[i], cv[i], Kv[i]);
+        } else {
+            q[i] = add(q[i], Kq[i]);
+            v[i] = add(v[i], Kv[i]);
+        }
     }
 }
 

@@ -19,7 +19,25 @@
 #define AFM_TAB_MAX 4096   // half-step drive phases per period (2 * steps_per_cycle)
 #define AFM_SEG 32         // adjoint checkpoint interval (RK4 steps)
 
+#if defined(__CUDACC__)
+#define AFM_HD __host__ __device__
+#else
+#define AFM_HD
+#endif
+
 namespace afm {
+
+// Which modes take compensated (Kahan) state updates.  FP64: all.  FP32: the
+// lowest mode only.  It carries the resonant response, and its RK4 increment
+// is a small fraction of the state (omega_1 h << 1), so that a plain sum
+// drops low bits of the deflection every step; the higher modes are driven
+// far off resonance, with amplitudes ~(omega_1 / omega_i)^2 / Q of the first
+// mode's, and their plain-sum rounding stays far below FP32 resolution of
+// the tip deflection.
+template <typename T>
+AFM_HD constexpr bool comp_mode(int i) {
+    return sizeof(T) == 8 || i == 0;
+}
 
 enum ForceKind { F_LINEAR = 0, F_DMT = 1, F_DMT_KV = 2, F_HOOKE = 3, F_SPRING_DAMPER = 4 };
 
@@ -39,6 +57,7 @@ struct Coef {
 template <typename T>
 struct KConst {
     T w2[AFM_MAXM], w2lo[AFM_MAXM], wq[AFM_MAXM], gam[AFM_MAXM], tip[AFM_MAXM];
+    T cmask[AFM_MAXM];              // 1: mode i takes compensated sums (comp_mode), else 0
     T q0[AFM_MAXM], v0[AFM_MAXM];
     T Zc;
     double drive_amp, drive_phase;  // g = drive_amp * sin(2 pi j / spc2 + drive_phase)

@@ -96,8 +96,8 @@ __device__ __forceinline__ void rk4_step_tl(const KConst<float>& K, const Coef<f
         for (int i = 0; i < M; ++i) {
             Kq[i] = Kq[i] + vs[i];
             Kv[i] = Kv[i] + a[i];
-            kahan_add(q[i], cq[i], Kq[i]);
-            kahan_add(v[i], cv[i], Kv[i]);
+            state_add(i, q[i], cq[i], Kq[i]);
+            state_add(i, v[i], cv[i], Kv[i]);
         }
     }
 #pragma unroll

@@ -187,6 +187,7 @@ void fill_kconst(const afm_problem& pr, int spc, int n_steps, KConst<T>& K) {
             K.wq[i] = (T)(s.w[i] * tau / pr.Q[i]);
             K.gam[i] = (T)s.gam[i];
             K.tip[i] = (T)1;
+            K.cmask[i] = afm::comp_mode<T>(i) ? (T)1 : (T)0;
             K.q0[i] = drv ? (T)0 : (T)(s.q0[i] / nm);        // drive mode 1 starts at rest
             K.v0[i] = drv ? (T)0 : (T)(s.v0[i] * tau / nm);
         }

@@ -2,9 +2,11 @@
 // the misfit S (Eq. 5) with respect to the normalised force parameters x,
 // through every RK4 step of Eq. 2 (Sec. 3.2), one thread per particle.
 //
-// Forward pass: the RK4 loop of afm_device.cuh, storing the full state
-// (modal deflections, rates and their Kahan compensations) every AFM_SEG
-// steps.  Reverse pass: for each segment, last first, the AFM_SEG steps are
+// Forward pass: the RK4 loop of afm_device.cuh with every mode compensated
+// (the gradient is more sensitive to the trajectory's rounding than the
+// misfit; the forward kernels compensate the lowest mode only), storing the
+// full state (modal deflections, rates and their Kahan compensations) every
+// AFM_SEG steps.  Reverse pass: for each segment, last first, the AFM_SEG steps are
 // recomputed from their checkpoint (bit-identical to the forward pass) while
 // the gap d and gap rate d' of each RK4 stage and the tip deflection after
 // each step are kept in shared memory; then the adjoint state runs back
@@ -66,7 +68,8 @@ __device__ __forceinline__ void rhs_vjp(const KConst<float>& K, const Coef<float
     for (int k = 0; k < 4; ++k) cb[k] = fmaf(Fbar, Fc[k], cb[k]);
 }
 
-// One RK4 step as in rk4_step, recording (d, d') of each stage.
+// One RK4 step as in rk4_step (every mode compensated), recording (d, d') of
+// each stage.
 template <int M, int FORCE>
 __device__ __forceinline__ void rk4_step_rec(const KConst<float>& K, const Coef<float>& c, float* q,
                                              float* v, float* cq, float* cv, float g0, float gh,
@@ -115,8 +118,8 @@ __device__ __forceinline__ void rk4_step_rec(const KConst<float>& K, const Coef<
     for (int i = 0; i < M; ++i) {
         Kq[i] = Kq[i] + vs[i];
         Kv[i] = Kv[i] + a[i];
-        kahan_add(q[i], cq[i], Kq[i]);
-        kahan_add(v[i], cv[i], Kv[i]);
+        state_add<float, true>(i, q[i], cq[i], Kq[i]);
+        state_add<float, true>(i, v[i], cv[i], Kv[i]);
     }
 }
 
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(const KConst<float
         const float g0 = tab[j], gh = tab[j + 1], g1 = tab[j + 2];
         j += 2;
         if (j >= K.spc2) j = 0;
-        rk4_step<float, M, FORCE>(K, c, q, v, cq, cv, g0, gh, g1);
+        rk4_step<float, M, FORCE, true>(K, c, q, v, cq, cv, g0, gh, g1);
         const float r = U[n] - tip_sum<float, M>(q);
         const float y = fmaf(r, r, -cS);
         const float t = add_rn(S, y);
@@ -184,11 +187,16 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(const KConst<float
     S_out[p] = S;
 
     // reverse pass
-    float lq[M], lv[M];
+    // adjoint state with Kahan compensations: like the forward state it takes
+    // per-step increments far smaller than itself over the whole record
+    float lq[M], lv[M], clq[M], clv[M];
 #pragma unroll
-    for (int i = 0; i < M; ++i) lq[i] = lv[i] = 0.f;
-    float cb[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = 0; i < M; ++i) lq[i] = lv[i] = clq[i] = clv[i] = 0.f;
+    // force-coefficient cotangents: FP32 within a segment, folded into FP64
+    // after each (the sum runs over every stage of every step)
+    double cbd[4] = {0.0, 0.0, 0.0, 0.0};
     for (int sg = nseg - 1; sg >= 0; --sg) {
+        float cb[4] = {0.f, 0.f, 0.f, 0.f};
         const int n0 = sg * SEG, n1 = min(N, n0 + SEG);
         const float* ck = ckpt + (size_t)sg * 4 * M * P + p;
 #pragma unroll
@@ -215,14 +223,14 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(const KConst<float
             // misfit term of the state after step n
             const float r = U[n] - sb[8 * ADJ_THREADS];
 #pragma unroll
-            for (int i = 0; i < M; ++i) lq[i] = fmaf(-2.f, r, lq[i]);
+            for (int i = 0; i < M; ++i) kahan_add(lq[i], clq[i], -2.f * r);
             // reverse RK4 step: stage cotangents kb_s (k1..k4 weights 1,2,2,1)
             float k1q[M], k1v[M], k2q[M], k2v[M], k3q[M], k3v[M], oq[M], ov[M];
             float yq[M], yv[M];
 #pragma unroll
             for (int i = 0; i < M; ++i) {
-                yq[i] = lq[i];
-                yv[i] = lv[i];
+                yq[i] = 0.f;   // the step's increment of the adjoint state
+                yv[i] = 0.f;
                 k1q[i] = lq[i];
                 k1v[i] = lv[i];
                 k2q[i] = 2.f * lq[i];
@@ -261,16 +269,18 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(const KConst<float
             rhs_vjp<M, FORCE>(K, c, sb[0], sb[1 * ADJ_THREADS], k1q, k1v, oq, ov, cb);
 #pragma unroll
             for (int i = 0; i < M; ++i) {
-                lq[i] = yq[i] + oq[i];
-                lv[i] = yv[i] + ov[i];
+                kahan_add(lq[i], clq[i], yq[i] + oq[i]);
+                kahan_add(lv[i], clv[i], yv[i] + ov[i]);
             }
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cbd[k] += (double)cb[k];
     }
     double J[4][AFM_MAXD];
     coef_jacobian<float>(K, xd, J);
     for (int d = 0; d < K.D; ++d) {
         double g = 0.0;
-        for (int k = 0; k < 4; ++k) g += (double)cb[k] * J[k][d];
+        for (int k = 0; k < 4; ++k) g += cbd[k] * J[k][d];
         G[(size_t)d * P + p] = (float)g;
     }
 }

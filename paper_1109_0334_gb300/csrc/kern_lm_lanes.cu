@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(kLaneThreads) sens_modes_kernel(
     }
     const float w2 = K.w2[k], w2lo = k == 0 ? K.w2lo[0] : 0.f, wq = K.wq[k], gam = K.gam[k];
     float q = K.q0[k], v = K.v0[k], cq = 0.f, cv = 0.f, tq = 0.f, tv = 0.f;
+    const int cmb = K.cmask[k] != 0.f ? -1 : 0;
     double aH[D], ab = 0.0;
     float hc[D], bc = 0.f;
 #pragma unroll
@@ -288,6 +289,12 @@ __global__ void __launch_bounds__(kLaneThreads) sens_modes_kernel(
         Kv = Kv + a4;
         kahan_add(q, cq, Kq);
         kahan_add(v, cv, Kv);
+        // modes taking plain sums hold their compensation at zero
+        // (state_add; the run-time mask KConst::cmask as bits)
+        if (k > 0) {
+            cq = __int_as_float(__float_as_int(cq) & cmb);
+            cv = __int_as_float(__float_as_int(cv) & cmb);
+        }
         // the tangent of direction e for this lane's mode
         float ta = tl_lane(P1, Jc, w2, wq, tq, tv, dbase);
         float tKq = tv, tKv = ta;

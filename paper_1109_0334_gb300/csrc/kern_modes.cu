@@ -36,6 +36,7 @@ namespace {
 template <int S>
 struct Slots {
     float w2[S], w2lo[S], wq[S], gam[S], tip[S];
+    int cmb[S];
 };
 
 // The force-independent part of accel's acceleration for one slot, then the
@@ -107,6 +108,7 @@ __device__ __forceinline__ float integrate_modes(const KConst<float>& K, const C
         C.wq[k] = real ? K.wq[i] : 0.f;
         C.gam[k] = real ? K.gam[i] : 0.f;
         C.tip[k] = real ? 1.f : 0.f;
+        C.cmb[k] = (real && K.cmask[i] != 0.f) ? -1 : 0;
         q[k] = real ? K.q0[i] : 0.f;
         v[k] = real ? K.v0[i] : 0.f;
         cq[k] = 0.f;
@@ -200,6 +202,12 @@ __device__ __forceinline__ float integrate_modes(const KConst<float>& K, const C
             Kv = Kv + a4;
             kahan_add(q[k], cq[k], Kq);
             kahan_add(v[k], cv[k], Kv);
+            // modes taking plain sums hold their compensation at zero
+            // (state_add; C.cmb: the run-time mask KConst::cmask as bits)
+            if (lane * S + k > 0) {
+                cq[k] = __int_as_float(__float_as_int(cq[k]) & C.cmb[k]);
+                cv[k] = __int_as_float(__float_as_int(cv[k]) & C.cmb[k]);
+            }
         }
     }
     return S2;
@@ -216,7 +224,7 @@ __device__ __forceinline__ unsigned long long modes_key(float S, int p) {
 // together, and lane 0 updates the bests.  Groups beyond P run the last
 // particle without storing (the shuffles need every lane).
 template <int M, int FORCE, int L, int NP>
-__global__ void invert_modes_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
+__global__ void __launch_bounds__(32, 1) invert_modes_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
                                     const float* __restrict__ U, float* __restrict__ history,
                                     int it) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

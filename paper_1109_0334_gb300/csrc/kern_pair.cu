@@ -86,8 +86,8 @@ __device__ __forceinline__ void rk4_step_pair(const KConst<float>& K, const Coef
         Kv = fmaf(2.f, a2[i], Kv);
         Kv = fmaf(2.f, a3[i], Kv);
         Kv = Kv + a4[i];
-        kahan_add(q[i], cq[i], Kq);
-        kahan_add(v[i], cv[i], Kv);
+        state_add(i, q[i], cq[i], Kq);
+        state_add(i, v[i], cv[i], Kv);
     }
 }
 
@@ -130,7 +130,7 @@ __device__ __forceinline__ unsigned long long pair_key(float S, int p) {
 // integrate it together; the even lane updates the bests.  Pairs beyond P run
 // the last particle without storing (the shuffles need every lane).
 template <int M, int FORCE>
-__global__ void invert_pair_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
+__global__ void __launch_bounds__(32, 1) invert_pair_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
                                    const float* __restrict__ U, float* __restrict__ history,
                                    int it) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

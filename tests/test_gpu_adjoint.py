@@ -43,11 +43,15 @@ def test_adjoint_vs_oracle_complex_step(orc, afm, name, cycles, P):
     S, G = afm.adjoint(prob, xt, Ut)
     _, S_fwd = afm.forward_batch(prob, xt, Ut, want_defl=False)
     torch.cuda.synchronize()
-    assert torch.equal(S, S_fwd)   # the adjoint's forward pass is the forward kernel's arithmetic
+    # the adjoint integrates with every mode compensated, the forward kernel
+    # the lowest mode only: the two misfits agree within the misfit
+    # tolerance, and the adjoint's is the oracle's to the same bound
+    torch.testing.assert_close(S, S_fwd, rtol=1e-4, atol=0)
     G = G.cpu().numpy()
     c, pm = orc.make_case(spec), orc.make_pmap(spec)
     for p in range(P):
         S_o, g_o = orc.grad_cs(c, pm, x[:, p].astype(np.float64), U_m)
+        assert abs(float(S[p]) - S_o / NM ** 2) <= 1e-4 * S_o / NM ** 2
         g_o = g_o / NM ** 2
         scale = np.max(np.abs(g_o))
         assert np.max(np.abs(G[:, p] - g_o)) <= GRAD_TOL * scale, (p, G[:, p], g_o)
