@@ -111,10 +111,11 @@ __device__ __forceinline__ T fe_sum(const T* wp) {
     return s[0];
 }
 
-// z = base + cz F(Zc + z) by Newton from z = base.
+// z = base + cz F(Zc + z) by Newton from z = base + cz Fguess.
 template <int FORCE, typename T>
-__device__ __forceinline__ T fe_newton(const Coef<T>& c, T Zc, T base, T cz, int iters, T& Fz) {
-    T z = base, dF;
+__device__ __forceinline__ T fe_newton(const Coef<T>& c, T Zc, T base, T cz, T Fguess, int iters,
+                                       T& Fz) {
+    T z = fma(cz, Fguess, base), dF;
     for (int it = 0; it < iters; ++it) {
         fe_force<FORCE, T>(c, Zc + z, Fz, dF);
         const T phi = z - base - cz * Fz;
@@ -224,10 +225,13 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
     fe_force<FORCE, T>(cfc, Zc + (T)F.utipm, Fm, dF);
     T S = (T)0, cS = (T)0, u2 = (T)0;
     const int spc = F.spc;
-    // the tip coupling is a contraction of ~1e-4: Newton from the uncoupled
-    // deflection is converged to FP32 rounding after one step (a second one
-    // changes no result in the tests' cases), to FP64 after 3
-    const int newton_it = sizeof(T) == 8 ? 3 : 1;
+    // the tip coupling is a contraction of ~1e-4.  FP32: Newton from the
+    // uncoupled deflection is converged to FP32 rounding after one step (a
+    // second one changes no result in the tests' cases).  FP64: from the
+    // deflection the step's current force would give (the predictor base +
+    // cz F_n, off by cz times one step's change of the force), converged
+    // to FP64 after 2
+    const int newton_it = sizeof(T) == 8 ? 2 : 1;
     int jn = 0;
     // the record value of step n is loaded during step n - 1, so that no
     // step waits for a global-memory load
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
 #pragma unroll
         for (int o = FEL / 2; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
         T Fp;
-        fe_newton<FORCE, T>(cfc, Zc, tsum, ctip, newton_it, Fp);
+        fe_newton<FORCE, T>(cfc, Zc, tsum, ctip, sizeof(T) == 8 ? Fn : (T)0, newton_it, Fp);
         // compensated updates of both the increment and the modal coordinate
         // (in FP32 for the lowest modes only)
 #pragma unroll
