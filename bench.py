@@ -1100,6 +1100,8 @@ def run_ours(args):
         rate, threads, desc, _ = oracle_c3_sample(spec)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
                "extrapolated_ms_per_batch": units_rank / rate * 1e3}
+        if not args.no_c2:
+            cpu["other_workloads"] = oracle_per_config(W, threads)
 
     if rank == 0:
         ok = sum(1 for r in out_res if r["status"] == 0)
@@ -1177,6 +1179,71 @@ def oracle_c3_sample(spec, n_sub: int = 32):
             f"is extrapolated from this rate to all {spec['n_pix']} pixels x "
             f"{spec['iters'] + 1} evaluations")
     return units / wall, threads, desc, wall
+
+
+def oracle_per_config(W, threads: int) -> dict:
+    """The oracle beside the GPU numbers of the other workloads, each on a
+    bounded sample timed on the host cores (OpenMP over particles) and
+    extrapolated where stated: C1 the full inversion; C2 one whole-swarm
+    evaluation, extrapolated to its 101; C4 one whole-swarm evaluation and
+    the complex-step gradients of the 32 particles its polish takes; C5 one
+    swarm pass of 64 of the 8192 particles, extrapolated to 8192 x 61.
+    Records are the oracle's own (seeded truths, dt/4 integration, noise)."""
+    import numpy as np
+    from oracle import oracle as O
+    O.build()
+    O.set_threads(threads)
+
+    def setup(name):
+        spec = W.get(name)
+        c, pm = O.make_case(spec), O.make_pmap(spec)
+        n = W.n_steps(spec)
+        xt = O.truth_x(pm.D, spec["seed"])
+        U = O.record(c, pm, xt, n, spec["record_sub"], spec["sigma"], spec["seed"])
+        U = (U / 1e-9).astype(np.float32).astype(np.float64) * 1e-9
+        x, _ = O.pso_init(spec["P"], pm.D, spec["seed"], 0)
+        return spec, c, pm, n, U, np.ascontiguousarray(x)
+
+    out = {}
+    spec, c, pm, n, U, x = setup("c1")
+    t0 = time.perf_counter()
+    O.invert(c, pm, U, spec["P"], spec["iters"], spec["w"], spec["c1"], spec["c2"], spec["seed"])
+    wall = time.perf_counter() - t0
+    units = spec["P"] * (spec["iters"] + 1) * n
+    out["c1"] = {"value": units / wall, "unit": UNIT, "ms_per_inversion": wall * 1e3,
+                 "sample": f"the full inversion ({spec['P']} particles x {spec['iters']} "
+                           f"updates, {n} steps)"}
+    for name in ("c2", "c4"):
+        spec, c, pm, n, U, x = setup(name)
+        t0 = time.perf_counter()
+        O.misfit_batch(c, pm, x, U)
+        wall = time.perf_counter() - t0
+        rate = x.shape[1] * n / wall
+        iters = 100 if name == "c4" else spec["iters"]
+        out[name] = {"value": rate, "unit": UNIT,
+                     "extrapolated_ms_per_plain_inversion": x.shape[1] * (iters + 1) * n / rate * 1e3,
+                     "sample": f"one whole-swarm evaluation ({x.shape[1]} particles, {n} steps), "
+                               f"{wall:.2f} s wall, extrapolated to {iters + 1} evaluations"}
+        if name == "c4":
+            t0 = time.perf_counter()
+            for p in range(32):
+                O.grad_cs(c, pm, x[:, p].copy(), U)
+            g_wall = time.perf_counter() - t0
+            out[name]["ms_per_gradient"] = g_wall / 32 * 1e3
+            out[name]["sample"] += (f"; complex-step gradients of 32 particles, {g_wall:.2f} s "
+                                    f"wall (one particle at a time)")
+    spec, c, pm, n, U, x = setup("c5")
+    xs = np.ascontiguousarray(x[:, :64])
+    t0 = time.perf_counter()
+    O.misfit_batch(c, pm, xs, U)
+    wall = time.perf_counter() - t0
+    rate = xs.shape[1] * n / wall
+    out["c5"] = {"value": rate, "unit": UNIT,
+                 "extrapolated_ms_per_inversion": spec["P"] * (spec["iters"] + 1) * n / rate * 1e3,
+                 "sample": f"one swarm pass of 64 of the {spec['P']} particles ({n} steps), "
+                           f"{wall:.2f} s wall, extrapolated to {spec['P']} particles x "
+                           f"{spec['iters'] + 1} evaluations"}
+    return out
 
 
 def run_reference(args):
