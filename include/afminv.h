@@ -227,13 +227,17 @@ afm_status afm_profile_read(afm_ctx* ctx, double* ms, int* launches);
 
 /* ---- forward problem FP (Sec. 2.2; Eq. 2; RK4 of Sec. 3.2) --------------
  * P candidate parameter sets x [D][P] (device, normalised) are integrated for
- * prob->n_steps steps in FP32.  Outputs (each optional, NULL to skip):
+ * prob->n_steps steps in FP32: the lowest (resonant) mode's state with
+ * Kahan-compensated updates, the others with plain sums (FE beam: the
+ * lowest 8 modes compensated), the misfit compensated.  Outputs (each
+ * optional, NULL to skip):
  *   defl [n_steps][P]  tip deflection after every step (device)
  *   S    [P]           misfit against U (device; requires U [n_steps])
  * A misfit that is not finite (a diverging candidate) is stored as +inf. */
 afm_status afm_forward_batch(afm_ctx* ctx, const afm_problem* prob, const float* x, int P,
                              float* defl, const float* U, float* S, void* stream);
-/* The same in FP64 throughout (x, defl, U, S all double). */
+/* The same in FP64 throughout (x, defl, U, S all double; every mode
+ * compensated). */
 afm_status afm_forward_batch_f64(afm_ctx* ctx, const afm_problem* prob, const double* x,
                                  int P, double* defl, const double* U, double* S,
                                  void* stream);
@@ -308,11 +312,13 @@ afm_status afm_invert(afm_ctx* ctx, const afm_problem* prob, const float* U,
                       afm_result* result, float* history, void* stream);
 
 /* ---- gradient of the misfit (discrete adjoint) --------------------------
- * For P parameter sets x [D][P] (device, normalised): S [P] (as
- * afm_forward_batch) and dS_dx [D][P] = d S / d x, the exact derivative of the
- * FP32 RK4 recurrence (Eq. 2, Sec. 3.2) and compensated sum (Eq. 5), by the
- * discrete adjoint: the state is checkpointed every 32 steps and each
- * 32-step segment is recomputed during the reverse sweep.  The Kahan
+ * For P parameter sets x [D][P] (device, normalised): S [P] and dS_dx [D][P]
+ * = d S / d x, the exact derivative of the FP32 RK4 recurrence (Eq. 2, Sec.
+ * 3.2) and compensated sum (Eq. 5), by the discrete adjoint: the state is
+ * checkpointed every 32 steps and each 32-step segment is recomputed during
+ * the reverse sweep.  The adjoint compensates the state update of every
+ * mode (afm_forward_batch: the lowest mode only), so its S agrees with
+ * afm_forward_batch's within 1e-4 relative, not bit for bit.  The Kahan
  * compensation is treated as exact addition.  workspace: device,
  * >= afm_adjoint_workspace_size (the checkpoints: ceil(n_steps/32) x 4 x
  * modes x P floats). */
