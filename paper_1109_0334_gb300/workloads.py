@@ -43,8 +43,10 @@ WORKLOADS = {
                # 8 while they fit the GPU's sub-partitions, and reach the
                # optimum far more often: a sweep over 16 records put 16 of 16
                # at delta chi^2 <= 1 against 13 of 16 with 8 candidates; 3
-               # updates and 6 steps keep 16 of 16, within 0.02 of the best)
-               lm_polish=dict(iters=3, polish_k=64, polish_steps=6, n_cand=8),
+               # updates and 5 steps keep 16 of 16 within 0.03 of the best,
+               # as do 4 steps, but 4 steps left two C4 records 30 variances
+               # off after 4 updates)
+               lm_polish=dict(iters=3, polish_k=64, polish_steps=5, n_cand=8),
                **_CANTILEVER, **_PSO),
     # 4096 independent pixels, 20..200 cycles each, 256 particles x 60 updates.
     "c3": dict(name="4096 pixels, 3-mode EB DMT, 256 particles x 60 updates",
@@ -64,7 +66,7 @@ WORKLOADS = {
                model="modal_eb", n_modes=3, spc=256, cycles=100, force="dmt_kv",
                free=[_E, _H, _R, _A0, _ETA], fixed=[0.0, 0.0, 0.0, 0.0, 0.0],
                P=1024, iters=40, polish_k=32, polish_steps=20, seed=SEED_BASE + 4,
-               lm_polish=dict(iters=3, polish_k=64, polish_steps=6, n_cand=8),
+               lm_polish=dict(iters=3, polish_k=64, polish_steps=5, n_cand=8),
                **_CANTILEVER, **_PSO),
     # 32-element Hermite FE beam, Newmark beta = 1/4.
     "c5": dict(name="FE Hermite 32 elements DMT, 4 unknowns, 8192 particles x 60 updates",
