@@ -11,7 +11,7 @@
 // partial sums, so every lane holds the same deflection and evaluates the
 // tip force itself.  For a rate-free law the forces of stages 1 and 2 depend
 // on the step's start state only, and those of stages 3 and 4 only on the
-// forces of stages 1 and 2: two rounds of shuffles per step.
+// forces of stages 1 and 2: two shuffle exchanges per step.
 //
 // The partial sums meet in the order of the one-lane kernels ((q0 + q1) + q2
 // for three modes, q0 + q1 for two) and every per-mode operation is
@@ -125,7 +125,7 @@ __device__ __forceinline__ float integrate_modes(const KConst<float>& K, const C
         float qs2[S];
 #pragma unroll
         for (int k = 0; k < S; ++k) qs2[k] = fmaf(3.f, v[k], q[k]);
-        // round 1: the step's start deflection (the previous step's output)
+        // first exchange: the step's start deflection (the previous step's output)
         // and the stage-2 deflection
         float u1, u2;
         if constexpr (POINTS) {
@@ -182,7 +182,7 @@ __device__ __forceinline__ float integrate_modes(const KConst<float>& K, const C
             vs3[k] = fmaf(3.f, a2[k], v[k]);
             qs4[k] = fmaf(6.f, vs3[k], q[k]);
         }
-        // round 2: stage-3 and stage-4 deflections
+        // second exchange: stage-3 and stage-4 deflections
         const float u3 = group_sum<L>(slot_sum<S>(qs3));
         const float u4 = group_sum<L>(slot_sum<S>(qs4));
         const float F3 = tip_force<FORCE, float>(c, K.Zc + u3, 0.f);
