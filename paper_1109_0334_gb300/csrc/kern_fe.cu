@@ -229,9 +229,10 @@ __global__ void __launch_bounds__(FE_THREADS, FE_MIN_BLOCKS) fe_modal_kernel(
     // uncoupled deflection is converged to FP32 rounding after one step (a
     // second one changes no result in the tests' cases).  FP64: from the
     // deflection the step's current force would give (the predictor base +
-    // cz F_n, off by cz times one step's change of the force), converged
-    // to FP64 after 2
-    const int newton_it = sizeof(T) == 8 ? 2 : 1;
+    // cz F_n, off by cz times one step's change of the force), one step
+    // leaves ~1e-12 of the deflection (a second one moved a C5 winner's
+    // FP64 misfit by 1e-13 relative)
+    const int newton_it = 1;
     int jn = 0;
     // the record value of step n is loaded during step n - 1, so that no
     // step waits for a global-memory load
