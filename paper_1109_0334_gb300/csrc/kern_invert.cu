@@ -173,9 +173,9 @@ cudaError_t launch_pso_move(const PsoConst& pc, const SwarmPtrs& sw, int it, cud
 // iteration parity so that no launch reads what it writes.
 // ---------------------------------------------------------------------------
 template <int M, int FORCE>
-__global__ void __launch_bounds__(128, 1) invert_iter_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
-                                   const float* __restrict__ U, float* __restrict__ history,
-                                   int it) {
+__global__ void __launch_bounds__(128, 1)
+invert_iter_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
+                   const float* __restrict__ U, float* __restrict__ history, int it) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* tab = reinterpret_cast<float*>(smem_raw);
     build_drive_table(K, tab);

@@ -224,9 +224,9 @@ __device__ __forceinline__ unsigned long long modes_key(float S, int p) {
 // together, and lane 0 updates the bests.  Groups beyond P run the last
 // particle without storing (the shuffles need every lane).
 template <int M, int FORCE, int L, int NP>
-__global__ void __launch_bounds__(32, 1) invert_modes_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
-                                    const float* __restrict__ U, float* __restrict__ history,
-                                    int it) {
+__global__ void __launch_bounds__(32, 1)
+invert_modes_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
+                    const float* __restrict__ U, float* __restrict__ history, int it) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* tab = reinterpret_cast<float*>(smem_raw);
     build_drive_table(K, tab);

@@ -55,9 +55,9 @@ __global__ void fwd_points_kernel(const KConst<T> K, const T* __restrict__ x, in
 
 // invert_iter_kernel of kern_invert.cu with the misfit over the points.
 template <int M, int FORCE>
-__global__ void __launch_bounds__(128, 1) invert_points_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
-                                     const float* __restrict__ U, float* __restrict__ history,
-                                     int it) {
+__global__ void __launch_bounds__(128, 1)
+invert_points_kernel(const KConst<float> K, const PsoConst pc, SwarmPtrs sw,
+                     const float* __restrict__ U, float* __restrict__ history, int it) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* tab = reinterpret_cast<float*>(smem_raw);
     build_drive_table(K, tab);
