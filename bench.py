@@ -1127,7 +1127,7 @@ def run_ours(args):
                 "frac_pixels_meeting": polished["accuracy_vs_oracle"]["frac_meeting_both"],
                 "criterion": "delta chi^2 <= 1 against the oracle's optimum and <= 0.5 % "
                              "parameter error along every direction the record determines to "
-                             "0.5 % (32-pixel subset)"},
+                             f"0.5 % ({polished['accuracy_vs_oracle']['pixels']}-pixel subset)"},
             "lm_polished_batch": polished,
         }
         out.update(extras)

@@ -30,13 +30,12 @@ def c2_invert():
                           spec["c2"], spec["seed"])
     # the converged optimum (reference of the accuracy criterion): 12
     # Levenberg-Marquardt steps from the swarm's winner and from the seeded
-    # truth, the lowest of the three points refined to convergence in the box
+    # truth, each of the three points refined to convergence in the box, the
+    # lowest kept
     starts = np.array([np.asarray(x, dtype=np.float64), np.asarray(xt, dtype=np.float64)]).T.copy()
     xo, So = O.lm_polish(c, pm, U_m, starts, steps=12)
-    cands = [(float(S), np.asarray(x, dtype=np.float64))] + \
-        [(float(So[k]), xo[:, k]) for k in range(2)]
-    _, x_best = min(cands, key=lambda t: t[0])
-    x_opt, S_opt = O.refine_optimum(c, pm, U_m, x_best)
+    cands = [np.asarray(x, dtype=np.float64), xo[:, 0], xo[:, 1]]
+    x_opt, S_opt = min((O.refine_optimum(c, pm, U_m, xc) for xc in cands), key=lambda t: t[1])
     return dict(workload="c2", x=[float(v) for v in x], S_m2=float(S),
                 x_opt=[float(v) for v in x_opt], S_opt_m2=float(S_opt),
                 sumU2_m2=float(np.sum(U_m ** 2)), truth_x=[float(v) for v in xt],
@@ -67,15 +66,17 @@ def c4_invert():
                 oracle_seconds=time.time() - t, threads=O.get_threads())
 
 
-def c3_subset(n_sub: int = 32):
+def c3_subset(n_sub: int = 64):
     """The oracle's optimum of each of the first n_sub pixels of the
     4096-pixel batch (their seeded truths, lengths and noise, records made by
     the oracle): its own swarm of the batch configuration (256 particles x
     60 updates, Philox pixel word = pixel index), then 12 Levenberg-Marquardt
     steps from that winner and from the seeded truth (an input of the
-    workload); the lowest misfit of the three, refined to convergence within
-    the parameter box (refine_optimum: the fixed-ladder LM polish can stop
-    short in a flat, curved valley or on a bound), is the stored optimum."""
+    workload); each of the three refined to convergence within the
+    parameter box (refine_optimum: the fixed-ladder LM polish can stop short
+    in a flat, curved valley or on a bound, and the lowest start does not
+    always lead to the lowest optimum), the lowest misfit of the three is
+    the stored optimum."""
     spec = W.get("c3")
     cyc, xt = W.c3_layout(spec)
     pm = O.make_pmap(spec)
@@ -93,8 +94,8 @@ def c3_subset(n_sub: int = 32):
         xo, So = O.lm_polish(c, pm, U_m, starts, steps=12)
         cands = [(float(S), np.asarray(x, dtype=np.float64))] + \
             [(float(So[k]), xo[:, k]) for k in range(2)]
-        S_opt, x_opt = min(cands, key=lambda t: t[0])
-        x_opt, S_opt = O.refine_optimum(c, pm, U_m, x_opt)
+        refined = [O.refine_optimum(c, pm, U_m, xc) for _, xc in cands]
+        x_opt, S_opt = min(refined, key=lambda t: t[1])
         pixels.append(dict(pixel=i, cycles=int(cyc[i]), x=[float(v) for v in x_opt],
                            S_m2=S_opt, x_pso=[float(v) for v in x], S_pso_m2=float(S),
                            sumU2_m2=float(np.sum(U_m ** 2)),
