@@ -1285,6 +1285,115 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # Small untimed cases for profiler captures
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# Configuration sweeps behind the workloads' polish settings (--sweep)
+# ---------------------------------------------------------------------------
+def _timed_results(A, fn):
+    """One untimed call, then one timed call; (ms, decoded results)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1), A.decode_results(r[0] if isinstance(r, tuple) else r)
+
+
+def sweep_lm(A, W, dev, name):
+    """Swarm updates x LM steps of the single-inversion polish (64
+    candidates, 8 damping values) on 16 seeded records: median ms and the
+    records within one noise variance of the best point any run found
+    (a 100-update plain swarm and a 6 x 12 polish included)."""
+    import numpy as np
+    import torch
+    spec = W.get(name)
+    D, N = len(spec["free"]), W.n_steps(spec)
+    prob = A.make_problem(spec)
+    var = (spec["sigma"] / 1e-9) ** 2
+    off = torch.tensor([0, N], dtype=torch.int64, device=dev)
+    configs = [(3, 6), (3, 5), (2, 5), (3, 4), (4, 4), (2, 6)]
+    runs = {c: [] for c in configs}
+    best = []
+    for pix in range(16):
+        rng = np.random.default_rng(spec["seed"] + 1000 * pix)
+        xt = rng.uniform(0.1, 0.9, size=(D, 1))
+        U = A.synth_records(prob, torch.from_numpy(xt).to(dev), off, spec["record_sub"],
+                            spec["sigma"], spec["seed"], pix)
+        Ss = [A.decode_result(A.invert(prob, U, A.make_pso(dict(spec, iters=100), pixel=pix))[0])["S_f64"],
+              A.decode_result(A.invert_polished(prob, U, A.make_pso(dict(spec, iters=6), pixel=pix),
+                                                64, 12, 8, method="lm")[0])["S_f64"]]
+        for (it, st) in configs:
+            cfg = A.make_pso(dict(spec, iters=it), pixel=pix)
+            ms, r = _timed_results(A, lambda: A.invert_polished(prob, U, cfg, 64, st, 8, method="lm"))
+            runs[(it, st)].append((ms, r[0]["S_f64"]))
+            Ss.append(r[0]["S_f64"])
+        best.append(min(Ss))
+    for c in configs:
+        d = np.array([(s - b) / var for (_, s), b in zip(runs[c], best)])
+        print(json.dumps({"workload": name, "updates": c[0], "lm_steps": c[1],
+                          "median_ms": float(np.median([m for m, _ in runs[c]])),
+                          "records_at_best": int((d <= 1.0).sum()), "max_dchi2": float(d.max())}))
+
+
+def sweep_polish(A, W, dev):
+    """Swarm updates x best K x LM steps (4 damping values) of the polished
+    4096-pixel batch: ms, the pixels within one noise variance of the better
+    of it and the plain batch, and the accuracy against the oracle's stored
+    optima (accuracy_vs_oracle)."""
+    import numpy as np
+    import torch
+    spec, prob, U, off, _, _, _ = c3_inputs(A, W, dev)
+    var = (spec["sigma"] / 1e-9) ** 2
+    _, plain = _timed_results(A, lambda: A.invert_batch(prob, U, off, A.make_pso(spec)))
+    Sp = np.array([r["S_f64"] for r in plain])
+    for it, k, st in ((2, 32, 5), (2, 32, 4), (2, 32, 3), (2, 16, 5), (1, 32, 5), (1, 32, 4),
+                      (1, 32, 3), (1, 24, 4), (0, 32, 5)):
+        cfg = A.make_pso(dict(spec, iters=it))
+        ms, rs = _timed_results(A, lambda: A.invert_batch_polished(prob, U, off, cfg, k, st, 4,
+                                                                  method="lm"))
+        S = np.array([r["S_f64"] for r in rs])
+        acc = accuracy_vs_oracle(A, spec, U, off, rs)
+        print(json.dumps({"updates": it, "best_k": k, "lm_steps": st, "ms": ms,
+                          "frac_dchi2_le_1_vs_plain": float(np.mean((S - np.minimum(S, Sp)) / var <= 1.0)),
+                          "oracle_pixels": acc["pixels"], "frac_meeting_both": acc["frac_meeting_both"]}))
+
+
+def sweep_image(A, W, dev):
+    """Cold and warm-start configurations of the 64 x 64 image scan: ms and
+    the pixels within one noise variance of the best of all runs."""
+    import numpy as np
+    import torch
+    spec = W.get("f1_image")
+    Wd, Hd = spec["width"], spec["height"]
+    n_pix, D, N = Wd * Hd, len(spec["free"]), W.n_steps(spec)
+    xt = W.image_truth(D, Wd, Hd, spec["seed"])
+    prob = A.make_problem(spec)
+    off = torch.arange(0, (n_pix + 1) * N, N, dtype=torch.int64, device=dev)
+    U = A.synth_records(prob, torch.from_numpy(xt).to(dev), off, spec["record_sub"], spec["sigma"],
+                        spec["seed"], 0)
+    var = (spec["sigma"] / 1e-9) ** 2
+    runs = {}
+    for c in ((5, 8, 12, 8), (1, 32, 4, 4), (2, 32, 4, 4), (1, 32, 5, 4), (1, 16, 4, 4)):
+        cfg = A.make_pso(dict(spec, iters=c[0]))
+        runs[("cold",) + c] = _timed_results(
+            A, lambda: A.invert_batch_polished(prob, U, off, cfg, c[1], c[2], c[3], method="lm"))
+    for c, f in (((5, 8, 12, 8), (0, 4, 6)), ((1, 32, 4, 4), (0, 4, 6)), ((1, 32, 4, 4), (0, 8, 4)),
+                 ((1, 32, 4, 4), (0, 4, 4)), ((5, 8, 12, 8), (0, 8, 4))):
+        coarse = A.make_pso(dict(spec, iters=c[0]))
+        fine = A.make_pso(dict(spec, P=spec["fine"]["P"], iters=f[0]))
+        icfg = A.make_image_cfg(Wd, Hd, spec["stride"], spec["margin"], coarse, fine,
+                                coarse_polish=(c[1], c[2]), fine_polish=(f[1], f[2]), n_cand=c[3],
+                                method="lm")
+        runs[("warm",) + c + f] = _timed_results(A, lambda: A.invert_image(prob, U, off, icfg))
+    S = {k: np.array([r["S_f64"] for r in v[1]]) for k, v in runs.items()}
+    best = np.min(np.array(list(S.values())), axis=0)
+    for k, (ms, _) in runs.items():
+        print(json.dumps({"run": list(k), "ms": ms,
+                          "frac_dchi2_le_1_vs_best": float(np.mean((S[k] - best) / var <= 1.0))}))
+
+
 def run_probe(args):
     """--probe invert: one inversion of the workload with --probe-iters
     updates; --probe forward: two forward + misfit launches over
@@ -1414,6 +1523,8 @@ def main():
                                         "polish_full"],
                     default=None,
                     help="run one small untimed case for a profiler capture and exit")
+    ap.add_argument("--sweep", choices=["lm_c2", "lm_c4", "polish", "image"], default=None,
+                    help="run the configuration sweep behind a workload's polish settings and exit")
     ap.add_argument("--probe-iters", type=int, default=2)
     ap.add_argument("--probe-kp", type=int, default=None,
                     help="particles per thread of the batch probe (default: autotuned)")
@@ -1421,6 +1532,19 @@ def main():
     args = ap.parse_args()
     if args.probe:
         run_probe(args)
+    elif args.sweep is not None:
+        import torch
+        from paper_1109_0334_gb300 import build as B
+        B.build()
+        from paper_1109_0334_gb300 import afminv as A
+        from paper_1109_0334_gb300 import workloads as W
+        dev = torch.device("cuda", 0)
+        if args.sweep.startswith("lm_"):
+            sweep_lm(A, W, dev, args.sweep[3:])
+        elif args.sweep == "polish":
+            sweep_polish(A, W, dev)
+        else:
+            sweep_image(A, W, dev)
     elif args.impl == "reference":
         run_reference(args)
     else:
